@@ -1,0 +1,341 @@
+#!/usr/bin/env python
+"""Benchmark of FGA registration on GB300 (one JSON line on stdout).
+
+Workload: two 120k-point LiDAR-like sweeps (64 rings, ground plane + box
+obstacles, 1/r^2 density fall-off, ~50 % overlap, sigma = 0.02 m), NIV masses
+(lattice 16), Barnes-Hut with theta = 0.5, 200 iterations of Algorithm 2,
+FP32 forces with FP64 reductions. One step = one whole registration
+(normalisation, masses, tree build, 200 iterations, de-normalisation) of one
+pair whose inputs are already resident in device memory.
+
+Metric: pair-interactions/s = force terms evaluated (accepted cells + leaf
+particles, counted on the device) per second of registration time; the line
+also carries registrations/s and p50/p99 latency. ``e2e`` repeats the
+measurement through the same C call with pinned HOST inputs (host->device
+copies and the result read-back inside the timed region).
+
+``--impl reference`` times the FP64 CPU oracle on the same workload (each step
+a bounded sample: one iteration of the loop on the full pair) on the host
+cores.
+
+Multi-GPU (torchrun): every rank registers its own pairs (no collective on the
+data path); the timing is the max over ranks, the value the sum over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+FLOPS_NOTE = "12 FP32 instructions + 1 MUFU rsqrt per interaction"
+FP32_INSTR_PER_INTERACTION = 12
+FP32_LANES_PER_SM = 128
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=120_000, help="points per sweep")
+    ap.add_argument("--iters", type=int, default=200)
+    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--pairs", type=int, default=2, help="distinct seeded pairs per rank")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-iters", type=int, default=2, help="oracle iterations per CPU sample")
+    return ap.parse_args(argv)
+
+
+# --------------------------------------------------------------------------- distributed helpers
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def shard_seeds(rank: int, world: int, pairs: int, base: int = 1000):
+    """Seeds of the pairs a rank registers: disjoint across ranks (weak scaling)."""
+    return [base * (rank + 1) + k for k in range(pairs)]
+
+
+def reduce_max_sum(t_ms: float, units: float, world: int):
+    """(max over ranks of t_ms, sum over ranks of units)."""
+    if world == 1:
+        return t_ms, units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    a = torch.tensor([t_ms], dtype=torch.float64, device=dev)
+    b = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(a, op=dist.ReduceOp.MAX)
+    dist.all_reduce(b, op=dist.ReduceOp.SUM)
+    return float(a.item()), float(b.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# --------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for ln in open(self.path):
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons, "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------- roofline
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def source_hash(path):
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel_file: str, summary: str):
+    """Per-launch DRAM bytes from a committed ncu summary, if it was taken on the
+    current source of the kernel (line 'traffic_bytes_per_launch: <B> source_sha: <h>')."""
+    p = os.path.join(ROOT, "profiles", summary)
+    if not os.path.exists(p):
+        return None
+    cur = source_hash(os.path.join(ROOT, kernel_file))
+    for ln in open(p):
+        if ln.startswith("traffic_bytes_per_launch:"):
+            parts = ln.split()
+            if len(parts) >= 4 and parts[3] == cur:
+                return float(parts[1])
+    return None
+
+
+# --------------------------------------------------------------------------- workload
+
+def workload_config(a):
+    return {"workload": "lidar-sweeps-%dk-bh-theta%.1f-%dit" % (a.n // 1000, a.theta, a.iters),
+            "N": a.n, "M": a.n, "iterations": a.iters, "method": "barnes-hut", "theta": a.theta,
+            "masses": "NIV lattice 16 (reference), uniform (template)", "eps": 0.2, "eta": 0.2,
+            "dt": 0.1, "G": 66.7, "pairs_per_rank": a.pairs,
+            "l2": "flushed between steps (256 MB device write outside the timed events)",
+            "inputs": "resident in HBM at the start of each timed step"}
+
+
+def make_pairs(seeds, n):
+    return [synth.lidar_pair(s, n=n) for s in seeds]
+
+
+def cpu_sample(pair, a, iters):
+    """The FP64 oracle on one full pair for `iters` iterations (bounded sample)."""
+    import oracle
+    oracle.build()
+    X, Y, _, _ = pair
+    p = oracle.Params(method=oracle.FGA_BH, theta=a.theta, max_iter=iters, niv_masses=True)
+    t0 = time.perf_counter()
+    o = oracle.register_full(X, Y, p)
+    dt = time.perf_counter() - t0
+    return o["interactions"], dt, oracle.max_threads()
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    pair = make_pairs(shard_seeds(0, 1, 1), a.n)[0]
+    for _ in range(a.warmup):
+        cpu_sample(pair, a, 1)
+    total_i, total_t, cores = 0, 0.0, 1
+    for _ in range(a.steps):
+        i, t, cores = cpu_sample(pair, a, 1)
+        total_i += i
+        total_t += t
+    value = total_i / total_t
+    sample = ("FP64 C oracle, Algorithm 2 with BHForce: normalisation, NIV masses, tree and ONE "
+              "iteration of the loop on the full %d x %d pair per step" % (a.n, a.n))
+    line = {"impl": "reference", "metric": "pair-interactions/s", "value": value,
+            "unit": "interactions/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * total_t / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": workload_config(a),
+            "cpu_baseline": {"value": value, "unit": "interactions/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "interactions/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(a):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2009_14005_gb300 as fga
+
+    pairs = make_pairs(shard_seeds(rank, world, a.pairs), a.n)
+    dev = [(torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda")) for X, Y, _, _ in pairs]
+    host = [(torch.from_numpy(X).pin_memory(), torch.from_numpy(Y).pin_memory()) for X, Y, _, _ in pairs]
+    p = fga.params(method=fga.FGA_BH, theta=a.theta, max_iter=a.iters, mass_mode=fga.FGA_MASS_NIV,
+                   profile=1)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    for k in range(a.warmup):
+        Xd, Yd = dev[k % len(dev)]
+        fga.fga_register(Xd, Yd, p)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = fga.fga_launch_count()
+    step_ms, inter, force_ms, force_launches = [], 0, 0.0, 0
+    for k in range(a.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        Xd, Yd = dev[k % len(dev)]
+        e0.record(stream)
+        R, t, st = fga.fga_register(Xd, Yd, p, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        inter += st["interactions"]
+        force_ms += st["force_ms"]
+        force_launches += st["force_launches"]
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = fga.fga_launch_count() - launches0
+    clk = clocks.stop()
+    t_local = sum(step_ms)
+    t_max, inter_all = reduce_max_sum(t_local, float(inter), world)
+    value = inter_all / (t_max / 1e3)
+
+    # end to end through the same C call with pinned host inputs
+    e2e_t, e2e_i, h2d, d2h = 0.0, 0, 0, 0
+    for k in range(a.e2e_steps):
+        Xh, Yh = host[k % len(host)]
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        R, t, st = fga.fga_register(Xh, Yh, p, stream=stream)
+        e2e_t += time.perf_counter() - t0
+        e2e_i += st["interactions"]
+        h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
+    e2e_tmax, e2e_iall = reduce_max_sum(1e3 * e2e_t, float(e2e_i), world)
+
+    if rank != 0:
+        return 0
+    peaks, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_rate = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / FP32_INSTR_PER_INTERACTION
+    launch_inter = inter / max(force_launches, 1)
+    launch_s = force_ms / 1e3 / max(force_launches, 1)
+    achieved = launch_inter / launch_s if launch_s > 0 else 0.0
+    roof = {"bound": "alu", "kernel": "k_bh", "achieved": achieved / 1e9, "peak": peak_rate / 1e9,
+            "unit": "Ginteractions/s", "frac": achieved / peak_rate,
+            "traffic": recorded_traffic("paper_2009_14005_gb300/csrc/fga_force.cu",
+                                        "k_bh_lidar120k.md"),
+            "peak_source": "%d SMs x %d FP32 lanes x %.0f MHz (sm_max_mhz, %s) / %d FP32 "
+                           "instructions per interaction" % (sms, FP32_LANES_PER_SM, sm_mhz, peak_src,
+                                                             FP32_INSTR_PER_INTERACTION),
+            "launches": force_launches, "interactions_per_launch": launch_inter,
+            "mean_launch_ms": 1e3 * launch_s, "share_of_step": force_ms / max(t_local, 1e-9)}
+    line = {"metric": "pair-interactions/s", "value": value, "unit": "interactions/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(a),
+            "registrations_per_s": a.steps * world / (t_max / 1e3),
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "e2e": {"value": e2e_iall / (e2e_tmax / 1e3), "unit": "interactions/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_tmax / max(a.e2e_steps, 1)},
+            "gpu_launches": launches, "roofline": roof, "clocks": clk}
+    if world == 1 and not a.no_cpu_baseline:
+        i, t, cores = cpu_sample(pairs[0], a, a.cpu_iters)
+        line["cpu_baseline"] = {"value": i / t, "unit": "interactions/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": "FP64 C oracle (OpenMP), normalisation + NIV masses + tree + "
+                                          "%d of %d iterations on the first %dk x %dk pair (%.1f s)"
+                                          % (a.cpu_iters, a.iters, a.n // 1000, a.n // 1000, t)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    a = parse_args(argv)
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_ours(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,231 @@
+/*
+ * libfga -- GB300 (sm_103a) implementation of the hot path of the Fast
+ * Gravitational Approach (FGA) to rigid point-set registration
+ * (arXiv 2009.14005, "Fast Gravitational Approach for Rigid Point Set
+ * Registration with Ordinary Differential Equations").
+ *
+ * Plain C ABI: host or device pointers and sizes, no C++ or framework types.
+ * Notation follows the paper (Sec. IV-A): the template Y has M points and moves,
+ * the reference X has N points and is fixed, D = 3.
+ *
+ * Conventions for every entry point
+ *  - Point arrays are contiguous row-major float[n][3] (x, y, z per point),
+ *    mass arrays float[n]. Unless an argument says otherwise they are DEVICE
+ *    pointers on the current CUDA device, owned by the caller, and must stay
+ *    valid until the work queued on `stream` has finished.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *    stream. Work is queued asynchronously unless the function says it
+ *    synchronises.
+ *  - Return value: FGA_OK (0) or a negative FGA_E* code. Nothing is thrown
+ *    across the ABI. fga_last_error() returns a thread-local message for the
+ *    last failure of the calling thread.
+ *  - Opaque handles (fga_tree, fga_state) are owned by the library and freed by
+ *    the matching *_destroy call.
+ */
+#ifndef FGA_H
+#define FGA_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ----------------------------------------------------------------- status codes */
+#define FGA_OK 0
+#define FGA_EINVAL -1      /* bad size, non-finite input, eps <= 0, theta < 0, ... */
+#define FGA_ENOMEM -2      /* device or host allocation failed                      */
+#define FGA_ECUDA -3       /* a CUDA runtime call failed (message has the name)     */
+#define FGA_EDEGENERATE -4 /* a rigid fit had rank(C) < 2; best-effort R, t returned */
+#define FGA_EINTERNAL -5   /* a device-side consistency check failed                */
+
+/* ----------------------------------------------------------------- parameters */
+#define FGA_DIRECT 0 /* all-pairs sum of Eq. 6                          */
+#define FGA_BH 1     /* Barnes-Hut tree (Algorithm 1) + BHForce (Eq. 15) */
+
+#define FGA_VEL_UNCONSTRAINED 0 /* velocities of Eq. 9 persist between iterations */
+#define FGA_VEL_RIGID 1         /* velocities replaced by the rigid motion        */
+
+#define FGA_MASS_UNIFORM 0 /* equal masses                              */
+#define FGA_MASS_NIV 1     /* normalised intrinsic volume, Eq. 18       */
+
+typedef struct fga_params {
+  float G;           /* gravitational constant (paper default 66.7)             */
+  float eps;         /* softening length epsilon of Eq. 6 (0.2)                 */
+  float eta;         /* dissipation eta of Eq. 7 (0.2)                          */
+  float dt;          /* time step of Eqs. 9-10 (0.1)                            */
+  float theta;       /* opening criterion of Eq. 15 (0.6)                       */
+  int max_iter;      /* iterations of Algorithm 2's loop                        */
+  float conv_tol;    /* stop once |T_k - T_{k-2}|_F^2 <= conv_tol; <= 0 disables */
+  int method;        /* FGA_DIRECT or FGA_BH                                    */
+  int normalize;     /* 1: scale inputs into [a, b] (Appendix A) in fga_register */
+  float a, b;        /* normalisation range (-5, 5)                             */
+  int velocity_mode; /* FGA_VEL_UNCONSTRAINED or FGA_VEL_RIGID                  */
+  int max_depth;     /* BH tree depth limit, 1..20 (20)                         */
+  int mass_mode;     /* reference masses in fga_register: FGA_MASS_UNIFORM/_NIV  */
+  int lattice;       /* NIV lattice resolution varrho (16)                      */
+  int profile;       /* 1: time every force-kernel launch with CUDA events on the
+                        launch stream (reported in fga_stats.force_ms)           */
+} fga_params;
+
+/* Fills `p` with the paper's defaults (Sec. V, parameter settings):
+ * G = 66.7, eps = 0.2, eta = 0.2, dt = 0.1, theta = 0.6, [a, b] = [-5, 5],
+ * depth 20, lattice 16; plus max_iter = 100, conv_tol = 0 (fixed iteration
+ * count), method = FGA_BH, normalize = 1, velocity_mode = UNCONSTRAINED,
+ * mass_mode = UNIFORM, profile = 0. */
+void fga_params_default(fga_params* p);
+
+typedef struct fga_stats {
+  int iterations;           /* iterations actually run                         */
+  int converged;            /* 1 if the conv_tol test stopped the loop         */
+  int degenerate_fits;      /* iterations whose rigid fit was rank-deficient   */
+  int status;               /* FGA_OK or the code that fga_register returned   */
+  int64_t interactions;     /* force terms evaluated (direct: N*M per iteration;
+                               BH: accepted cells + leaf particles, counted on
+                               the device)                                      */
+  double last_conv;         /* last |T_k - T_{k-2}|_F^2                         */
+  double net_force[3];      /* sum_i m_Yi a_i of the last iteration (FP64)      */
+  double torque[3];         /* sum_i (Y_i - mu_Y) x m_Yi a_i, last iteration    */
+  double R_norm[9];         /* final R in the normalised frame (row-major)     */
+  double t_norm[3];         /* final t in the normalised frame                  */
+  double norm_info[8];      /* Xbar[3], Ybar[3], l, s of Appendix A             */
+  double elapsed_ms;        /* host wall time of the call                       */
+  double force_ms;          /* with profile: summed device time of the force
+                               kernels (all-pairs or BH), CUDA events           */
+  int force_launches;       /* with profile: number of force-kernel launches    */
+  int64_t h2d_bytes;        /* fga_register: bytes copied host -> device        */
+  int64_t d2h_bytes;        /* fga_register: bytes copied device -> host        */
+} fga_stats;
+
+/* ----------------------------------------------------------------- error query */
+/* Message of the calling thread's last failure ("" if none). Owned by the library. */
+const char* fga_last_error(void);
+/* Number of kernels this library has launched in this process (all threads). */
+int64_t fga_launch_count(void);
+
+/* ----------------------------------------------------------------- Appendix A */
+/* Normalisation of Appendix A, Eqs. A.1-A.3: subtracts each cloud's mean,
+ * takes the global scalar minimum l and maximum r over all coordinates of both
+ * centred clouds, and writes X^ = (X - Xbar - l)(b - a)/(r - l) + a (same for Y).
+ * X (N x 3), Y (M x 3), Xn_out (N x 3), Yn_out (M x 3): device pointers; the
+ * outputs may alias the inputs. info_out (host, 8 doubles) receives
+ * {Xbar[3], Ybar[3], l, s = (b-a)/(r-l)}; the call synchronises `stream`.
+ * Errors: FGA_EINVAL if N or M <= 0, b <= a, a non-finite input, or r == l. */
+int fga_normalize(const float* X, int64_t N, const float* Y, int64_t M, float a, float b,
+                  float* Xn_out, float* Yn_out, double info_out[8], void* stream);
+
+/* De-normalised translation (host only, no GPU work). For a transform
+ * [R | t_norm] that maps the normalised template onto the normalised
+ * reference, returns t such that X = R Y + t in the original frames:
+ * t = Xbar - R Ybar + l (1 - R 1) + (R a1 + t_norm - a1) / s, the solution of
+ * A.3 for X (Appendix, derivation of dnorm(t)). R is row-major, unchanged by
+ * the isotropic normalisation. */
+void fga_denormalize(const double R[9], const double t_norm[3], const double info[8], float a,
+                     double t_out[3]);
+
+/* ----------------------------------------------------------------- Sec. IV-F */
+/* Point masses (boundary conditions, Sec. IV-F), scaled so that they sum to
+ * `total`. mode = FGA_MASS_UNIFORM gives total/n each; FGA_MASS_NIV evaluates
+ * Eq. 18 on a lattice^3 lattice over [a, b]^3 (points are expected inside the
+ * normalised domain; outside points are clamped to the border cells): each
+ * point carries a ball of radius (b-a)/(2*3*lattice), a cell holding n points
+ * is covered to the fraction f = 1 - (1 - V(ball)/V(cell))^n, and a point's
+ * weight is 1/f of its cell.
+ * pts: device (n x 3); masses_out: device (n). lattice in 1..256.
+ * Errors: FGA_EINVAL for n <= 0, bad mode/lattice, b <= a, total <= 0. */
+int fga_masses(const float* pts, int64_t n, int mode, int lattice, float a, float b,
+               double total, float* masses_out, void* stream);
+
+/* ----------------------------------------------------------------- Sec. IV-E */
+typedef struct fga_tree fga_tree;
+
+/* Barnes-Hut tree of Algorithm 1 on the (normalised) reference X with masses
+ * mX: the root box is the tight bounding box of X, a cell with more than one
+ * point above depth p->max_depth is split at its box midpoint into 2^3 cells
+ * (points on a split plane go to the upper cell; an axis of zero extent is not
+ * split), and every cell stores its diagonal l, mass and centre of mass. Cells
+ * with a single non-empty child are skipped (their BH contribution equals the
+ * child's). Only p->max_depth is read from `p`.
+ * X: device (N x 3), mX: device (N) or NULL for masses 1/N. The tree keeps its
+ * own copy of the bodies; X and mX may be freed once the stream has passed.
+ * Errors: FGA_EINVAL (N <= 0, bad depth, non-finite X), FGA_ENOMEM, FGA_ECUDA. */
+int fga_tree_build(const float* X, const float* mX, int64_t N, const fga_params* p,
+                   fga_tree** out, void* stream);
+void fga_tree_destroy(fga_tree* t);
+/* Number of stored cells (internal cells with >= 2 children, plus leaves). */
+int64_t fga_tree_node_count(const fga_tree* t);
+
+/* Host copy of the tree in canonical pre-order, children in octant order
+ * (the same layout the FP64 oracle exports): ints (cap x 7) = depth, cell x,
+ * cell y, cell z, points, is_leaf, parent; dbls (cap x 5) = mass, CoM x, y, z,
+ * l; leaf_of (N, optional) = index of the leaf holding each original point.
+ * Host pointers; synchronises `stream`. Returns the node count (>= 0) or an
+ * FGA_E* code. Call with cap = 0 to size the buffers. */
+int64_t fga_tree_export(const fga_tree* t, int64_t cap, int64_t* ints, double* dbls,
+                        int64_t* leaf_of, void* stream);
+
+/* ----------------------------------------------------------------- Sec. IV-C/E */
+/* Gravitational force on every template point, Eq. 6:
+ *   F_i = G m_Yi sum_j m_Xj (X_j - Y_i) / (|X_j - Y_i|^2 + eps^2)^(3/2),
+ * summed over all X (tree == NULL: X, mX, N are used) or approximated by
+ * BHForce on `tree` with opening parameter p->theta (Eq. 15; X, mX, N are then
+ * ignored and may be NULL). mY NULL means m_Yi = 1, i.e. the output is the
+ * acceleration. FP32 arithmetic with compensated per-point accumulation.
+ * Y: device (M x 3); acc_out: device (M x 3), same order as Y.
+ * interactions_out (host, optional): number of force terms evaluated; when
+ * given, the call synchronises `stream`.
+ * Errors: FGA_EINVAL (sizes, eps <= 0, theta < 0), FGA_ENOMEM, FGA_ECUDA. */
+int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N, const float* Y,
+               const float* mY, int64_t M, const fga_params* p, float* acc_out,
+               int64_t* interactions_out, void* stream);
+
+/* ----------------------------------------------------------------- Algorithm 2 */
+typedef struct fga_state fga_state;
+
+/* Device-resident state of Algorithm 2 on NORMALISED inputs with FINAL masses:
+ * T = [I | 0], V = 0. Xn (N x 3), mX (N, NULL: 1/N each), Yn (M x 3),
+ * mY (M, NULL: dt each, i.e. Eq. 7's friction removes the fraction eta of the
+ * velocity per step) are device pointers copied into the state. For
+ * p->method == FGA_BH the tree is built from Xn/mX unless `tree` is given
+ * (borrowed, must outlive the state). The state keeps the template sorted
+ * along a Morton curve so that neighbouring threads follow similar tree paths.
+ * Errors: FGA_EINVAL, FGA_ENOMEM, FGA_ECUDA. */
+int fga_state_create(const float* Xn, const float* mX, int64_t N, const float* Yn,
+                     const float* mY, int64_t M, const fga_tree* tree, const fga_params* p,
+                     fga_state** out, void* stream);
+
+/* Queues n_iter iterations of Algorithm 2's loop body on `stream`, no host
+ * synchronisation: Y = R Y0 + t; forces (Eq. 6 or BHForce); V, D (Eqs. 7-10);
+ * rigid fit R', t' (Eqs. 14, 16, FP64 reduction and 3x3 SVD on the device);
+ * R = R'R, t = R't + t'; convergence test. Once the test has fired, further
+ * iterations are no-ops. Errors: FGA_EINVAL (n_iter < 0), FGA_ECUDA. */
+int fga_step(fga_state* s, int n_iter, void* stream);
+
+/* Synchronises `stream` and reads the state: R (row-major, 9) and t (3) in the
+ * normalised frame, and optionally stats (host). Returns FGA_EDEGENERATE if any
+ * iteration's fit was rank-deficient, FGA_EINTERNAL if a device check failed. */
+int fga_state_get(fga_state* s, double R[9], double t[3], fga_stats* stats, void* stream);
+
+/* Synchronises and copies [R (9) | t (3)] after each of the first `n` iterations
+ * run so far into `out` (host, n x 12). Returns the number of rows written. */
+int fga_state_trajectory(fga_state* s, double* out, int n, void* stream);
+
+void fga_state_destroy(fga_state* s);
+
+/* Whole registration (Algorithm 2 with Appendix A): normalises X and Y into
+ * [a, b] (if p->normalize), assigns masses (mX NULL: p->mass_mode with sum 1;
+ * mY NULL: dt each; given masses are rescaled to those totals), builds the
+ * tree for FGA_BH, runs p->max_iter iterations (fewer if conv_tol stops them)
+ * and returns R, t (host, FP64) with X ~ R Y + t in the ORIGINAL frames.
+ * X, Y, mX, mY may be host or device pointers (detected per pointer); host
+ * inputs are copied to the device inside the call. Synchronises `stream`.
+ * stats (host, optional) receives the counters and the normalised-frame result.
+ * Errors: FGA_EINVAL, FGA_ENOMEM, FGA_ECUDA, FGA_EDEGENERATE (R, t still set). */
+int fga_register(const float* X, int64_t N, const float* Y, int64_t M, const float* mX,
+                 const float* mY, const fga_params* p, double R_out[9], double t_out[3],
+                 fga_stats* stats, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FGA_H */

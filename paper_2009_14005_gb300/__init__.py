@@ -1,0 +1,393 @@
+"""Python binding of libfga, the GB300 implementation of the FGA hot path.
+
+Argument marshalling only: every step runs in the CUDA kernels of
+``libfga.so`` (see ``include/fga.h`` for the C ABI). PyTorch provides device
+memory and streams. Importing this package fails loudly if ``libfga.so`` has
+not been built (``python -m paper_2009_14005_gb300.build``); there is no CPU
+fallback.
+
+The functions keep the C names:
+
+==========================  ============================================
+``fga_normalize``            Appendix A (A.1-A.3)
+``fga_denormalize``          dnorm(t) of the Appendix (host arithmetic)
+``fga_masses``               Sec. IV-F, uniform or NIV (Eq. 18)
+``fga_tree_build``           Algorithm 1 -> :class:`Tree`
+``fga_forces``               Eq. 6 (all pairs) or BHForce (Eq. 15)
+``fga_state_create``         Algorithm 2 state -> :class:`State`
+``fga_step`` / ``fga_state_get`` / ``fga_state_trajectory``
+``fga_register``             Algorithm 2 end to end (host or device inputs)
+==========================  ============================================
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libfga.so")
+
+FGA_OK = 0
+FGA_EINVAL = -1
+FGA_ENOMEM = -2
+FGA_ECUDA = -3
+FGA_EDEGENERATE = -4
+FGA_EINTERNAL = -5
+
+FGA_DIRECT = 0
+FGA_BH = 1
+FGA_VEL_UNCONSTRAINED = 0
+FGA_VEL_RIGID = 1
+FGA_MASS_UNIFORM = 0
+FGA_MASS_NIV = 1
+
+SYMBOLS = [
+    "fga_params_default", "fga_last_error", "fga_launch_count", "fga_normalize",
+    "fga_denormalize", "fga_masses", "fga_tree_build", "fga_tree_destroy",
+    "fga_tree_node_count", "fga_tree_export", "fga_forces", "fga_state_create", "fga_step",
+    "fga_state_get", "fga_state_trajectory", "fga_state_destroy", "fga_register",
+]
+
+
+class fga_params(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_float), ("eps", ctypes.c_float), ("eta", ctypes.c_float),
+                ("dt", ctypes.c_float), ("theta", ctypes.c_float), ("max_iter", ctypes.c_int),
+                ("conv_tol", ctypes.c_float), ("method", ctypes.c_int),
+                ("normalize", ctypes.c_int), ("a", ctypes.c_float), ("b", ctypes.c_float),
+                ("velocity_mode", ctypes.c_int), ("max_depth", ctypes.c_int),
+                ("mass_mode", ctypes.c_int), ("lattice", ctypes.c_int),
+                ("profile", ctypes.c_int)]
+
+
+class fga_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("converged", ctypes.c_int),
+                ("degenerate_fits", ctypes.c_int), ("status", ctypes.c_int),
+                ("interactions", ctypes.c_int64), ("last_conv", ctypes.c_double),
+                ("net_force", ctypes.c_double * 3), ("torque", ctypes.c_double * 3),
+                ("R_norm", ctypes.c_double * 9), ("t_norm", ctypes.c_double * 3),
+                ("norm_info", ctypes.c_double * 8), ("elapsed_ms", ctypes.c_double),
+                ("force_ms", ctypes.c_double), ("force_launches", ctypes.c_int),
+                ("h2d_bytes", ctypes.c_int64), ("d2h_bytes", ctypes.c_int64)]
+
+    def to_dict(self):
+        return dict(iterations=self.iterations, converged=bool(self.converged),
+                    degenerate_fits=self.degenerate_fits, status=self.status,
+                    interactions=int(self.interactions), last_conv=self.last_conv,
+                    net_force=np.array(self.net_force[:]), torque=np.array(self.torque[:]),
+                    R_norm=np.array(self.R_norm[:]).reshape(3, 3), t_norm=np.array(self.t_norm[:]),
+                    norm_info=np.array(self.norm_info[:]), elapsed_ms=self.elapsed_ms,
+                    force_ms=self.force_ms, force_launches=self.force_launches,
+                    h2d_bytes=int(self.h2d_bytes), d2h_bytes=int(self.d2h_bytes))
+
+
+class FGAError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("libfga error %d: %s" % (code, msg))
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libfga.so is not built; run `python -m paper_2009_14005_gb300.build` "
+                          "(there is no CPU fallback)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I64, VP, F, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_float, ctypes.c_double
+    PP = ctypes.POINTER(fga_params)
+    DP = ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "fga_params_default": (None, [PP]),
+        "fga_last_error": (ctypes.c_char_p, []),
+        "fga_launch_count": (I64, []),
+        "fga_normalize": (ctypes.c_int, [P, I64, P, I64, F, F, P, P, DP, VP]),
+        "fga_denormalize": (None, [DP, DP, DP, F, DP]),
+        "fga_masses": (ctypes.c_int, [P, I64, ctypes.c_int, ctypes.c_int, F, F, D, P, VP]),
+        "fga_tree_build": (ctypes.c_int, [P, P, I64, PP, ctypes.POINTER(ctypes.c_void_p), VP]),
+        "fga_tree_destroy": (None, [P]),
+        "fga_tree_node_count": (I64, [P]),
+        "fga_tree_export": (I64, [P, I64, P, P, P, VP]),
+        "fga_forces": (ctypes.c_int, [P, P, P, I64, P, P, I64, PP, P, ctypes.POINTER(I64), VP]),
+        "fga_state_create": (ctypes.c_int, [P, P, I64, P, P, I64, P, PP,
+                                            ctypes.POINTER(ctypes.c_void_p), VP]),
+        "fga_step": (ctypes.c_int, [P, ctypes.c_int, VP]),
+        "fga_state_get": (ctypes.c_int, [P, DP, DP, ctypes.POINTER(fga_stats), VP]),
+        "fga_state_trajectory": (ctypes.c_int, [P, DP, ctypes.c_int, VP]),
+        "fga_state_destroy": (None, [P]),
+        "fga_register": (ctypes.c_int, [P, I64, P, I64, P, P, PP, DP, DP,
+                                        ctypes.POINTER(fga_stats), VP]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _err(code):
+    if code != FGA_OK:
+        raise FGAError(code, lib.fga_last_error().decode())
+
+
+def last_error() -> str:
+    return lib.fga_last_error().decode()
+
+
+def fga_launch_count() -> int:
+    return int(lib.fga_launch_count())
+
+
+def params(**kw) -> fga_params:
+    """fga_params with the paper's defaults (``fga_params_default``) and overrides."""
+    p = fga_params()
+    lib.fga_params_default(ctypes.byref(p))
+    for k, v in kw.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+# --------------------------------------------------------------------------- marshalling
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(_torch().cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev(t, cols=None, name="tensor"):
+    """Contiguous float32 CUDA tensor (no copy if it already is one)."""
+    torch = _torch()
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(np.asarray(t, dtype=np.float32))
+    if not t.is_cuda:
+        t = t.to("cuda")
+    t = t.to(torch.float32).contiguous()
+    if cols is not None and (t.dim() != 2 or t.shape[1] != cols):
+        raise ValueError("%s must have shape (n, %d)" % (name, cols))
+    return t
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _d(a, n):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64).reshape(n))
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+# --------------------------------------------------------------------------- Appendix A
+
+def fga_normalize(X, Y, a: float = -5.0, b: float = 5.0, stream=None):
+    torch = _torch()
+    X, Y = _dev(X, 3, "X"), _dev(Y, 3, "Y")
+    Xn, Yn = torch.empty_like(X), torch.empty_like(Y)
+    info = np.zeros(8)
+    _err(lib.fga_normalize(_ptr(X), X.shape[0], _ptr(Y), Y.shape[0], a, b, _ptr(Xn), _ptr(Yn),
+                           _dp(info), _stream(stream)))
+    return Xn, Yn, info
+
+
+def fga_denormalize(R, t_norm, info, a: float = -5.0):
+    R, t_norm, info = _d(R, 9), _d(t_norm, 3), _d(info, 8)
+    out = np.zeros(3)
+    lib.fga_denormalize(_dp(R), _dp(t_norm), _dp(info), a, _dp(out))
+    return out
+
+
+def fga_masses(pts, mode: int = FGA_MASS_UNIFORM, lattice: int = 16, a: float = -5.0,
+               b: float = 5.0, total: float = 1.0, stream=None):
+    torch = _torch()
+    pts = _dev(pts, 3, "pts")
+    out = torch.empty(pts.shape[0], dtype=torch.float32, device=pts.device)
+    _err(lib.fga_masses(_ptr(pts), pts.shape[0], mode, lattice, a, b, total, _ptr(out),
+                        _stream(stream)))
+    return out
+
+
+# --------------------------------------------------------------------------- Algorithm 1
+
+class Tree:
+    """Owner of an ``fga_tree`` handle (freed with fga_tree_destroy)."""
+
+    def __init__(self, handle, n):
+        self._h = handle
+        self.N = n
+
+    @property
+    def handle(self):
+        return self._h
+
+    def node_count(self) -> int:
+        return int(lib.fga_tree_node_count(self._h))
+
+    def export(self, stream=None):
+        n = self.node_count()
+        ints = np.zeros((n, 7), dtype=np.int64)
+        dbls = np.zeros((n, 5))
+        leaf_of = np.full(self.N, -1, dtype=np.int64)
+        got = lib.fga_tree_export(self._h, n, ints.ctypes.data_as(ctypes.c_void_p),
+                                  dbls.ctypes.data_as(ctypes.c_void_p),
+                                  leaf_of.ctypes.data_as(ctypes.c_void_p), _stream(stream))
+        if got < 0:
+            _err(int(got))
+        return dict(depth=ints[:, 0], cell=ints[:, 1:4], npts=ints[:, 4], is_leaf=ints[:, 5] != 0,
+                    parent=ints[:, 6], mass=dbls[:, 0], com=dbls[:, 1:4], l=dbls[:, 4],
+                    leaf_of=leaf_of)
+
+    def close(self):
+        if self._h:
+            lib.fga_tree_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fga_tree_build(X, mX=None, p: fga_params | None = None, stream=None) -> Tree:
+    p = p or params()
+    X = _dev(X, 3, "X")
+    mX = _dev(mX) if mX is not None else None
+    h = ctypes.c_void_p()
+    _err(lib.fga_tree_build(_ptr(X), _ptr(mX), X.shape[0], ctypes.byref(p), ctypes.byref(h),
+                            _stream(stream)))
+    return Tree(h, X.shape[0])
+
+
+# --------------------------------------------------------------------------- Eq. 6 / BHForce
+
+def fga_forces(tree, X, mX, Y, mY=None, p: fga_params | None = None, want_count: bool = False,
+               stream=None):
+    """Eq. 6 per template point; tree=None -> all pairs, else BHForce on ``tree``."""
+    torch = _torch()
+    p = p or params()
+    Y = _dev(Y, 3, "Y")
+    X = _dev(X, 3, "X") if X is not None else None
+    mX = _dev(mX) if mX is not None else None
+    mY = _dev(mY) if mY is not None else None
+    out = torch.empty_like(Y)
+    cnt = ctypes.c_int64(0)
+    N = X.shape[0] if X is not None else 0
+    _err(lib.fga_forces(tree.handle if tree is not None else None, _ptr(X), _ptr(mX), N, _ptr(Y),
+                        _ptr(mY), Y.shape[0], ctypes.byref(p), _ptr(out),
+                        ctypes.byref(cnt) if want_count else None, _stream(stream)))
+    return (out, int(cnt.value)) if want_count else out
+
+
+# --------------------------------------------------------------------------- Algorithm 2
+
+class State:
+    """Owner of an ``fga_state`` handle; keeps its tree and inputs alive."""
+
+    def __init__(self, handle, keep):
+        self._h = handle
+        self._keep = keep
+
+    @property
+    def handle(self):
+        return self._h
+
+    def step(self, n_iter: int, stream=None):
+        fga_step(self, n_iter, stream)
+
+    def get(self, stream=None):
+        return fga_state_get(self, stream)
+
+    def trajectory(self, n: int, stream=None):
+        return fga_state_trajectory(self, n, stream)
+
+    def close(self):
+        if self._h:
+            lib.fga_state_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fga_state_create(Xn, mX, Yn, mY, p: fga_params, tree: Tree | None = None, stream=None) -> State:
+    Xn, Yn = _dev(Xn, 3, "Xn"), _dev(Yn, 3, "Yn")
+    mX = _dev(mX) if mX is not None else None
+    mY = _dev(mY) if mY is not None else None
+    h = ctypes.c_void_p()
+    _err(lib.fga_state_create(_ptr(Xn), _ptr(mX), Xn.shape[0], _ptr(Yn), _ptr(mY), Yn.shape[0],
+                              tree.handle if tree is not None else None, ctypes.byref(p),
+                              ctypes.byref(h), _stream(stream)))
+    return State(h, (tree, Xn, Yn, mX, mY))
+
+
+def fga_step(state: State, n_iter: int, stream=None):
+    _err(lib.fga_step(state.handle, int(n_iter), _stream(stream)))
+
+
+def fga_state_get(state: State, stream=None):
+    """Returns (R, t, stats-dict) in the normalised frame; stats['status'] has the code."""
+    R = np.zeros(9)
+    t = np.zeros(3)
+    st = fga_stats()
+    code = lib.fga_state_get(state.handle, _dp(R), _dp(t), ctypes.byref(st), _stream(stream))
+    if code not in (FGA_OK, FGA_EDEGENERATE):
+        _err(code)
+    return R.reshape(3, 3), t, st.to_dict()
+
+
+def fga_state_trajectory(state: State, n: int, stream=None):
+    out = np.zeros((max(n, 0), 12))
+    rows = lib.fga_state_trajectory(state.handle, _dp(out), int(n), _stream(stream))
+    if rows < 0:
+        _err(rows)
+    return out[:rows]
+
+
+def fga_register(X, Y, p: fga_params | None = None, mX=None, mY=None, stream=None):
+    """Whole registration. X, Y (and masses) may be CUDA tensors or host arrays
+    (numpy / CPU tensors; copied to the device inside the C call).
+    Returns (R, t, stats-dict) with X ~ R Y + t in the original frames."""
+    torch = _torch()
+    p = p or params()
+
+    def host_or_dev(a, cols):
+        if a is None:
+            return None
+        if isinstance(a, torch.Tensor):
+            if a.is_cuda:
+                return _dev(a, cols)
+            return a.to(torch.float32).contiguous()
+        t = torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32)))
+        return t
+
+    Xa, Ya = host_or_dev(X, 3), host_or_dev(Y, 3)
+    mXa, mYa = host_or_dev(mX, None), host_or_dev(mY, None)
+    R = np.zeros(9)
+    t = np.zeros(3)
+    st = fga_stats()
+    code = lib.fga_register(_ptr(Xa), Xa.shape[0], _ptr(Ya), Ya.shape[0], _ptr(mXa), _ptr(mYa),
+                            ctypes.byref(p), _dp(R), _dp(t), ctypes.byref(st), _stream(stream))
+    if code not in (FGA_OK, FGA_EDEGENERATE):
+        _err(code)
+    d = st.to_dict()
+    d["status"] = code
+    return R.reshape(3, 3), t, d

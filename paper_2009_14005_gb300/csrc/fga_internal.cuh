@@ -1,0 +1,168 @@
+// Internal declarations shared by the libfga translation units.
+// Not part of the public ABI (that is include/fga.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "fga.h"
+
+namespace fga {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string& msg);
+void clear_error();
+void count_launch(int n = 1);
+
+struct Status {
+  int code = FGA_OK;
+  bool ok() const { return code == FGA_OK; }
+};
+
+#define FGA_CUDA_TRY(call)                                                          \
+  do {                                                                              \
+    cudaError_t _e = (call);                                                        \
+    if (_e != cudaSuccess) {                                                        \
+      ::fga::set_error(std::string(#call) + ": " + cudaGetErrorString(_e));         \
+      return FGA_ECUDA;                                                             \
+    }                                                                               \
+  } while (0)
+
+#define FGA_LAUNCH_CHECK(name)                                                      \
+  do {                                                                              \
+    ::fga::count_launch();                                                          \
+    cudaError_t _e = cudaGetLastError();                                            \
+    if (_e != cudaSuccess) {                                                        \
+      ::fga::set_error(std::string("launch ") + name + ": " + cudaGetErrorString(_e)); \
+      return FGA_ECUDA;                                                             \
+    }                                                                               \
+  } while (0)
+
+// ------------------------------------------------------------------ memory
+// Stream-ordered allocations from a library-owned pool per device (freed memory
+// stays cached in the pool instead of going back to the driver).
+int dev_alloc(void** p, size_t bytes, cudaStream_t s);
+void dev_free(void* p, cudaStream_t s);
+
+template <class T>
+int dev_alloc_n(T** p, size_t n, cudaStream_t s) {
+  return dev_alloc(reinterpret_cast<void**>(p), n * sizeof(T) + (n == 0 ? 16 : 0), s);
+}
+
+// Grid sizing: multiples of the SM count.
+int sm_count();
+
+// ------------------------------------------------------------------ device state
+// Per-registration state read by the force and epilogue kernels every iteration
+// and written by the rigid-fit step (one thread) at the end of every iteration.
+struct DevState {
+  double R[9], t[3];      // accumulated transform, normalised frame
+  double Tm1[12], Tm2[12];// [R|t] after the previous two iterations
+  double mu0[3];          // centroid of the initial template
+  float Rf[9], tf[3];     // FP32 copies of R, t used to place the template
+  float muf[3];           // FP32 centroid of the current template, R mu0 + t
+  float A[9], b[3];       // rigid-velocity coefficients: v = A y + b
+  double last_conv;       // |T_k - T_{k-2}|_F^2 of the last iteration
+  double netF[3], torque[3];
+  unsigned long long interactions;
+  int iter;               // iterations completed
+  int done;               // convergence test fired
+  int status;             // bit 0: stack overflow in BH traversal; bit 1: non-finite fit
+  int degenerate;         // rigid fits with rank(C) < 2
+};
+
+// Number of FP64 reduction values per block: sum y_c (3), sum d (3),
+// sum y_c y_c^T (6), sum d y_c^T (9), net force (3), torque (3).
+constexpr int NRED = 27;
+
+// ------------------------------------------------------------------ tree
+}  // namespace fga
+
+struct fga_tree {
+  int64_t N = 0;          // bodies
+  int64_t n_nodes = 0;    // stored cells
+  int n_unique = 0;       // distinct Morton keys (= leaves)
+  int max_depth = 20;
+  int device = 0;
+  float4* bodies = nullptr;      // N: x, y, z, m in Morton order
+  int* body_index = nullptr;     // N: original index of each sorted body
+  unsigned long long* keys = nullptr;  // N: sorted Morton keys
+  float4* node_cm = nullptr;     // n_nodes: centre of mass xyz, mass
+  int4* node_info = nullptr;     // n_nodes: {bits of l^2, first, count, depth}
+                                 //  count > 0: children first .. first+count-1
+                                 //  count < 0: leaf, bodies first .. first-count-1
+  int2* node_bodies = nullptr;   // n_nodes: body range [x, y) of the cell
+  float box_lo[3], box_hi[3];    // root box (tight bounding box of X)
+  cudaStream_t stream = nullptr; // stream the buffers were allocated on
+};
+
+namespace fga {
+
+// ------------------------------------------------------------------ prep kernels (fga_prep.cu)
+int check_finite(const float* p, int64_t n, int* d_flag, cudaStream_t s);
+int check_masses(const float* m, int64_t n, int* d_flag, cudaStream_t s);
+// Appendix A on the device: d_info = {Xbar[3], Ybar[3], l, s} (FP64, device),
+// d_ok = 1 if r > l. Writes normalised float xyz triples.
+int normalize_device(const float* X, int64_t N, const float* Y, int64_t M, float a, float b,
+                     float* Xn, float* Yn, double* d_info, int* d_ok, cudaStream_t s);
+int masses_device(const float* pts, int64_t n, int mode, int lattice, float a, float b,
+                  double total, float* out, cudaStream_t s);
+// Rescale masses (device) so they sum to `total`.
+int rescale_masses(const float* in, int64_t n, double total, float* out, cudaStream_t s);
+// Tight bounding box of float xyz triples or float4 bodies (device lo/hi, 3 floats each).
+int bbox_xyz(const float* p, int64_t n, float* d_lo, float* d_hi, cudaStream_t s);
+// Morton keys: `bits` per axis of floor((x - lo)/(hi - lo) * 2^bits), FP64, clamped.
+int morton_keys(const float* xyz, int64_t n, const float* d_lo, const float* d_hi, int bits,
+                unsigned long long* keys, int* idx, cudaStream_t s);
+// Stable LSD radix sort of (key, value) over the low `bits` bits; keys/vals hold
+// the result, tmp buffers are scratch of the same size.
+int radix_sort_pairs(unsigned long long* keys, int* vals, unsigned long long* keys_tmp,
+                     int* vals_tmp, int64_t n, int bits, cudaStream_t s);
+// Exclusive scan of n uint32 (device), total (device, optional).
+int scan_exclusive(const unsigned* in, unsigned* out, int64_t n, unsigned* d_total,
+                   cudaStream_t s);
+// Centroid (FP64) of float4 xyz.
+int centroid4(const float4* p, int64_t n, double* d_out3, cudaStream_t s);
+
+// ------------------------------------------------------------------ tree (fga_tree.cu)
+int tree_build(const float* X, const float* mX, int64_t N, int max_depth, fga_tree** out,
+               cudaStream_t s);
+
+// ------------------------------------------------------------------ forces (fga_force.cu)
+struct ForceBuffers {
+  float4* hi = nullptr;   // S x M compensated partial sums (value)
+  float4* lo = nullptr;   // S x M (compensation)
+  int S = 1;              // number of source splits
+};
+
+// Plan for the all-pairs kernel: block size, queries per thread, source split.
+struct DirectPlan {
+  int bs = 256, qpt = 1, S = 1;
+  int64_t chunk = 0;
+};
+DirectPlan plan_direct(int64_t N, int64_t M);
+
+int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const DevState* ds,
+                  float eps, const DirectPlan& plan, ForceBuffers& fb, cudaStream_t s);
+int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, float eps,
+              float theta, ForceBuffers& fb, cudaStream_t s);
+
+struct EpiParams {
+  float G, dt, eta;
+  int vmode;
+  double conv_tol;
+  int max_traj;
+};
+int launch_epilogue(const float4* Y0, int64_t M, const ForceBuffers& fb, float4* V,
+                    DevState* ds, double* d_partials, unsigned* d_counter, double* d_traj,
+                    const EpiParams& ep, cudaStream_t s, unsigned long long inter_add);
+int epilogue_blocks(int64_t M);
+// acc_out[perm[i]] = G * mY[i] * sum of partials (or the acceleration if mY is null).
+int launch_forces_out(const ForceBuffers& fb, int64_t M, const float4* Y0, int use_mass,
+                      float G, const int* perm, float* acc_out, cudaStream_t s);
+// Initialise DevState (identity transform, mu0 from d_mu0).
+int launch_state_init(DevState* ds, const double* d_mu0, cudaStream_t s);
+
+}  // namespace fga

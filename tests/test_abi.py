@@ -1,0 +1,64 @@
+"""The C-ABI library loads and exports what include/fga.h declares (no GPU needed)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "fga.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fga_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def fga():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2009_14005_gb300 as m
+    return m
+
+
+def test_every_declared_symbol_is_exported(fga):
+    lib = ctypes.CDLL(fga.LIB_PATH)
+    declared = _declared()
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert sorted(fga.SYMBOLS) == declared
+
+
+def test_defaults_are_the_papers(fga):
+    p = fga.params()
+    assert p.G == pytest.approx(66.7) and p.eps == pytest.approx(0.2) and p.eta == pytest.approx(0.2)
+    assert p.dt == pytest.approx(0.1) and p.theta == pytest.approx(0.6)
+    assert (p.a, p.b, p.max_depth, p.lattice) == (-5.0, 5.0, 20, 16)
+
+
+def test_host_denormalize_matches_oracle(fga, orc):
+    import synth
+    rng = np.random.default_rng(0)
+    X = rng.normal(size=(50, 3)) * 3 + 1
+    Y = rng.normal(size=(40, 3)) - 2
+    _, _, info = orc.normalize(X, Y, -5.0, 5.0)
+    R = synth.random_rotation(rng, 120)
+    t = rng.normal(size=3)
+    np.testing.assert_allclose(fga.fga_denormalize(R, t, info, -5.0),
+                               orc.denormalize(R, t, info, -5.0), rtol=1e-14, atol=1e-14)
+
+
+def test_errors_without_gpu_work(fga):
+    # argument checks happen before any device call
+    R, t = (ctypes.c_double * 9)(), (ctypes.c_double * 3)()
+    code = fga.lib.fga_register(None, 0, None, 0, None, None, ctypes.byref(fga.params()), R, t,
+                                None, None)
+    assert code == fga.FGA_EINVAL
+    assert "bad arguments" in fga.last_error()
+    code = fga.lib.fga_state_create(None, None, 0, None, None, 0, None, ctypes.byref(fga.params()),
+                                    ctypes.byref(ctypes.c_void_p()), None)
+    assert code == fga.FGA_EINVAL

@@ -1,0 +1,273 @@
+"""CUDA path vs the FP64 oracle, through the C ABI (needs a GPU).
+
+Tolerances (derived in DESIGN.md, "Parity bars"):
+* normalisation: 1e-6 absolute (one float32 rounding of values in [-5, 5]);
+* masses: 1e-6 relative (float32 output of FP64 arithmetic);
+* tree: structure bit-exact, mass / CoM to float32 rounding;
+* all-pairs force: per point |dF| <= 1e-5 * sum_j |F_ij| and field rel-L2 <= 1e-5;
+* BH force: rel-L2 vs the exact sum no worse than the oracle's BH + 1e-5;
+* registration: rotation within 0.01 deg, translation within 1e-4 bbox diagonal.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fga():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2009_14005_gb300 as m
+    return m
+
+
+def _cuda(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def _f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def _norm_pair(orc, X, Y):
+    Xn, Yn, info = orc.normalize(X, Y)
+    return _f32(Xn), _f32(Yn), info
+
+
+# --------------------------------------------------------------------------- Appendix A, Eq. 18
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_normalize_matches_oracle(fga, orc, seed):
+    X, Y, _, _ = synth.lidar_pair(seed, n=7001, m=5003)
+    Xn_o, Yn_o, info_o = orc.normalize(X, Y)
+    Xn, Yn, info = fga.fga_normalize(_cuda(X), _cuda(Y))
+    np.testing.assert_allclose(info, info_o, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(Xn.cpu().numpy(), Xn_o, atol=1e-6, rtol=0)
+    np.testing.assert_allclose(Yn.cpu().numpy(), Yn_o, atol=1e-6, rtol=0)
+
+
+def test_niv_masses_match_oracle(fga, orc):
+    X, Y, _, _ = synth.lidar_pair(2, n=20000)
+    Xn, _, _ = _norm_pair(orc, X, Y)
+    m_o = orc.masses_niv(Xn, 16, -5.0, 5.0, 1.0)
+    m = fga.fga_masses(_cuda(Xn), fga.FGA_MASS_NIV, 16, -5.0, 5.0, 1.0).cpu().numpy()
+    np.testing.assert_allclose(m, m_o, rtol=1e-6)
+    u = fga.fga_masses(_cuda(Xn), fga.FGA_MASS_UNIFORM, total=3.0).cpu().numpy()
+    np.testing.assert_allclose(u, 3.0 / len(Xn), rtol=1e-7)
+
+
+# --------------------------------------------------------------------------- Algorithm 1
+
+def _tree_cases():
+    rng = np.random.default_rng(11)
+    cases = {}
+    cases["gauss"] = (rng.normal(size=(5000, 3)) * [2, 1, 0.5], rng.uniform(0.1, 2, 5000), 20)
+    X, _, _, _ = synth.lidar_pair(3, n=30000)
+    cases["lidar"] = (X.astype(np.float64) / 10, rng.uniform(0.5, 1.5, 30000), 20)
+    dup = np.concatenate([rng.uniform(-1, 1, (300, 3)), np.tile([[0.25, -0.5, 0.125]], (9, 1))])
+    cases["dups"] = (dup, np.ones(len(dup)), 20)
+    cases["shallow"] = (rng.uniform(-1, 1, (4000, 3)), np.ones(4000), 4)
+    cases["one"] = (np.array([[0.3, 0.2, 0.1]]), np.array([2.0]), 20)
+    cases["two"] = (np.array([[0.0, 0.0, 0.0], [1.0, 1.0, 1.0]]), np.array([1.0, 3.0]), 20)
+    cases["planar"] = (np.c_[rng.uniform(-1, 1, (2000, 2)), np.zeros(2000)], np.ones(2000), 20)
+    cases["hand"] = (np.array([[0, 0, 0], [4, 4, 4], [3, 3, 3], [0.5, 0, 0]], float),
+                     np.array([1.0, 2, 3, 4]), 20)
+    return cases
+
+
+@pytest.mark.parametrize("name", list(_tree_cases().keys()))
+def test_tree_matches_oracle(fga, orc, name):
+    X, m, depth = _tree_cases()[name]
+    X = _f32(X)
+    m = _f32(m)
+    eo = orc.Tree(X, m, max_depth=depth).export()
+    t = fga.fga_tree_build(_cuda(X), _cuda(m), fga.params(max_depth=depth))
+    eg = t.export()
+    assert len(eg["depth"]) == len(eo["depth"])
+    for k in ["depth", "cell", "npts", "is_leaf", "parent", "leaf_of"]:
+        np.testing.assert_array_equal(eg[k], eo[k], err_msg=k)
+    np.testing.assert_allclose(eg["mass"], eo["mass"], rtol=2e-7)
+    scale = np.abs(X).max() + 1e-30
+    np.testing.assert_allclose(eg["com"], eo["com"], rtol=0, atol=4e-7 * scale)
+    np.testing.assert_allclose(eg["l"], eo["l"], rtol=1e-14)
+
+
+# --------------------------------------------------------------------------- Eq. 6
+
+@pytest.mark.parametrize("N,M", [(1000, 1000), (3001, 777), (257, 4099), (1, 5), (70000, 300)])
+def test_direct_forces_match_oracle(fga, orc, N, M):
+    rng = np.random.default_rng(N + M)
+    X = _f32(rng.normal(size=(N, 3)) * 2)
+    Y = _f32(rng.normal(size=(M, 3)) * 2)
+    mX = _f32(rng.uniform(0.1, 1.0, N) / N)
+    a_o, ab = orc.direct_acc(X, mX, Y, 66.7, 0.05, want_abs=True)
+    a = fga.fga_forces(None, _cuda(X), _cuda(mX), _cuda(Y), None,
+                       fga.params(G=66.7, eps=0.05)).cpu().numpy().astype(np.float64)
+    err = np.linalg.norm(a - a_o, axis=1)
+    assert np.all(err <= 1e-5 * ab + 1e-30), (err / ab).max()
+    assert np.linalg.norm(a - a_o) <= 1e-5 * np.linalg.norm(a_o)
+
+
+def test_direct_forces_with_template_masses(fga, orc):
+    rng = np.random.default_rng(5)
+    X = _f32(rng.normal(size=(500, 3)))
+    Y = _f32(rng.normal(size=(300, 3)))
+    mY = _f32(rng.uniform(0.5, 2.0, 300))
+    a_o = orc.direct_acc(X, np.full(500, 1.0 / 500), Y, 2.0, 0.1)
+    F = fga.fga_forces(None, _cuda(X), None, _cuda(Y), _cuda(mY), fga.params(G=2.0, eps=0.1))
+    np.testing.assert_allclose(F.cpu().numpy(), mY[:, None] * a_o, rtol=2e-5, atol=1e-6)
+
+
+# --------------------------------------------------------------------------- BHForce
+
+@pytest.mark.parametrize("theta", [0.0, 0.3, 0.5, 0.8])
+def test_bh_forces_match_oracle(fga, orc, theta):
+    X, Y, _, _ = synth.lidar_pair(4, n=20000, m=2000)
+    Xn, Yn, _ = _norm_pair(orc, X, Y)
+    mX = _f32(orc.masses_niv(Xn))
+    p = fga.params(theta=theta, eps=0.2)
+    tree_o = orc.Tree(Xn, mX)
+    a_bo, c_o = tree_o.bh_acc(Yn, p.G, 0.2, theta)
+    a_d = orc.direct_acc(Xn, mX, Yn, p.G, 0.2)
+    t = fga.fga_tree_build(_cuda(Xn), _cuda(mX), p)
+    a, cnt = fga.fga_forces(t, None, None, _cuda(Yn), None, p, want_count=True)
+    a = a.cpu().numpy().astype(np.float64)
+    err_gpu = np.linalg.norm(a - a_d) / np.linalg.norm(a_d)
+    err_orc = np.linalg.norm(a_bo - a_d) / np.linalg.norm(a_d)
+    assert err_gpu <= err_orc + 1e-5, (err_gpu, err_orc)
+    # same walk as the per-point BHForce: term counts agree up to rare
+    # opening-criterion ties decided differently in FP32 and FP64
+    assert abs(cnt - c_o.sum()) <= 1e-3 * c_o.sum()
+    close = np.linalg.norm(a - a_bo, axis=1) <= 1e-4 * np.linalg.norm(a_bo, axis=1) + 1e-6
+    assert close.mean() > 0.99
+    if theta == 0.0:
+        assert cnt == len(Xn) * len(Yn)
+
+
+# --------------------------------------------------------------------------- Algorithm 2
+
+def _gt_errors(R, t, R_ref, t_ref, X):
+    diag = np.linalg.norm(X.max(0) - X.min(0))
+    import oracle
+    return oracle.rotation_error_deg(R, R_ref), np.linalg.norm(np.asarray(t) - t_ref) / diag
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_register_direct_sphere_matches_oracle(fga, orc, seed):
+    # 1k x 1k sphere pair, eps = 0.05, eta = 0.1, 100 iterations, all pairs
+    X, Y, _, _ = synth.sphere_pair(seed)
+    po = orc.Params(eps=0.05, eta=0.1, max_iter=100, method=orc.FGA_DIRECT)
+    o = orc.register_full(X, Y, po)
+    p = fga.params(eps=0.05, eta=0.1, max_iter=100, method=fga.FGA_DIRECT)
+    R, t, st = fga.fga_register(_cuda(X), _cuda(Y), p)
+    dphi, dt = _gt_errors(R, t, o["R"], o["t"], X)
+    assert dphi <= 0.01 and dt <= 1e-4, (dphi, dt)
+    assert st["iterations"] == 100
+    assert st["interactions"] == 100 * 1000 * 1000
+
+
+@pytest.mark.parametrize("vm", [0, 1])
+def test_register_box_recovers_ground_truth_and_matches(fga, orc, vm):
+    X, Y, R_gt, t_gt = synth.box_pair(0, 500, 15.0)
+    po = orc.Params(max_iter=150, velocity_mode=vm, method=orc.FGA_DIRECT)
+    o = orc.register_full(X, Y, po)
+    p = fga.params(max_iter=150, velocity_mode=vm, method=fga.FGA_DIRECT)
+    R, t, st = fga.fga_register(X, Y, p)  # host inputs
+    dphi, dt = _gt_errors(R, t, o["R"], o["t"], X)
+    assert dphi <= 0.01 and dt <= 1e-4
+    gphi, gt = _gt_errors(R, t, R_gt, t_gt, X)
+    assert gphi < 0.01 and gt < 1e-4
+
+
+def test_register_bh_lidar_matches_oracle(fga, orc):
+    X, Y, _, _ = synth.lidar_pair(5, n=6000)
+    po = orc.Params(method=orc.FGA_BH, theta=0.5, max_iter=200, niv_masses=True)
+    o = orc.register_full(X, Y, po)
+    p = fga.params(method=fga.FGA_BH, theta=0.5, max_iter=200, mass_mode=fga.FGA_MASS_NIV)
+    R, t, st = fga.fga_register(_cuda(X), _cuda(Y), p)
+    dphi, dt = _gt_errors(R, t, o["R"], o["t"], X)
+    assert dphi <= 0.01 and dt <= 1e-4, (dphi, dt)
+    assert abs(st["interactions"] - o["interactions"]) <= 1e-3 * o["interactions"]
+
+
+def test_trajectory_and_chunked_steps(fga, orc):
+    X, Y, _, _ = synth.box_pair(1, 400, 20.0)
+    Xn, Yn, _ = _norm_pair(orc, X, Y)
+    mX = _f32(np.full(len(Xn), 1.0 / len(Xn)))
+    mY = _f32(np.full(len(Yn), 0.1))
+    po = orc.Params(max_iter=30)
+    o = orc.register(Xn, mX, Yn, mY, po, want_traj=True)
+    p = fga.params(max_iter=30, method=fga.FGA_DIRECT)
+    s = fga.fga_state_create(_cuda(Xn), _cuda(mX), _cuda(Yn), _cuda(mY), p)
+    s.step(7)
+    s.step(23)
+    tr = s.trajectory(30)
+    assert tr.shape == (30, 12)
+    import oracle
+    for k in range(30):
+        assert oracle.rotation_error_deg(tr[k, :9].reshape(3, 3), o["traj"][k, :9].reshape(3, 3)) < 1e-3
+        np.testing.assert_allclose(tr[k, 9:], o["traj"][k, 9:], atol=1e-5)
+
+
+def test_convergence_stop_matches_oracle(fga, orc):
+    X, Y, _, _ = synth.box_pair(5, 400, 10.0)
+    o = orc.register_full(X, Y, orc.Params(max_iter=300, conv_tol=1e-6))
+    R, t, st = fga.fga_register(_cuda(X), _cuda(Y),
+                                fga.params(max_iter=300, conv_tol=1e-6, method=fga.FGA_DIRECT))
+    assert st["converged"]
+    assert abs(st["iterations"] - o["iters"]) <= 1
+
+
+def test_host_and_device_inputs_agree_and_runs_are_deterministic(fga):
+    X, Y, _, _ = synth.lidar_pair(6, n=5000)
+    p = fga.params(method=fga.FGA_BH, theta=0.5, max_iter=20)
+    R1, t1, _ = fga.fga_register(X, Y, p)
+    R2, t2, _ = fga.fga_register(_cuda(X), _cuda(Y), p)
+    R3, t3, _ = fga.fga_register(_cuda(X), _cuda(Y), p)
+    assert np.array_equal(R1, R2) and np.array_equal(t1, t2)
+    assert np.array_equal(R2, R3) and np.array_equal(t2, t3)
+
+
+# --------------------------------------------------------------------------- edge cases
+
+def test_invalid_inputs_are_rejected(fga):
+    X = np.random.default_rng(0).normal(size=(10, 3)).astype(np.float32)
+    Xbad = X.copy()
+    Xbad[3, 1] = np.nan
+    with pytest.raises(fga.FGAError) as e:
+        fga.fga_register(_cuda(Xbad), _cuda(X), fga.params())
+    assert e.value.code == fga.FGA_EINVAL
+    with pytest.raises(fga.FGAError):
+        fga.fga_register(_cuda(X), _cuda(X), fga.params(eps=0.0))
+    with pytest.raises(fga.FGAError):
+        fga.fga_register(_cuda(X), _cuda(X), fga.params(max_depth=21))
+    with pytest.raises(fga.FGAError):
+        fga.fga_tree_build(_cuda(Xbad), None, fga.params())
+    with pytest.raises(fga.FGAError):
+        fga.fga_register(_cuda(X), _cuda(X), fga.params(), mX=-np.ones(10, np.float32))
+    same = np.ones((5, 3), np.float32)
+    with pytest.raises(fga.FGAError):
+        fga.fga_register(_cuda(same), _cuda(same), fga.params())
+
+
+def test_single_template_point_is_degenerate(fga):
+    X = np.random.default_rng(1).normal(size=(50, 3)).astype(np.float32)
+    R, t, st = fga.fga_register(_cuda(X), _cuda(X[:1]), fga.params(max_iter=3, method=fga.FGA_DIRECT))
+    assert st["status"] == fga.FGA_EDEGENERATE
+    np.testing.assert_allclose(R, np.eye(3))
+
+
+def test_aligned_identical_sets_stay_put(fga):
+    X = np.random.default_rng(2).uniform(-1, 1, size=(300, 3)).astype(np.float32) * [1, 0.6, 0.3]
+    X = X.astype(np.float32)
+    for method in [fga.FGA_DIRECT, fga.FGA_BH]:
+        R, t, st = fga.fga_register(_cuda(X), _cuda(X), fga.params(max_iter=40, method=method))
+        np.testing.assert_allclose(R, np.eye(3), atol=1e-5)
+        np.testing.assert_allclose(t, 0, atol=1e-5)
