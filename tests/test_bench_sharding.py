@@ -1,0 +1,47 @@
+"""Multi-rank logic of bench.py on CPU (gloo, world size 2): disjoint work per
+rank, max-over-ranks time and sum-over-ranks units."""
+import os
+import socket
+
+import pytest
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    seeds = bench.shard_seeds(rank, world, 3)
+    t, u = bench.reduce_max_sum(10.0 * (rank + 1), 100.0 + rank, world)
+    bench.barrier(world)
+    q.put((rank, seeds, t, u))
+    dist.destroy_process_group()
+
+
+def test_two_rank_sharding_and_reduction():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in range(2)]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    out.sort()
+    s0, s1 = set(out[0][1]), set(out[1][1])
+    assert s0.isdisjoint(s1) and len(s0) == len(s1) == 3
+    for _, _, t, u in out:
+        assert t == pytest.approx(20.0)
+        assert u == pytest.approx(201.0)
