@@ -179,6 +179,35 @@ int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N,
                const float* mY, int64_t M, const fga_params* p, float* acc_out,
                int64_t* interactions_out, void* stream);
 
+/* ----------------------------------------------------------------- no allocation */
+/* Size, in float4 (16 bytes), of the device array that fga_forces_direct_static
+ * uses for all its intermediate buffers: 524288 float4 = 8 MiB. */
+#define FGA_STATIC_SCRATCH_FLOAT4 524288
+
+/* The all-pairs forces of fga_forces(tree = NULL, ...) without any device
+ * allocation. The paper has no counterpart: this entry point exists for
+ * callers that must not call cudaMalloc / cudaFree, for example a loop with a
+ * hard latency budget (the allocator can block and synchronise the device) or
+ * a plug-in whose host application owns all device memory through its own
+ * pool. Inputs, outputs and their meaning are those of fga_forces with
+ * tree = NULL (X: device N x 3, mX: device N or NULL for 1/N each, Y: device
+ * M x 3, mY: device M or NULL for unit masses, acc_out: device M x 3).
+ * Packed inputs, per-split partial sums and the kernel's state block live in
+ * one array of FGA_STATIC_SCRATCH_FLOAT4 float4 compiled into the library; it
+ * occupies every device that loads the library until the process exits.
+ * Limit: 32 + N + M + 2 M <= FGA_STATIC_SCRATCH_FLOAT4 (one source split; the
+ * call uses more splits when they fit); larger inputs are rejected with
+ * FGA_EINVAL and a message, before any GPU work. The first call on each device
+ * looks up the array's address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture. Every call shares
+ * the array and overwrites what it reads before reading it, so leftovers of an
+ * earlier call do not matter; calls that overlap on the GPU (unordered streams
+ * or concurrent host threads) race on the array and must be serialised by the
+ * caller. No host synchronisation. */
+int fga_forces_direct_static(const float* X, const float* mX, int64_t N, const float* Y,
+                             const float* mY, int64_t M, const fga_params* p, float* acc_out,
+                             void* stream);
+
 /* ----------------------------------------------------------------- Algorithm 2 */
 typedef struct fga_state fga_state;
 

@@ -3,7 +3,7 @@
 Argument marshalling only: every step runs in the CUDA kernels of
 ``libfga.so`` (see ``include/fga.h`` for the C ABI). PyTorch provides device
 memory and streams. Importing this package fails loudly if ``libfga.so`` has
-not been built (``python -m paper_2009_14005_gb300.build``); there is no CPU
+not been built (``python paper_2009_14005_gb300/build.py``); there is no CPU
 fallback.
 
 The functions keep the C names:
@@ -48,7 +48,9 @@ SYMBOLS = [
     "fga_denormalize", "fga_masses", "fga_tree_build", "fga_tree_destroy",
     "fga_tree_node_count", "fga_tree_export", "fga_forces", "fga_state_create", "fga_step",
     "fga_state_get", "fga_state_trajectory", "fga_state_destroy", "fga_register",
+    "fga_forces_direct_static",
 ]
+FGA_STATIC_SCRATCH_FLOAT4 = 524288
 
 
 class fga_params(ctypes.Structure):
@@ -90,7 +92,7 @@ class FGAError(RuntimeError):
 
 def _load():
     if not os.path.exists(LIB_PATH):
-        raise ImportError("libfga.so is not built; run `python -m paper_2009_14005_gb300.build` "
+        raise ImportError("libfga.so is not built; run `python paper_2009_14005_gb300/build.py` "
                           "(there is no CPU fallback)")
     lib = ctypes.CDLL(LIB_PATH)
     P, I64, VP, F, D = ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_float, ctypes.c_double
@@ -116,6 +118,7 @@ def _load():
         "fga_state_destroy": (None, [P]),
         "fga_register": (ctypes.c_int, [P, I64, P, I64, P, P, PP, DP, DP,
                                         ctypes.POINTER(fga_stats), VP]),
+        "fga_forces_direct_static": (ctypes.c_int, [P, P, I64, P, P, I64, PP, P, VP]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -292,6 +295,23 @@ def fga_forces(tree, X, mX, Y, mY=None, p: fga_params | None = None, want_count:
                         _ptr(mY), Y.shape[0], ctypes.byref(p), _ptr(out),
                         ctypes.byref(cnt) if want_count else None, _stream(stream)))
     return (out, int(cnt.value)) if want_count else out
+
+
+def fga_forces_direct_static(X, mX, Y, mY=None, p: fga_params | None = None, out=None,
+                             stream=None):
+    """All-pairs forces like ``fga_forces(None, ...)`` but without any device
+    allocation inside the library (for callers that must not allocate): the
+    intermediates live in a fixed 8 MiB device array; pass ``out`` to avoid the
+    one allocation this wrapper would otherwise make for the result."""
+    torch = _torch()
+    p = p or params()
+    X, Y = _dev(X, 3, "X"), _dev(Y, 3, "Y")
+    mX = _dev(mX) if mX is not None else None
+    mY = _dev(mY) if mY is not None else None
+    out = torch.empty_like(Y) if out is None else out
+    _err(lib.fga_forces_direct_static(_ptr(X), _ptr(mX), X.shape[0], _ptr(Y), _ptr(mY), Y.shape[0],
+                                      ctypes.byref(p), _ptr(out), _stream(stream)))
+    return out
 
 
 # --------------------------------------------------------------------------- Algorithm 2

@@ -2,7 +2,8 @@
 
 Each .cu file is compiled to an object in parallel, then linked into
 ``paper_2009_14005_gb300/libfga.so``. Objects live in ``_build/`` beside this
-file. ``python -m paper_2009_14005_gb300.build`` rebuilds.
+file. ``python paper_2009_14005_gb300/build.py`` rebuilds (a path, so the package and
+its library are not imported first).
 """
 from __future__ import annotations
 
