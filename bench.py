@@ -52,9 +52,10 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=120_000, help="points per sweep")
-    ap.add_argument("--iters", type=int, default=200)
-    ap.add_argument("--theta", type=float, default=0.5)
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lidar-bh")
+    ap.add_argument("--n", type=int, default=None, help="points per cloud (workload default)")
+    ap.add_argument("--iters", type=int, default=None, help="iterations (workload default)")
+    ap.add_argument("--theta", type=float, default=None, help="BH opening parameter")
     ap.add_argument("--pairs", type=int, default=2, help="distinct seeded pairs per rank")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -175,25 +176,78 @@ def recorded_traffic(kernel_file: str, summary: str):
 
 # --------------------------------------------------------------------------- workload
 
+WORKLOADS = {
+    # the headline configuration: LiDAR-like sweeps, Barnes-Hut
+    # (G = 1 from the paper's parameter range: with 66.7 the trajectory on this
+    # cloud is chaotic, so no FP32 run can track the FP64 one)
+    "lidar-bh": dict(gen="lidar", n=120_000, iters=200, method="bh", theta=0.5, niv=True,
+                     G=1.0, eps=0.2, eta=0.2),
+    # 1k x 1k points on the unit sphere, all-pairs sum
+    "sphere-direct": dict(gen="sphere", n=1000, iters=100, method="direct", theta=0.5, niv=False,
+                          G=66.7, eps=0.05, eta=0.1),
+    # large piecewise-planar scenes, all-pairs sum (a few iterations per step)
+    "planar-direct": dict(gen="planar", n=262_144, iters=5, method="direct", theta=0.5, niv=False,
+                          G=66.7, eps=0.2, eta=0.2),
+    # large piecewise-planar scenes, Barnes-Hut
+    "planar-bh": dict(gen="planar", n=1_000_000, iters=100, method="bh", theta=0.5, niv=False,
+                      G=66.7, eps=0.2, eta=0.2),
+}
+
+
+def workload(a):
+    w = dict(WORKLOADS[a.workload])
+    for k in ("n", "iters", "theta"):
+        v = getattr(a, k)
+        if v is not None:
+            w[k] = v
+    return w
+
+
 def workload_config(a):
-    return {"workload": "lidar-sweeps-%dk-bh-theta%.1f-%dit" % (a.n // 1000, a.theta, a.iters),
-            "N": a.n, "M": a.n, "iterations": a.iters, "method": "barnes-hut", "theta": a.theta,
-            "masses": "NIV lattice 16 (reference), uniform (template)", "eps": 0.2, "eta": 0.2,
-            "dt": 0.1, "G": 66.7, "pairs_per_rank": a.pairs,
+    w = workload(a)
+    name = "%s-%dk-%s%s-%dit" % (
+        {"lidar": "lidar-sweeps", "sphere": "unit-sphere", "planar": "planar-scene"}[w["gen"]],
+        max(w["n"] // 1000, 1), "bh-theta%.1f" % w["theta"] if w["method"] == "bh" else "direct",
+        "", w["iters"])
+    return {"workload": name, "N": w["n"], "M": w["n"], "iterations": w["iters"],
+            "method": "barnes-hut" if w["method"] == "bh" else "all-pairs",
+            "theta": w["theta"] if w["method"] == "bh" else None,
+            "masses": ("NIV lattice 16 (reference), uniform (template)" if w["niv"] else "uniform"),
+            "eps": w["eps"], "eta": w["eta"], "dt": 0.1, "G": w["G"], "pairs_per_rank": a.pairs,
             "l2": "flushed between steps (256 MB device write outside the timed events)",
             "inputs": "resident in HBM at the start of each timed step"}
 
 
-def make_pairs(seeds, n):
-    return [synth.lidar_pair(s, n=n) for s in seeds]
+def make_pairs(seeds, a):
+    w = workload(a)
+    gen = {"lidar": synth.lidar_pair, "sphere": synth.sphere_pair,
+           "planar": synth.planar_scene_pair}[w["gen"]]
+    return [gen(s, n=w["n"]) for s in seeds]
+
+
+def lib_params(fga, a):
+    w = workload(a)
+    return fga.params(method=fga.FGA_BH if w["method"] == "bh" else fga.FGA_DIRECT,
+                      theta=w["theta"], max_iter=w["iters"], G=w["G"], eps=w["eps"], eta=w["eta"],
+                      mass_mode=fga.FGA_MASS_NIV if w["niv"] else fga.FGA_MASS_UNIFORM, profile=1)
 
 
 def cpu_sample(pair, a, iters):
-    """The FP64 oracle on one full pair for `iters` iterations (bounded sample)."""
+    """The FP64 oracle on one pair for `iters` iterations (bounded sample).
+
+    For the all-pairs workloads whose sample would exceed ~2e10 terms, the
+    template is cut to its first points (the time per term does not depend on
+    which points)."""
     import oracle
     oracle.build()
+    w = workload(a)
     X, Y, _, _ = pair
-    p = oracle.Params(method=oracle.FGA_BH, theta=a.theta, max_iter=iters, niv_masses=True)
+    if w["method"] == "direct":
+        keep = int(max(1, min(len(Y), 2e10 / (len(X) * iters))))
+        Y = Y[:keep]
+    p = oracle.Params(method=oracle.FGA_BH if w["method"] == "bh" else oracle.FGA_DIRECT,
+                      theta=w["theta"], max_iter=iters, niv_masses=w["niv"], G=w["G"], eps=w["eps"],
+                      eta=w["eta"])
     t0 = time.perf_counter()
     o = oracle.register_full(X, Y, p)
     dt = time.perf_counter() - t0
@@ -204,7 +258,7 @@ def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    pair = make_pairs(shard_seeds(0, 1, 1), a.n)[0]
+    pair = make_pairs(shard_seeds(0, 1, 1), a)[0]
     for _ in range(a.warmup):
         cpu_sample(pair, a, 1)
     total_i, total_t, cores = 0, 0.0, 1
@@ -214,7 +268,8 @@ def run_reference(a):
         total_t += t
     value = total_i / total_t
     sample = ("FP64 C oracle, Algorithm 2 with BHForce: normalisation, NIV masses, tree and ONE "
-              "iteration of the loop on the full %d x %d pair per step" % (a.n, a.n))
+              "iteration of the loop on the full %d x %d pair per step" % (workload(a)["n"],
+                                                                           workload(a)["n"]))
     line = {"impl": "reference", "metric": "pair-interactions/s", "value": value,
             "unit": "interactions/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * total_t / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -238,11 +293,10 @@ def run_ours(a):
     __graft_entry__.build_library()
     import paper_2009_14005_gb300 as fga
 
-    pairs = make_pairs(shard_seeds(rank, world, a.pairs), a.n)
+    pairs = make_pairs(shard_seeds(rank, world, a.pairs), a)
     dev = [(torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda")) for X, Y, _, _ in pairs]
     host = [(torch.from_numpy(X).pin_memory(), torch.from_numpy(Y).pin_memory()) for X, Y, _, _ in pairs]
-    p = fga.params(method=fga.FGA_BH, theta=a.theta, max_iter=a.iters, mass_mode=fga.FGA_MASS_NIV,
-                   profile=1)
+    p = lib_params(fga, a)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
 
@@ -300,10 +354,11 @@ def run_ours(a):
     launch_inter = inter / max(force_launches, 1)
     launch_s = force_ms / 1e3 / max(force_launches, 1)
     achieved = launch_inter / launch_s if launch_s > 0 else 0.0
-    roof = {"bound": "alu", "kernel": "k_bh", "achieved": achieved / 1e9, "peak": peak_rate / 1e9,
+    kname = "k_bh" if workload(a)["method"] == "bh" else "k_direct"
+    roof = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e9, "peak": peak_rate / 1e9,
             "unit": "Ginteractions/s", "frac": achieved / peak_rate,
             "traffic": recorded_traffic("paper_2009_14005_gb300/csrc/fga_force.cu",
-                                        "k_bh_lidar120k.md"),
+                                        "%s_%s.md" % (kname, a.workload)),
             "peak_source": "%d SMs x %d FP32 lanes x %.0f MHz (sm_max_mhz, %s) / %d FP32 "
                            "instructions per interaction" % (sms, FP32_LANES_PER_SM, sm_mhz, peak_src,
                                                              FP32_INSTR_PER_INTERACTION),
@@ -315,7 +370,8 @@ def run_ours(a):
             "data": "synthetic", "config": workload_config(a),
             "registrations_per_s": a.steps * world / (t_max / 1e3),
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
-            "e2e": {"value": e2e_iall / (e2e_tmax / 1e3), "unit": "interactions/s",
+            "e2e": {"value": e2e_iall / (e2e_tmax / 1e3) if e2e_tmax > 0 else None,
+                    "unit": "interactions/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_tmax / max(a.e2e_steps, 1)},
             "gpu_launches": launches, "roofline": roof, "clocks": clk}
@@ -325,7 +381,8 @@ def run_ours(a):
                                 "kind": "oracle",
                                 "sample": "FP64 C oracle (OpenMP), normalisation + NIV masses + tree + "
                                           "%d of %d iterations on the first %dk x %dk pair (%.1f s)"
-                                          % (a.cpu_iters, a.iters, a.n // 1000, a.n // 1000, t)}
+                                          % (a.cpu_iters, workload(a)["iters"], workload(a)["n"] // 1000,
+                                             workload(a)["n"] // 1000, t)}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -348,7 +348,7 @@ int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N,
   if (tree) {
     if (sc.alloc(&perm, M)) return FGA_ENOMEM;
     rc = pack_template(Y, mY, 1.0f, M, true, Y0, perm, s);
-    fb.S = 1;
+    fb.S = tree->n_front;
   } else {
     if (sc.alloc(&X4, N)) return FGA_ENOMEM;
     rc = pack_template(Y, mY, 1.0f, M, false, Y0, nullptr, s);
@@ -406,7 +406,7 @@ static int state_create_checked(const float* Xn, const float* mX, int64_t N, con
       if ((rc = tree_build(Xn, mX, N, p->max_depth, &st->own_tree, s))) return fail(rc);
       st->tree = st->own_tree;
     }
-    st->fb.S = 1;
+    st->fb.S = st->tree->n_front;
   } else {
     if (dev_alloc_n(&st->X4, N, s)) return fail(FGA_ENOMEM);
     k_pack4<<<grid_for(N), 256, 0, s>>>(Xn, mX, (float)(1.0 / (double)N), N, st->X4);

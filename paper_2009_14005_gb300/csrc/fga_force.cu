@@ -159,133 +159,186 @@ int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const
 
 // ------------------------------------------------------------------ BHForce, Eq. 15
 //
-// A warp owns 32 consecutive template points (Morton-sorted, so they are close
-// in space) and walks the union of the cells they need with one shared stack.
-// Each stack entry carries a copy of the cell (CoM + mass, l^2, children) and
-// the mask of lanes that reached it without accepting an ancestor. At a popped
-// cell each of those lanes applies the paper's criterion l / |y - CoM| < theta
-// as l^2 < theta^2 |y - CoM|^2: accepting lanes add the cell as one particle
-// (Eq. 6 with the cell mass at its CoM); lanes that reject it continue into the
-// children (pushed with the rejecting lanes' mask) or, at a leaf, add each of
-// its particles. So every lane evaluates exactly the per-point BHForce of
-// Algorithm 2; the warp only shares the walk. Leaves holding one particle are
-// the particle itself, so they are always evaluated as such.
+// Every lane walks the tree for its own template point exactly as BHForce of
+// Algorithm 2 does, depth first with children in octant order:
+//   * a cell with l / |y - CoM| < theta (written l^2 < theta^2 |y - CoM|^2),
+//     or a leaf holding one particle, is added as one particle (Eq. 6 with the
+//     cell mass at its CoM);
+//   * otherwise an internal cell's children are visited next, and a leaf
+//     holding several particles adds each of them exactly.
+// The pending work of a lane is one range of unvisited siblings per level,
+// packed as (first cell << 4 | count) into one word; the current range lives
+// in registers and the rest in a per-lane column of shared memory (at most
+// one entry per tree level). A cell record is 32 bytes (CoM + mass, then l^2,
+// first child / body, child count, depth), fetched with two loads from the
+// same sector. Warps hold 32 Morton-neighbouring points, so their walks touch
+// mostly the same cells and the loads are served by L1.
+//
+// Work is split into tasks (32-point group, frontier cell): a task first
+// judges the frontier cell's ancestors (a lane accepting one stops; the
+// monopole is added by the task owning the ancestor's first frontier cell),
+// then walks the frontier cell's subtree. Tasks are handed out dynamically
+// from a counter in DevState; the last warp to finish resets it.
 static constexpr int BH_WARPS = 4;
-static constexpr int BH_STACK = 192;  // >= 7 * depth + 8 for depth <= 20
+static constexpr int BH_DEPTH = 24;  // > 21 tree levels: one pending range per level
 
-__global__ void __launch_bounds__(BH_WARPS * 32) k_bh(const float4* __restrict__ ncm,
-                                                      const int4* __restrict__ ninfo,
-                                                      const float4* __restrict__ bodies,
-                                                      const float4* __restrict__ Y0, int64_t M,
-                                                      DevState* __restrict__ ds, float eps2,
-                                                      float theta2, float4* __restrict__ hi_out,
-                                                      float4* __restrict__ lo_out) {
+__global__ void __launch_bounds__(BH_WARPS * 32, 8) k_bh(const float4* __restrict__ rec,
+                                                         const float4* __restrict__ bodies,
+                                                         const float4* __restrict__ Y0, int64_t M,
+                                                         const FrontCell* __restrict__ front, int K,
+                                                         DevState* __restrict__ ds, float eps2,
+                                                         float theta2, float4* __restrict__ hi_out,
+                                                         float4* __restrict__ lo_out) {
   if (ds->done) return;
-  __shared__ float4 s_cm[BH_WARPS][BH_STACK];
-  __shared__ int4 s_in[BH_WARPS][BH_STACK];
-  __shared__ unsigned s_mask[BH_WARPS][BH_STACK];
+  __shared__ unsigned s_stack[BH_WARPS][BH_DEPTH][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t i = ((int64_t)blockIdx.x * BH_WARPS + w) * 32 + lane;
-  const bool valid = i < M;
-  const unsigned live = __ballot_sync(FULL, valid);
-  if (live == 0) return;
+  unsigned* const stk = &s_stack[w][0][lane];
   const Xf xf = load_xf(ds);
-  const float3 y = place(xf, Y0[valid ? i : 0]);
-  float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-  float px = 0.f, py = 0.f, pz = 0.f;
-  unsigned count = 0;
-  if (lane == 0) {
-    s_cm[w][0] = ncm[0];
-    s_in[w][0] = ninfo[0];
-    s_mask[w][0] = live;
-  }
-  __syncwarp();
-  int sp = 1, since_flush = 0;
+  const unsigned ntasks = (unsigned)((M + 31) / 32) * (unsigned)K;
+  unsigned long long total = 0;
   bool overflow = false;
-  while (sp > 0) {
-    --sp;
-    const float4 cm = s_cm[w][sp];
-    const int4 in = s_in[w][sp];
-    const unsigned mask = s_mask[w][sp];
-    __syncwarp();
-    const bool act = (mask >> lane) & 1u;
-    const float dx = cm.x - y.x, dy = cm.y - y.y, dz = cm.z - y.z;
-    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-    const bool accept = act && (in.z == -1 || __int_as_float(in.x) < theta2 * d2);
+  for (;;) {
+    unsigned task = 0;
+    if (lane == 0) task = atomicAdd(&ds->bh_next, 1u);
+    task = __shfl_sync(FULL, task, 0);
+    if (task >= ntasks) break;
+    const unsigned g = task / (unsigned)K, f = task % (unsigned)K;
+    const int64_t i = (int64_t)g * 32 + lane;
+    const bool valid = i < M;
+    const float3 y = place(xf, Y0[valid ? i : 0]);
+    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+    float px = 0.f, py = 0.f, pz = 0.f;
+    unsigned count = 0;
+    bool live = valid;
     {
-      const float inv = rsqrtf(d2 + eps2);
-      const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
-      px = fmaf(wgt, dx, px);
-      py = fmaf(wgt, dy, py);
-      pz = fmaf(wgt, dz, pz);
-      count += accept;
-    }
-    const unsigned rej = __ballot_sync(FULL, act && !accept);
-    if (rej) {
-      if (in.z > 0) {
-        if (sp + in.z > BH_STACK) {
-          overflow = true;
-          break;
+      const int npath = front[f].npath;
+      const unsigned first_mask = front[f].first_mask;
+      for (int j = 0; j < npath; ++j) {
+        const int a = front[f].path[j];
+        const float4 cm = rec[2 * a];
+        const float l2 = rec[2 * a + 1].x;
+        const float dx = cm.x - y.x, dy = cm.y - y.y, dz = cm.z - y.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const bool accept = live && l2 < theta2 * d2;
+        if ((first_mask >> j) & 1u) {
+          const float inv = rsqrtf(d2 + eps2);
+          const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
+          px = fmaf(wgt, dx, px);
+          py = fmaf(wgt, dy, py);
+          pz = fmaf(wgt, dz, pz);
+          count += accept;
         }
-        if (lane < in.z) {
-          s_cm[w][sp + lane] = ncm[in.y + lane];
-          s_in[w][sp + lane] = ninfo[in.y + lane];
-          s_mask[w][sp + lane] = rej;
-        }
-        sp += in.z;
-        __syncwarp();
-      } else {
-        // leaf holding several particles (a depth-limit cell): the rejecting
-        // lanes add each particle exactly
-        const bool me = (rej >> lane) & 1u;
-        const int nb = -in.z;
-        for (int b = 0; b < nb; ++b) {
-          const float4 q = bodies[in.y + b];
-          const float ex = q.x - y.x, ey = q.y - y.y, ez = q.z - y.z;
-          const float inv = rsqrtf(fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, eps2))));
-          const float wgt = me ? q.w * (inv * inv * inv) : 0.f;
-          px = fmaf(wgt, ex, px);
-          py = fmaf(wgt, ey, py);
-          pz = fmaf(wgt, ez, pz);
-          if (++since_flush == 32) {
-            comp_add(hx, lx, px);
-            comp_add(hy, ly, py);
-            comp_add(hz, lz, pz);
-            px = py = pz = 0.f;
-            since_flush = 0;
-          }
-        }
-        count += me ? nb : 0;
+        live = live && !accept;
       }
     }
-    if (++since_flush >= 32) {
-      comp_add(hx, lx, px);
-      comp_add(hy, ly, py);
-      comp_add(hz, lz, pz);
-      px = py = pz = 0.f;
-      since_flush = 0;
+    // per-lane walk of the frontier cell's subtree
+    int cur = front[f].node;  // next cell of the current sibling range
+    int cnt = live ? 1 : 0;   // cells left in the current range
+    int sp = 0;               // saved ranges in shared memory
+    int since_flush = 0;
+    while (__any_sync(FULL, cnt > 0)) {
+      if (cnt > 0) {
+        const int v = cur;
+        ++cur;
+        --cnt;
+        const float4 cm = rec[2 * v];
+        const float4 ri = rec[2 * v + 1];
+        const int nchild = __float_as_int(ri.z);
+        const float dx = cm.x - y.x, dy = cm.y - y.y, dz = cm.z - y.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const bool accept = nchild == -1 || ri.x < theta2 * d2;
+        const float inv = rsqrtf(d2 + eps2);
+        const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
+        px = fmaf(wgt, dx, px);
+        py = fmaf(wgt, dy, py);
+        pz = fmaf(wgt, dz, pz);
+        count += accept;
+        if (!accept) {
+          if (nchild > 0) {
+            // descend: save the rest of this range, continue with the children
+            if (cnt > 0) {
+              if (sp < BH_DEPTH) stk[32 * sp] = ((unsigned)cur << 4) | (unsigned)cnt;
+              else overflow = true;
+              ++sp;
+            }
+            cur = __float_as_int(ri.y);
+            cnt = nchild;
+          } else {
+            // leaf holding several particles: add each exactly
+            const int b0 = __float_as_int(ri.y), nb = -nchild;
+            for (int b = 0; b < nb; ++b) {
+              const float4 q = bodies[b0 + b];
+              const float ex = q.x - y.x, ey = q.y - y.y, ez = q.z - y.z;
+              const float iq = rsqrtf(fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, eps2))));
+              const float wq = q.w * (iq * iq * iq);
+              px = fmaf(wq, ex, px);
+              py = fmaf(wq, ey, py);
+              pz = fmaf(wq, ez, pz);
+            }
+            count += (unsigned)nb;
+          }
+        }
+        if (cnt == 0 && sp > 0) {
+          --sp;
+          const unsigned e = sp < BH_DEPTH ? stk[32 * sp] : 0u;
+          cur = (int)(e >> 4);
+          cnt = (int)(e & 15u);
+        }
+      }
+      if (++since_flush == 32) {
+        comp_add(hx, lx, px);
+        comp_add(hy, ly, py);
+        comp_add(hz, lz, pz);
+        px = py = pz = 0.f;
+        since_flush = 0;
+      }
+    }
+    comp_add(hx, lx, px);
+    comp_add(hy, ly, py);
+    comp_add(hz, lz, pz);
+    if (valid) {
+      hi_out[(int64_t)f * M + i] = make_float4(hx, hy, hz, 0.f);
+      lo_out[(int64_t)f * M + i] = make_float4(lx, ly, lz, 0.f);
+    }
+    total += valid ? count : 0u;
+  }
+  if (__any_sync(FULL, overflow) && lane == 0) atomicOr(&ds->status, 1);
+  for (int off = 16; off > 0; off >>= 1) total += __shfl_down_sync(FULL, total, off);
+  if (lane == 0) {
+    if (total) atomicAdd(&ds->interactions, total);
+    // the last warp out resets the task counter for the next launch
+    __threadfence();
+    const unsigned out = atomicAdd(&ds->bh_exited, 1u);
+    if (out == gridDim.x * BH_WARPS - 1) {
+      ds->bh_next = 0u;
+      ds->bh_exited = 0u;
+      __threadfence();
     }
   }
-  comp_add(hx, lx, px);
-  comp_add(hy, ly, py);
-  comp_add(hz, lz, pz);
-  if (overflow && lane == 0) atomicOr(&ds->status, 1);
-  if (valid) {
-    hi_out[i] = make_float4(hx, hy, hz, 0.f);
-    lo_out[i] = make_float4(lx, ly, lz, 0.f);
+}
+
+static int bh_grid(int64_t M, int K) {
+  static int per_sm = 0;
+  if (per_sm == 0) {
+    int b = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bh, BH_WARPS * 32, 0) != cudaSuccess || b < 1) {
+      cudaGetLastError();
+      b = 1;
+    }
+    per_sm = b;
   }
-  unsigned long long c = valid ? count : 0u;
-  for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(FULL, c, off);
-  if (lane == 0 && c) atomicAdd(&ds->interactions, c);
+  const int64_t tasks = (M + 31) / 32 * K;
+  const int64_t need = (tasks + BH_WARPS - 1) / BH_WARPS;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)per_sm * sm_count()));
 }
 
 int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, float eps,
               float theta, ForceBuffers& fb, cudaStream_t s) {
-  const int64_t blocks = (M + BH_WARPS * 32 - 1) / (BH_WARPS * 32);
-  k_bh<<<(unsigned)blocks, BH_WARPS * 32, 0, s>>>(t->node_cm, t->node_info, t->bodies, Y0, M, ds,
-                                                  eps * eps, theta * theta, fb.hi, fb.lo);
+  k_bh<<<bh_grid(M, t->n_front), BH_WARPS * 32, 0, s>>>(t->node_rec, t->bodies, Y0, M, t->front,
+                                                        t->n_front, ds, eps * eps, theta * theta,
+                                                        fb.hi, fb.lo);
   FGA_LAUNCH_CHECK("bh");
-  fb.S = 1;
+  fb.S = t->n_front;
   return FGA_OK;
 }
 
@@ -294,7 +347,7 @@ static constexpr int EPI_BS = 256;
 
 int epilogue_blocks(int64_t M) {
   const int64_t g = (M + EPI_BS - 1) / EPI_BS;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 2 * (int64_t)sm_count()));
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 8 * (int64_t)sm_count()));
 }
 
 // Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations (FP64):
@@ -391,6 +444,56 @@ __device__ bool rigid_rotation(const double C[9], double R[9]) {
   return true;
 }
 
+// Orthogonal polar factor of C by the scaled Newton iteration
+// X <- (g X + X^{-T} / g) / 2, g = (|X^{-1}|_F / |X|_F)^{1/2} (Higham's scaling),
+// started from C / |C|_F. For det C > 0 the limit is U V^T of C = U S V^T,
+// which is Eq. 14's rotation (sgn det(U V^T) = +1). Needs a few 3x3 inverses
+// instead of an eigen-decomposition, which matters because every FP64
+// operation of this single thread is on the iteration's critical path.
+// Returns false when C is not safely positive-determinant (the caller then
+// takes the eigen-decomposition route, which also handles rank deficiency).
+__device__ bool polar_rotation(const double C[9], double R[9]) {
+  double nc = 0;
+  for (int k = 0; k < 9; ++k) nc += C[k] * C[k];
+  if (!(nc > 0.0)) return false;
+  nc = sqrt(nc);
+  double X[9];
+  for (int k = 0; k < 9; ++k) X[k] = C[k] / nc;
+  for (int it = 0; it < 30; ++it) {
+    // cofactors: X^{-T} = cof(X) / det(X)
+    double cf[9];
+    cf[0] = X[4] * X[8] - X[5] * X[7];
+    cf[1] = X[5] * X[6] - X[3] * X[8];
+    cf[2] = X[3] * X[7] - X[4] * X[6];
+    cf[3] = X[2] * X[7] - X[1] * X[8];
+    cf[4] = X[0] * X[8] - X[2] * X[6];
+    cf[5] = X[1] * X[6] - X[0] * X[7];
+    cf[6] = X[1] * X[5] - X[2] * X[4];
+    cf[7] = X[2] * X[3] - X[0] * X[5];
+    cf[8] = X[0] * X[4] - X[1] * X[3];
+    const double det = X[0] * cf[0] + X[1] * cf[1] + X[2] * cf[2];
+    if (!(det > 1e-9)) return false;  // |X|_F = O(1): small det means near rank 2
+    const double idet = 1.0 / det;
+    double nx = 0, ni = 0;
+    for (int k = 0; k < 9; ++k) {
+      cf[k] *= idet;
+      nx += X[k] * X[k];
+      ni += cf[k] * cf[k];
+    }
+    const double g = sqrt(sqrt(ni / nx));
+    const double a = 0.5 * g, b = 0.5 / g;
+    double diff = 0;
+    for (int k = 0; k < 9; ++k) {
+      const double xn = a * X[k] + b * cf[k];
+      diff += (xn - X[k]) * (xn - X[k]);
+      X[k] = xn;
+    }
+    if (diff < 1e-28) break;
+  }
+  for (int k = 0; k < 9; ++k) R[k] = X[k];
+  return true;
+}
+
 // One thread: reductions -> C -> (R', t') -> compose, convergence, next-iteration constants.
 __device__ void rigid_step(const double* red, int64_t M, DevState* ds, const EpiParams& ep,
                            double* traj, unsigned long long inter_add) {
@@ -407,7 +510,7 @@ __device__ void rigid_step(const double* red, int64_t M, DevState* ds, const Epi
     for (int c = 0; c < 3; ++c)
       C[3 * r + c] = S[3 * r + c] + red[12 + 3 * r + c] - Md * (ybar[r] + mud[r]) * ybar[c];
   double Rp[9];
-  const bool ok = rigid_rotation(C, Rp);
+  const bool ok = polar_rotation(C, Rp) || rigid_rotation(C, Rp);
   if (!ok) {
     for (int k = 0; k < 9; ++k) Rp[k] = (k % 4 == 0) ? 1.0 : 0.0;
     ds->degenerate += 1;
@@ -507,15 +610,24 @@ __global__ void __launch_bounds__(EPI_BS) k_epilogue(const float4* __restrict__ 
     const float3 y = place(xf, y0);
     const float cx = y.x - mu0, cy = y.y - mu1, cz = y.z - mu2;
     float ahx = 0.f, ahy = 0.f, ahz = 0.f, alx = 0.f, aly = 0.f, alz = 0.f;
-    for (int s = 0; s < S; ++s) {
-      const float4 h = hi[(int64_t)s * M + i];
-      const float4 l = lo[(int64_t)s * M + i];
-      comp_add(ahx, alx, h.x);
-      comp_add(ahy, aly, h.y);
-      comp_add(ahz, alz, h.z);
-      alx += l.x;
-      aly += l.y;
-      alz += l.z;
+    for (int s = 0; s < S; s += 4) {
+      // four independent loads in flight, then the same in-order compensated sum
+      float4 h[4], l[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool ok = s + k < S;
+        h[k] = ok ? hi[(int64_t)(s + k) * M + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        l[k] = ok ? lo[(int64_t)(s + k) * M + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        comp_add(ahx, alx, h[k].x);
+        comp_add(ahy, aly, h[k].y);
+        comp_add(ahz, alz, h[k].z);
+        alx += l[k].x;
+        aly += l[k].y;
+        alz += l[k].z;
+      }
     }
     const float ax = ep.G * (ahx + alx), ay = ep.G * (ahy + aly), az = ep.G * (ahz + alz);
     float vx, vy, vz;
@@ -659,6 +771,8 @@ __global__ void k_state_init(DevState* ds, const double* __restrict__ mu0) {
   z.done = 0;
   z.status = 0;
   z.degenerate = 0;
+  z.bh_next = 0u;
+  z.bh_exited = 0u;
   *ds = z;
 }
 

@@ -71,6 +71,8 @@ struct DevState {
   int done;               // convergence test fired
   int status;             // bit 0: stack overflow in BH traversal; bit 1: non-finite fit
   int degenerate;         // rigid fits with rank(C) < 2
+  unsigned bh_next;       // BH traversal: next 32-point group to hand out
+  unsigned bh_exited;     // BH traversal: warps that found no group left
 };
 
 // Number of FP64 reduction values per block: sum y_c (3), sum d (3),
@@ -78,6 +80,21 @@ struct DevState {
 constexpr int NRED = 27;
 
 // ------------------------------------------------------------------ tree
+// A frontier cell of the tree: the cells of the frontier partition the tree
+// (every leaf lies under exactly one of them). BH work for a group of template
+// points is split into one task per frontier cell. path[] lists the cell's
+// ancestors from the root; bit j of first_mask is set when this cell is the
+// first frontier cell (in depth-first order) under path[j], i.e. the task that
+// adds path[j]'s monopole for lanes that accept it.
+constexpr int FRONT_MAX_PATH = 27;
+struct FrontCell {
+  int node;
+  int npath;
+  unsigned first_mask;
+  int path[FRONT_MAX_PATH];
+  int pad;
+};
+constexpr int FRONT_TARGET = 16;  // frontier size the build aims for
 }  // namespace fga
 
 struct fga_tree {
@@ -94,6 +111,10 @@ struct fga_tree {
                                  //  count > 0: children first .. first+count-1
                                  //  count < 0: leaf, bodies first .. first-count-1
   int2* node_bodies = nullptr;   // n_nodes: body range [x, y) of the cell
+  fga::FrontCell* front = nullptr;  // frontier cells (device), depth-first order
+  float4* node_rec = nullptr;    // n_nodes x 2 float4: (CoM, mass), (info as int bits),
+                                 // one 32-byte record per cell for the traversal
+  int n_front = 0;
   float box_lo[3], box_hi[3];    // root box (tight bounding box of X)
   cudaStream_t stream = nullptr; // stream the buffers were allocated on
 };

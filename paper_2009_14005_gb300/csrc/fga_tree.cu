@@ -20,6 +20,7 @@
 // mass and centre of mass (FP64 sums, rounded once to FP32).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "fga_internal.cuh"
@@ -185,7 +186,81 @@ __global__ void k_mass_level(int L, const LevelInfo* __restrict__ lv, const floa
   }
 }
 
+// Frontier for splitting BH work (see FrontCell): starting from the root,
+// repeatedly replace the frontier cell holding the most bodies by its
+// children, until about FRONT_TARGET cells (never more than 32) or only
+// leaves remain. Uses the first levels of the breadth-first node arrays.
+static int build_frontier(fga_tree* T, cudaStream_t s) {
+  const int64_t P = std::min<int64_t>(T->n_nodes, 1 << 16);
+  std::vector<int4> info(P);
+  std::vector<int2> nb(P);
+  FGA_CUDA_TRY(cudaMemcpyAsync(info.data(), T->node_info, sizeof(int4) * P, cudaMemcpyDeviceToHost, s));
+  FGA_CUDA_TRY(cudaMemcpyAsync(nb.data(), T->node_bodies, sizeof(int2) * P, cudaMemcpyDeviceToHost, s));
+  FGA_CUDA_TRY(cudaStreamSynchronize(s));
+  struct Item {
+    int node;
+    std::vector<int> path;
+  };
+  std::vector<Item> front{{0, {}}};
+  const int kMax = 32;
+  while ((int)front.size() < FRONT_TARGET) {
+    int best = -1, best_n = 1;
+    for (int k = 0; k < (int)front.size(); ++k) {
+      const int v = front[k].node;
+      const int4 in = info[v];
+      if (in.z <= 0 || (int64_t)in.y + in.z > P || (int)front[k].path.size() >= FRONT_MAX_PATH) continue;
+      const int n = nb[v].y - nb[v].x;
+      if (n > best_n) {
+        best_n = n;
+        best = k;
+      }
+    }
+    if (best < 0) break;
+    const int v = front[best].node;
+    if ((int)front.size() - 1 + info[v].z > kMax) break;
+    std::vector<int> path = front[best].path;
+    path.push_back(v);
+    front.erase(front.begin() + best);
+    for (int c = 0; c < info[v].z; ++c) front.push_back({info[v].y + c, path});
+  }
+  std::sort(front.begin(), front.end(),
+            [&](const Item& a, const Item& b) { return nb[a.node].x < nb[b.node].x; });
+  std::vector<FrontCell> table(front.size());
+  for (size_t k = 0; k < front.size(); ++k) {
+    FrontCell& fc = table[k];
+    std::memset(&fc, 0, sizeof(fc));
+    fc.node = front[k].node;
+    fc.npath = (int)front[k].path.size();
+    for (int j = 0; j < fc.npath; ++j) {
+      fc.path[j] = front[k].path[j];
+      if (nb[fc.node].x == nb[fc.path[j]].x) fc.first_mask |= 1u << j;
+    }
+  }
+  int rc = dev_alloc_n(&T->front, table.size(), s);
+  if (rc) return rc;
+  FGA_CUDA_TRY(cudaMemcpyAsync(T->front, table.data(), sizeof(FrontCell) * table.size(),
+                               cudaMemcpyHostToDevice, s));
+  FGA_CUDA_TRY(cudaStreamSynchronize(s));
+  T->n_front = (int)table.size();
+  return FGA_OK;
+}
+
+__global__ void k_interleave(const float4* __restrict__ cm, const int4* __restrict__ info,
+                             int64_t n, float4* __restrict__ rec) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int4 in = info[i];
+    rec[2 * i] = cm[i];
+    rec[2 * i + 1] = make_float4(__int_as_float(in.x), __int_as_float(in.y), __int_as_float(in.z),
+                                 __int_as_float(in.w));
+  }
+}
+
 int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out, cudaStream_t s) {
+  if (N > ((int64_t)1 << 26)) {
+    set_error("tree_build: at most 2^26 points per tree");
+    return FGA_EINVAL;
+  }
   fga_tree* T = new fga_tree();
   T->N = N;
   T->max_depth = D;
@@ -286,6 +361,16 @@ int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out
   }
   T->n_nodes = h_lv.start[D + 1];
   T->n_unique = (int)h_nu;
+  if ((rc = build_frontier(T, s))) {
+    fga_tree_destroy(T);
+    return rc;
+  }
+  if (dev_alloc_n(&T->node_rec, (size_t)2 * T->n_nodes, s)) {
+    fga_tree_destroy(T);
+    return FGA_ENOMEM;
+  }
+  k_interleave<<<grid, TB, 0, s>>>(T->node_cm, T->node_info, T->n_nodes, T->node_rec);
+  FGA_LAUNCH_CHECK("interleave");
   *out = T;
   return FGA_OK;
 }
@@ -305,6 +390,8 @@ extern "C" void fga_tree_destroy(fga_tree* t) {
   dev_free(t->node_cm, t->stream);
   dev_free(t->node_info, t->stream);
   dev_free(t->node_bodies, t->stream);
+  dev_free(t->front, t->stream);
+  dev_free(t->node_rec, t->stream);
   if (prev != t->device) cudaSetDevice(prev);
   delete t;
 }
