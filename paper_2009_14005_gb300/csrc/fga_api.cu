@@ -437,7 +437,8 @@ static int state_create_checked(const float* Xn, const float* mX, int64_t N, con
 
 static int step_impl(fga_state* st, int n_iter, cudaStream_t s) {
   const fga_params& p = st->p;
-  EpiParams ep{p.G, p.dt, p.eta, p.velocity_mode, (double)p.conv_tol, st->max_traj};
+  EpiParams ep{p.G, p.dt, p.eta, p.velocity_mode, (double)p.conv_tol, st->max_traj,
+               1.0 / (double)st->M, 1.0 / (double)p.dt};
   const unsigned long long inter = p.method == FGA_BH ? 0ull : (unsigned long long)(st->N * st->M);
   if (p.profile) {
     const size_t need = 2 * (size_t)(st->timed + n_iter);

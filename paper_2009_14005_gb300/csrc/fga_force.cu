@@ -347,7 +347,9 @@ static constexpr int EPI_BS = 256;
 
 int epilogue_blocks(int64_t M) {
   const int64_t g = (M + EPI_BS - 1) / EPI_BS;
-  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 8 * (int64_t)sm_count()));
+  // at most 2 blocks per SM: each block leaves 27 FP64 partials for the last
+  // block to add, and FP64 adds are scarce on this GPU
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, 2 * (int64_t)sm_count()));
 }
 
 // Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations (FP64):
@@ -444,51 +446,72 @@ __device__ bool rigid_rotation(const double C[9], double R[9]) {
   return true;
 }
 
+// FP64 on this GPU has long dependent latencies (about 64 cycles per DFMA and
+// over 600 per division or square root), and the rigid fit is one thread's
+// dependency chain on the iteration's critical path. So the chain avoids FP64
+// division and square root: reciprocals are an FP32 seed refined by two
+// Newton steps in FP64 (r <- r + r (1 - d r), 24 -> 48 -> 53 bits), and sums
+// are pairwise.
+__device__ __forceinline__ double rcp64(double d) {
+  double r = (double)__frcp_rn((float)d);
+  r = fma(r, fma(-d, r, 1.0), r);
+  r = fma(r, fma(-d, r, 1.0), r);
+  return r;
+}
+
+__device__ __forceinline__ double sum9(const double v[9]) {
+  return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+}
+
 // Orthogonal polar factor of C by the scaled Newton iteration
-// X <- (g X + X^{-T} / g) / 2, g = (|X^{-1}|_F / |X|_F)^{1/2} (Higham's scaling),
-// started from C / |C|_F. For det C > 0 the limit is U V^T of C = U S V^T,
-// which is Eq. 14's rotation (sgn det(U V^T) = +1). Needs a few 3x3 inverses
-// instead of an eigen-decomposition, which matters because every FP64
-// operation of this single thread is on the iteration's critical path.
-// Returns false when C is not safely positive-determinant (the caller then
-// takes the eigen-decomposition route, which also handles rank deficiency).
+// X <- (g X + X^{-T} / g) / 2 (Higham), started from a positive multiple of C.
+// For det C > 0 the limit is U V^T of C = U S V^T, i.e. Eq. 14's rotation
+// (sgn det(U V^T) = +1). Any g > 0 keeps the same limit, so the scaling
+// g = (|X^{-1}|_F / |X|_F)^{1/2} and the start scale are computed in FP32;
+// the iterates themselves are FP64. Returns false when C is not safely
+// positive-determinant (the caller then takes the eigen-decomposition route,
+// which also handles rank deficiency).
 __device__ bool polar_rotation(const double C[9], double R[9]) {
-  double nc = 0;
-  for (int k = 0; k < 9; ++k) nc += C[k] * C[k];
-  if (!(nc > 0.0)) return false;
-  nc = sqrt(nc);
+  double sq[9];
+  for (int k = 0; k < 9; ++k) sq[k] = C[k] * C[k];
+  const double nc2 = sum9(sq);
+  if (!(nc2 > 0.0) || !isfinite(nc2)) return false;
+  const double s0 = (double)rsqrtf((float)nc2);
   double X[9];
-  for (int k = 0; k < 9; ++k) X[k] = C[k] / nc;
+  for (int k = 0; k < 9; ++k) X[k] = C[k] * s0;
+  bool scaled = true;  // unscaled steps near the limit: an FP32 g would move the fixed point
   for (int it = 0; it < 30; ++it) {
     // cofactors: X^{-T} = cof(X) / det(X)
     double cf[9];
-    cf[0] = X[4] * X[8] - X[5] * X[7];
-    cf[1] = X[5] * X[6] - X[3] * X[8];
-    cf[2] = X[3] * X[7] - X[4] * X[6];
-    cf[3] = X[2] * X[7] - X[1] * X[8];
-    cf[4] = X[0] * X[8] - X[2] * X[6];
-    cf[5] = X[1] * X[6] - X[0] * X[7];
-    cf[6] = X[1] * X[5] - X[2] * X[4];
-    cf[7] = X[2] * X[3] - X[0] * X[5];
-    cf[8] = X[0] * X[4] - X[1] * X[3];
-    const double det = X[0] * cf[0] + X[1] * cf[1] + X[2] * cf[2];
-    if (!(det > 1e-9)) return false;  // |X|_F = O(1): small det means near rank 2
-    const double idet = 1.0 / det;
-    double nx = 0, ni = 0;
+    cf[0] = fma(X[4], X[8], -X[5] * X[7]);
+    cf[1] = fma(X[5], X[6], -X[3] * X[8]);
+    cf[2] = fma(X[3], X[7], -X[4] * X[6]);
+    cf[3] = fma(X[2], X[7], -X[1] * X[8]);
+    cf[4] = fma(X[0], X[8], -X[2] * X[6]);
+    cf[5] = fma(X[1], X[6], -X[0] * X[7]);
+    cf[6] = fma(X[1], X[5], -X[2] * X[4]);
+    cf[7] = fma(X[2], X[3], -X[0] * X[5]);
+    cf[8] = fma(X[0], X[4], -X[1] * X[3]);
+    const double det = fma(X[0], cf[0], fma(X[1], cf[1], X[2] * cf[2]));
+    if (!(det > 1e-9)) return false;  // |X|_F ~ 1: a small det means near rank 2
+    const double idet = rcp64(det);
+    double xx[9], ii[9];
     for (int k = 0; k < 9; ++k) {
       cf[k] *= idet;
-      nx += X[k] * X[k];
-      ni += cf[k] * cf[k];
+      xx[k] = X[k] * X[k];
+      ii[k] = cf[k] * cf[k];
     }
-    const double g = sqrt(sqrt(ni / nx));
-    const double a = 0.5 * g, b = 0.5 / g;
-    double diff = 0;
+    const float g = scaled ? sqrtf(sqrtf((float)sum9(ii) / (float)sum9(xx))) : 1.0f;
+    const double a = 0.5 * (double)g, b = 0.5 * (double)(1.0f / g);
+    double dd[9];
     for (int k = 0; k < 9; ++k) {
-      const double xn = a * X[k] + b * cf[k];
-      diff += (xn - X[k]) * (xn - X[k]);
+      const double xn = fma(a, X[k], b * cf[k]);
+      dd[k] = (xn - X[k]) * (xn - X[k]);
       X[k] = xn;
     }
-    if (diff < 1e-28) break;
+    const double change = sum9(dd);
+    if (!scaled && change < 1e-28) break;
+    if (change < 1e-8) scaled = false;
   }
   for (int k = 0; k < 9; ++k) R[k] = X[k];
   return true;
@@ -500,8 +523,8 @@ __device__ void rigid_step(const double* red, int64_t M, DevState* ds, const Epi
   const double Md = (double)M;
   double ybar[3], mud[3];
   for (int k = 0; k < 3; ++k) {
-    ybar[k] = red[k] / Md;      // mean of the centred template (~0)
-    mud[k] = red[3 + k] / Md;   // mean displacement
+    ybar[k] = red[k] * ep.inv_M;     // mean of the centred template (~0)
+    mud[k] = red[3 + k] * ep.inv_M;  // mean displacement
   }
   // symmetric S = sum yc yc^T (xx, xy, xz, yy, yz, zz) and Dy = sum d yc^T
   const double S[9] = {red[6], red[7], red[8], red[7], red[9], red[10], red[8], red[10], red[11]};
@@ -562,7 +585,7 @@ __device__ void rigid_step(const double* red, int64_t M, DevState* ds, const Epi
                          Rn[3 * r + 2] * ds->mu0[2] + tn[r]);
   // rigid velocity of the next iteration: v = (y_new - y_old)/dt with
   // y_old = R'^T (y_new - t'), i.e. v = (I - R'^T)/dt y_new + R'^T t'/dt
-  const double idt = 1.0 / (double)ep.dt;
+  const double idt = ep.inv_dt;
   for (int r = 0; r < 3; ++r) {
     for (int c = 0; c < 3; ++c)
       ds->A[3 * r + c] = (float)(((r == c ? 1.0 : 0.0) - Rp[3 * c + r]) * idt);
@@ -678,28 +701,27 @@ __global__ void __launch_bounds__(EPI_BS) k_epilogue(const float4* __restrict__ 
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  // last block: FP64 sum over the per-block partials, fixed order
-  double d[NRED];
-#pragma unroll
-  for (int k = 0; k < NRED; ++k) d[k] = 0.0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += EPI_BS)
-#pragma unroll
-    for (int k = 0; k < NRED; ++k) d[k] += __ldcg(&partials[(int64_t)b * NRED + k]);
-#pragma unroll
-  for (int k = 0; k < NRED; ++k)
-    for (int off = 16; off > 0; off >>= 1) d[k] += __shfl_down_sync(FULL, d[k], off);
+  // last block: FP64 sum over the per-block partials in a fixed order.
+  // Thread t < 8 * NRED adds value k = t % NRED over blocks j, j + 8, ...
+  // (j = t / NRED); then NRED threads add the 8 strands.
+  __shared__ double s_strand[8][NRED];
+  __shared__ double s_red[NRED];
+  if (threadIdx.x < 8 * NRED) {
+    const int k = threadIdx.x % NRED, j = threadIdx.x / NRED;
+    double acc = 0.0;
+    for (int b = j; b < (int)gridDim.x; b += 8) acc += __ldcg(&partials[(int64_t)b * NRED + k]);
+    s_strand[j][k] = acc;
+  }
   __syncthreads();
-  if (lane == 0)
-#pragma unroll
-    for (int k = 0; k < NRED; ++k) s_w[w][k] = d[k];
+  if (threadIdx.x < NRED) {
+    double acc = 0.0;
+    for (int j = 0; j < 8; ++j) acc += s_strand[j][threadIdx.x];
+    s_red[threadIdx.x] = acc;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     double red[NRED];
-    for (int k = 0; k < NRED; ++k) {
-      double acc = 0;
-      for (int ww = 0; ww < EPI_BS / 32; ++ww) acc += s_w[ww][k];
-      red[k] = acc;
-    }
+    for (int k = 0; k < NRED; ++k) red[k] = s_red[k];
     rigid_step(red, M, ds, ep, traj, inter_add);
     *counter = 0u;
     __threadfence();

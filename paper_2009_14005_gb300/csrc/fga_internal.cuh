@@ -175,6 +175,7 @@ struct EpiParams {
   int vmode;
   double conv_tol;
   int max_traj;
+  double inv_M, inv_dt;  // 1/M and 1/dt, FP64, computed on the host
 };
 int launch_epilogue(const float4* Y0, int64_t M, const ForceBuffers& fb, float4* V,
                     DevState* ds, double* d_partials, unsigned* d_counter, double* d_traj,
