@@ -253,37 +253,37 @@ __global__ void __launch_bounds__(BH_WARPS * 32, 8) k_bh(const float4* __restric
         py = fmaf(wgt, dy, py);
         pz = fmaf(wgt, dz, pz);
         count += accept;
-        if (!accept) {
-          if (nchild > 0) {
-            // descend: save the rest of this range, continue with the children
-            if (cnt > 0) {
-              if (sp < BH_DEPTH) stk[32 * sp] = ((unsigned)cur << 4) | (unsigned)cnt;
-              else overflow = true;
-              ++sp;
-            }
-            cur = __float_as_int(ri.y);
-            cnt = nchild;
-          } else {
-            // leaf holding several particles: add each exactly
-            const int b0 = __float_as_int(ri.y), nb = -nchild;
-            for (int b = 0; b < nb; ++b) {
-              const float4 q = bodies[b0 + b];
-              const float ex = q.x - y.x, ey = q.y - y.y, ez = q.z - y.z;
-              const float iq = rsqrtf(fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, eps2))));
-              const float wq = q.w * (iq * iq * iq);
-              px = fmaf(wq, ex, px);
-              py = fmaf(wq, ey, py);
-              pz = fmaf(wq, ez, pz);
-            }
-            count += (unsigned)nb;
+        // descend into an internal cell that fails the test: save the rest of
+        // the current range, continue with the children (branch-free)
+        const bool descend = !accept && nchild > 0;
+        const bool save = descend && cnt > 0;
+        if (save) {
+          if (sp < BH_DEPTH) stk[32 * sp] = ((unsigned)cur << 4) | (unsigned)cnt;
+          else overflow = true;
+        }
+        sp += save;
+        cur = descend ? __float_as_int(ri.y) : cur;
+        cnt = descend ? nchild : cnt;
+        if (!accept && nchild < -1) {
+          // leaf holding several particles: add each exactly (rare)
+          const int b0 = __float_as_int(ri.y), nb = -nchild;
+          for (int b = 0; b < nb; ++b) {
+            const float4 q = bodies[b0 + b];
+            const float ex = q.x - y.x, ey = q.y - y.y, ez = q.z - y.z;
+            const float iq = rsqrtf(fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, eps2))));
+            const float wq = q.w * (iq * iq * iq);
+            px = fmaf(wq, ex, px);
+            py = fmaf(wq, ey, py);
+            pz = fmaf(wq, ez, pz);
           }
+          count += (unsigned)nb;
         }
-        if (cnt == 0 && sp > 0) {
-          --sp;
-          const unsigned e = sp < BH_DEPTH ? stk[32 * sp] : 0u;
-          cur = (int)(e >> 4);
-          cnt = (int)(e & 15u);
-        }
+        // range exhausted: resume the innermost saved range
+        const bool pop = cnt == 0 && sp > 0;
+        sp -= pop;
+        const unsigned e = (pop && sp < BH_DEPTH) ? stk[32 * sp] : 0u;
+        cur = pop ? (int)(e >> 4) : cur;
+        cnt = pop ? (int)(e & 15u) : cnt;
       }
       if (++since_flush == 32) {
         comp_add(hx, lx, px);

@@ -94,7 +94,7 @@ struct FrontCell {
   int path[FRONT_MAX_PATH];
   int pad;
 };
-constexpr int FRONT_TARGET = 16;  // frontier size the build aims for
+constexpr int FRONT_TARGET = 32;  // frontier size the build aims for
 }  // namespace fga
 
 struct fga_tree {
