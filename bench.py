@@ -191,6 +191,11 @@ WORKLOADS = {
     # large piecewise-planar scenes, Barnes-Hut
     "planar-bh": dict(gen="planar", n=1_000_000, iters=100, method="bh", theta=0.5, niv=False,
                       G=66.7, eps=0.2, eta=0.2),
+    # many independent pairs (N, M log-uniform in [500, 50k], sphere and planar
+    # shapes, rotations <= 60 deg), all-pairs or Barnes-Hut per pair by size,
+    # one graph-captured loop per step; n = number of pairs
+    "batch": dict(gen="batch", n=256, iters=100, method="auto", theta=0.5, niv=False,
+                  G=66.7, eps=0.2, eta=0.2),
 }
 
 
@@ -206,9 +211,18 @@ def workload(a):
 def workload_config(a):
     w = workload(a)
     name = "%s-%dk-%s%s-%dit" % (
-        {"lidar": "lidar-sweeps", "sphere": "unit-sphere", "planar": "planar-scene"}[w["gen"]],
+        {"lidar": "lidar-sweeps", "sphere": "unit-sphere", "planar": "planar-scene",
+         "batch": "batch"}[w["gen"]],
         max(w["n"] // 1000, 1), "bh-theta%.1f" % w["theta"] if w["method"] == "bh" else "direct",
         "", w["iters"])
+    if w["gen"] == "batch":
+        return {"workload": "batch-%d-pairs-500-50k-%dit" % (w["n"], w["iters"]), "pairs": w["n"],
+                "N_M": "log-uniform in [500, 50000], independently", "iterations": w["iters"],
+                "method": "per pair: all-pairs if N <= 32768 else barnes-hut (theta %.1f)" % w["theta"],
+                "masses": "uniform", "eps": w["eps"], "eta": w["eta"], "dt": 0.1, "G": w["G"],
+                "pairs_per_rank": a.pairs,
+                "l2": "flushed between steps (256 MB device write outside the timed events)",
+                "inputs": "resident in HBM at the start of each timed step"}
     return {"workload": name, "N": w["n"], "M": w["n"], "iterations": w["iters"],
             "method": "barnes-hut" if w["method"] == "bh" else "all-pairs",
             "theta": w["theta"] if w["method"] == "bh" else None,
@@ -220,6 +234,8 @@ def workload_config(a):
 
 def make_pairs(seeds, a):
     w = workload(a)
+    if w["gen"] == "batch":
+        return [synth.batch_pairs(s, count=w["n"]) for s in seeds]
     gen = {"lidar": synth.lidar_pair, "sphere": synth.sphere_pair,
            "planar": synth.planar_scene_pair}[w["gen"]]
     return [gen(s, n=w["n"]) for s in seeds]
@@ -227,7 +243,7 @@ def make_pairs(seeds, a):
 
 def lib_params(fga, a):
     w = workload(a)
-    return fga.params(method=fga.FGA_BH if w["method"] == "bh" else fga.FGA_DIRECT,
+    return fga.params(method={"bh": fga.FGA_BH, "direct": fga.FGA_DIRECT, "auto": fga.FGA_AUTO}[w["method"]],
                       theta=w["theta"], max_iter=w["iters"], G=w["G"], eps=w["eps"], eta=w["eta"],
                       mass_mode=fga.FGA_MASS_NIV if w["niv"] else fga.FGA_MASS_UNIFORM, profile=1)
 
@@ -241,6 +257,9 @@ def cpu_sample(pair, a, iters):
     import oracle
     oracle.build()
     w = workload(a)
+    if w["gen"] == "batch":
+        pair = pair[0]
+        w = dict(w, method="direct" if len(pair[0]) <= 32768 else "bh")
     X, Y, _, _ = pair
     if w["method"] == "direct":
         keep = int(max(1, min(len(Y), 2e10 / (len(X) * iters))))
@@ -387,10 +406,140 @@ def run_ours(a):
     return 0
 
 
+def run_ours_batch(a):
+    """One step = fga_register_batch over a whole batch of resident pairs."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2009_14005_gb300 as fga
+
+    batches = make_pairs(shard_seeds(rank, world, a.pairs), a)
+    dev = [[(torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda")) for X, Y, _, _ in b]
+           for b in batches]
+    host = [[(torch.from_numpy(X).pin_memory(), torch.from_numpy(Y).pin_memory()) for X, Y, _, _ in b]
+            for b in batches]
+    p = lib_params(fga, a)
+    p.profile = 0
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for k in range(a.warmup):
+        fga.fga_register_batch(dev[k % len(dev)], p, stream=stream)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = fga.fga_launch_count()
+    step_ms, inter, regs = [], 0, 0
+    for k in range(a.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res, st = fga.fga_register_batch(dev[k % len(dev)], p, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        inter += st["interactions"]
+        regs += len(res)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = fga.fga_launch_count() - launches0
+    clk = clocks.stop()
+    t_local = sum(step_ms)
+    t_max, inter_all = reduce_max_sum(t_local, float(inter), world)
+    _, regs_all = reduce_max_sum(t_local, float(regs), world)
+    value = inter_all / (t_max / 1e3)
+
+    # the force kernel alone: one profiled call (plain launches, events around each)
+    pp = lib_params(fga, a)
+    pp.profile = 1
+    flush.zero_()
+    _, pst = fga.fga_register_batch(dev[0], pp, stream=stream)
+    torch.cuda.synchronize()
+
+    # the same batch, one fga_register call per pair (the one-pair path)
+    seq_ms = 0.0
+    flush.zero_()
+    torch.cuda.synchronize()
+    s0 = torch.cuda.Event(enable_timing=True)
+    s1 = torch.cuda.Event(enable_timing=True)
+    s0.record(stream)
+    for Xd, Yd in dev[0]:
+        fga.fga_register(Xd, Yd, p, stream=stream)
+    s1.record(stream)
+    s1.synchronize()
+    seq_ms = s0.elapsed_time(s1)
+
+    # end to end: pinned host inputs through the same C call
+    e2e_t, e2e_i, h2d, d2h = 0.0, 0, 0, 0
+    for k in range(a.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res, st = fga.fga_register_batch(host[k % len(host)], p, stream=stream)
+        e2e_t += time.perf_counter() - t0
+        e2e_i += st["interactions"]
+        h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
+    e2e_tmax, e2e_iall = reduce_max_sum(1e3 * e2e_t, float(e2e_i), world)
+
+    if rank != 0:
+        return 0
+    peaks, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_rate = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / FP32_INSTR_PER_INTERACTION
+    launch_inter = pst["interactions"] / max(pst["force_launches"], 1)
+    launch_s = pst["force_ms"] / 1e3 / max(pst["force_launches"], 1)
+    achieved = launch_inter / launch_s if launch_s > 0 else 0.0
+    roof = {"bound": "alu", "kernel": "k_batch_force", "achieved": achieved / 1e9,
+            "peak": peak_rate / 1e9, "unit": "Ginteractions/s", "frac": achieved / peak_rate,
+            "traffic": recorded_traffic("paper_2009_14005_gb300/csrc/fga_batch.cu",
+                                        "k_batch_force_%s.md" % a.workload),
+            "peak_source": "%d SMs x %d FP32 lanes x %.0f MHz (sm_max_mhz, %s) / %d FP32 "
+                           "instructions per interaction" % (sms, FP32_LANES_PER_SM, sm_mhz, peak_src,
+                                                             FP32_INSTR_PER_INTERACTION),
+            "launches": pst["force_launches"], "interactions_per_launch": launch_inter,
+            "mean_launch_ms": 1e3 * launch_s,
+            "share_of_step": pst["force_ms"] / max(t_local / a.steps, 1e-9)}
+    nb = len(dev[0])
+    line = {"metric": "pair-interactions/s", "value": value, "unit": "interactions/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(a),
+            "registrations_per_s": regs_all / (t_max / 1e3),
+            "one_pair_path": {"registrations_per_s": nb / (seq_ms / 1e3), "ms_per_batch": seq_ms,
+                              "note": "the same %d pairs, one fga_register call each" % nb},
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "e2e": {"value": e2e_iall / (e2e_tmax / 1e3) if e2e_tmax > 0 else None,
+                    "unit": "interactions/s",
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "ms_per_step": e2e_tmax / max(a.e2e_steps, 1)},
+            "gpu_launches": launches, "roofline": roof, "clocks": clk}
+    if world == 1 and not a.no_cpu_baseline:
+        i, t, cores = cpu_sample(batches[0], a, a.cpu_iters)
+        line["cpu_baseline"] = {"value": i / t, "unit": "interactions/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": "FP64 C oracle (OpenMP), normalisation + tree + %d of %d "
+                                          "iterations on the first pair of the batch (%d x %d, %.1f s)"
+                                          % (a.cpu_iters, workload(a)["iters"], len(batches[0][0][0]),
+                                             len(batches[0][0][1]), t)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     a = parse_args(argv)
     if a.impl == "reference":
         return run_reference(a)
+    if workload(a)["gen"] == "batch":
+        return run_ours_batch(a)
     return run_ours(a)
 
 

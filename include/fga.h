@@ -42,6 +42,7 @@ extern "C" {
 /* ----------------------------------------------------------------- parameters */
 #define FGA_DIRECT 0 /* all-pairs sum of Eq. 6                          */
 #define FGA_BH 1     /* Barnes-Hut tree (Algorithm 1) + BHForce (Eq. 15) */
+#define FGA_AUTO 2   /* FGA_DIRECT when N <= fga_direct_max_n(0), else FGA_BH */
 
 #define FGA_VEL_UNCONSTRAINED 0 /* velocities of Eq. 9 persist between iterations */
 #define FGA_VEL_RIGID 1         /* velocities replaced by the rigid motion        */
@@ -57,7 +58,7 @@ typedef struct fga_params {
   float theta;       /* opening criterion of Eq. 15 (0.6)                       */
   int max_iter;      /* iterations of Algorithm 2's loop                        */
   float conv_tol;    /* stop once |T_k - T_{k-2}|_F^2 <= conv_tol; <= 0 disables */
-  int method;        /* FGA_DIRECT or FGA_BH                                    */
+  int method;        /* FGA_DIRECT, FGA_BH or FGA_AUTO                          */
   int normalize;     /* 1: scale inputs into [a, b] (Appendix A) in fga_register */
   float a, b;        /* normalisation range (-5, 5)                             */
   int velocity_mode; /* FGA_VEL_UNCONSTRAINED or FGA_VEL_RIGID                  */
@@ -253,6 +254,46 @@ void fga_state_destroy(fga_state* s);
 int fga_register(const float* X, int64_t N, const float* Y, int64_t M, const float* mX,
                  const float* mY, const fga_params* p, double R_out[9], double t_out[3],
                  fga_stats* stats, void* stream);
+
+/* ----------------------------------------------------------------- many pairs */
+/* One registration problem of a batch: points and optional masses as in
+ * fga_register (host or device pointers; N, M <= 2^26). */
+typedef struct fga_pair {
+  const float* X;
+  int64_t N;
+  const float* Y;
+  int64_t M;
+  const float* mX; /* NULL: p->mass_mode, sum 1 */
+  const float* mY; /* NULL: dt each              */
+} fga_pair;
+
+typedef struct fga_pair_result {
+  double R[9], t[3];    /* X ~ R Y + t in the original frames                */
+  int method;           /* FGA_DIRECT or FGA_BH, as chosen for this pair     */
+  int iterations;       /* iterations run before the stop test fired (or max) */
+  int converged;        /* 1 if the stop test fired                          */
+  int status;           /* FGA_OK, FGA_EDEGENERATE or FGA_EINTERNAL          */
+  int64_t interactions; /* force terms evaluated for this pair               */
+} fga_pair_result;
+
+/* Registers `count` independent pairs together (Algorithm 2 for each, with
+ * the same parameters): every pair is normalised, given masses and, for
+ * Barnes-Hut, a tree; then all pairs advance in lockstep, one iteration of
+ * all pairs per force launch plus one epilogue launch (each pair's rigid fit
+ * in its own block), and the p->max_iter iterations are captured in one CUDA
+ * graph. With p->method == FGA_AUTO each pair takes the all-pairs sum when
+ * N <= fga_direct_max_n(0) and Barnes-Hut otherwise. A pair whose stop test
+ * fires (conv_tol > 0) skips the remaining work. Results per pair go to
+ * results[count] (host). stats (optional): total interactions, elapsed_ms =
+ * whole call, force_ms = the iteration graph. Synchronises `stream`.
+ * Errors: FGA_EINVAL (any pair invalid; message names it), FGA_ENOMEM,
+ * FGA_ECUDA; FGA_EDEGENERATE / FGA_EINTERNAL if some pair reports it. */
+int fga_register_batch(const fga_pair* pairs, int count, const fga_params* p,
+                       fga_pair_result* results, fga_stats* stats, void* stream);
+
+/* Crossover of FGA_AUTO: returns the current N limit for the all-pairs sum
+ * and, if new_value > 0, sets it (process-wide). */
+int64_t fga_direct_max_n(int64_t new_value);
 
 #ifdef __cplusplus
 }

@@ -38,6 +38,7 @@ FGA_EINTERNAL = -5
 
 FGA_DIRECT = 0
 FGA_BH = 1
+FGA_AUTO = 2
 FGA_VEL_UNCONSTRAINED = 0
 FGA_VEL_RIGID = 1
 FGA_MASS_UNIFORM = 0
@@ -48,7 +49,7 @@ SYMBOLS = [
     "fga_denormalize", "fga_masses", "fga_tree_build", "fga_tree_destroy",
     "fga_tree_node_count", "fga_tree_export", "fga_forces", "fga_state_create", "fga_step",
     "fga_state_get", "fga_state_trajectory", "fga_state_destroy", "fga_register",
-    "fga_forces_direct_static",
+    "fga_forces_direct_static", "fga_register_batch", "fga_direct_max_n",
 ]
 FGA_STATIC_SCRATCH_FLOAT4 = 524288
 
@@ -82,6 +83,17 @@ class fga_stats(ctypes.Structure):
                     norm_info=np.array(self.norm_info[:]), elapsed_ms=self.elapsed_ms,
                     force_ms=self.force_ms, force_launches=self.force_launches,
                     h2d_bytes=int(self.h2d_bytes), d2h_bytes=int(self.d2h_bytes))
+
+
+class fga_pair(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("N", ctypes.c_int64), ("Y", ctypes.c_void_p),
+                ("M", ctypes.c_int64), ("mX", ctypes.c_void_p), ("mY", ctypes.c_void_p)]
+
+
+class fga_pair_result(ctypes.Structure):
+    _fields_ = [("R", ctypes.c_double * 9), ("t", ctypes.c_double * 3), ("method", ctypes.c_int),
+                ("iterations", ctypes.c_int), ("converged", ctypes.c_int), ("status", ctypes.c_int),
+                ("interactions", ctypes.c_int64)]
 
 
 class FGAError(RuntimeError):
@@ -119,6 +131,10 @@ def _load():
         "fga_register": (ctypes.c_int, [P, I64, P, I64, P, P, PP, DP, DP,
                                         ctypes.POINTER(fga_stats), VP]),
         "fga_forces_direct_static": (ctypes.c_int, [P, P, I64, P, P, I64, PP, P, VP]),
+        "fga_register_batch": (ctypes.c_int, [ctypes.POINTER(fga_pair), ctypes.c_int, PP,
+                                              ctypes.POINTER(fga_pair_result),
+                                              ctypes.POINTER(fga_stats), VP]),
+        "fga_direct_max_n": (I64, [I64]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -411,3 +427,52 @@ def fga_register(X, Y, p: fga_params | None = None, mX=None, mY=None, stream=Non
     d = st.to_dict()
     d["status"] = code
     return R.reshape(3, 3), t, d
+
+
+def fga_direct_max_n(new_value: int = 0) -> int:
+    """FGA_AUTO crossover: returns the current N limit of the all-pairs sum, sets it if > 0."""
+    return int(lib.fga_direct_max_n(int(new_value)))
+
+
+def fga_register_batch(pairs, p: fga_params | None = None, stream=None):
+    """Register many (X, Y) pairs together (one graph-captured loop for all).
+
+    ``pairs``: list of (X, Y) or (X, Y, mX, mY); arrays may be CUDA tensors or
+    host arrays. Returns (list of dicts with R, t, method, iterations,
+    converged, status, interactions; stats dict)."""
+    torch = _torch()
+    p = p or params()
+    keep = []
+
+    def arr(a, cols):
+        if a is None:
+            return None
+        if isinstance(a, torch.Tensor):
+            t = _dev(a, cols) if a.is_cuda else a.to(torch.float32).contiguous()
+        else:
+            t = torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32)))
+        keep.append(t)
+        return t
+
+    n = len(pairs)
+    cp = (fga_pair * n)()
+    for k, pr in enumerate(pairs):
+        X, Y = pr[0], pr[1]
+        mX = pr[2] if len(pr) > 2 else None
+        mY = pr[3] if len(pr) > 3 else None
+        Xt, Yt, mXt, mYt = arr(X, 3), arr(Y, 3), arr(mX, None), arr(mY, None)
+        cp[k] = fga_pair(Xt.data_ptr(), Xt.shape[0], Yt.data_ptr(), Yt.shape[0],
+                         mXt.data_ptr() if mXt is not None else None,
+                         mYt.data_ptr() if mYt is not None else None)
+    res = (fga_pair_result * n)()
+    st = fga_stats()
+    code = lib.fga_register_batch(cp, n, ctypes.byref(p), res, ctypes.byref(st), _stream(stream))
+    if code not in (FGA_OK, FGA_EDEGENERATE):
+        _err(code)
+    out = [dict(R=np.array(r.R[:]).reshape(3, 3), t=np.array(r.t[:]), method=r.method,
+                iterations=r.iterations, converged=bool(r.converged), status=r.status,
+                interactions=int(r.interactions)) for r in res]
+    d = st.to_dict()
+    d["status"] = code
+    return out, d
+

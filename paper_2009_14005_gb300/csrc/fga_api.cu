@@ -83,23 +83,7 @@ int sm_count() {
   return n;
 }
 
-// Scope guard for temporary device buffers of one call.
-struct Scratch {
-  cudaStream_t s;
-  std::vector<void*> ptrs;
-  explicit Scratch(cudaStream_t st) : s(st) {}
-  ~Scratch() {
-    for (void* p : ptrs) dev_free(p, s);
-  }
-  template <class T>
-  int alloc(T** p, size_t n) {
-    int rc = dev_alloc_n(p, n, s);
-    if (rc == FGA_OK) ptrs.push_back(*p);
-    return rc;
-  }
-};
-
-static int check_params(const fga_params* p, bool need_tree) {
+int check_params(const fga_params* p, bool need_tree) {
   if (!p) {
     set_error("null fga_params");
     return FGA_EINVAL;
@@ -116,8 +100,8 @@ static int check_params(const fga_params* p, bool need_tree) {
     set_error("dt must be > 0 and G, eta finite");
     return FGA_EINVAL;
   }
-  if (p->method != FGA_DIRECT && p->method != FGA_BH) {
-    set_error("method must be FGA_DIRECT or FGA_BH");
+  if (p->method != FGA_DIRECT && p->method != FGA_BH && p->method != FGA_AUTO) {
+    set_error("method must be FGA_DIRECT, FGA_BH or FGA_AUTO");
     return FGA_EINVAL;
   }
   if (p->velocity_mode != FGA_VEL_UNCONSTRAINED && p->velocity_mode != FGA_VEL_RIGID) {
@@ -136,7 +120,7 @@ static int check_params(const fga_params* p, bool need_tree) {
 }
 
 // Read back device flags (synchronises s).
-static int read_flags(const int* d_flags, int n, int* h, cudaStream_t s) {
+int read_flags(const int* d_flags, int n, int* h, cudaStream_t s) {
   FGA_CUDA_TRY(cudaMemcpyAsync(h, d_flags, sizeof(int) * n, cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaStreamSynchronize(s));
   return FGA_OK;
@@ -158,14 +142,14 @@ __global__ void k_gather4(const float* __restrict__ xyz, const float* __restrict
   }
 }
 
-static unsigned grid_for(int64_t n) {
+unsigned grid_for(int64_t n) {
   return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, 8 * (int64_t)sm_count()));
 }
 
 // Pack template points into float4 (x, y, z, m); with `sort`, order them along
 // a Morton curve of their own bounding box (10 bits per axis) and return the
 // permutation (sorted position -> original index).
-static int pack_template(const float* Y, const float* mY, float m_default, int64_t M, bool sort,
+int pack_template(const float* Y, const float* mY, float m_default, int64_t M, bool sort,
                          float4* Y0, int* perm, cudaStream_t s) {
   if (!sort) {
     k_pack4<<<grid_for(M), 256, 0, s>>>(Y, mY, m_default, M, Y0);
@@ -184,6 +168,98 @@ static int pack_template(const float* Y, const float* mY, float m_default, int64
   k_gather4<<<grid_for(M), 256, 0, s>>>(Y, mY, m_default, M, perm, Y0);
   FGA_LAUNCH_CHECK("gather4");
   return FGA_OK;
+}
+
+// Device pointer or host pointer? Unregistered host memory reports
+// cudaMemoryTypeUnregistered; pinned host memory cudaMemoryTypeHost.
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+
+// Register-level parameter checks beyond check_params.
+int check_register_params(const fga_params* p) {
+  int rc = check_params(p, p && p->method != FGA_DIRECT);
+  if (rc) return rc;
+  if (p->normalize && !(p->b > p->a)) {
+    set_error("b must exceed a");
+    return FGA_EINVAL;
+  }
+  if (p->mass_mode != FGA_MASS_UNIFORM && p->mass_mode != FGA_MASS_NIV) {
+    set_error("bad mass_mode");
+    return FGA_EINVAL;
+  }
+  if (p->mass_mode == FGA_MASS_NIV && (p->lattice < 1 || p->lattice > 256)) {
+    set_error("lattice must be in 1..256");
+    return FGA_EINVAL;
+  }
+  return FGA_OK;
+}
+
+// Stage one pair on the device (host inputs are copied), check it, normalise
+// it (Appendix A, if p->normalize) and assign the masses: reference masses
+// sum to 1 (p->mass_mode, or the given ones rescaled), template masses have
+// mean dt. No synchronisation: out.flags (8 ints) hold 1 at [0..3] for a
+// non-finite coordinate or a bad mass of X, Y, mX, mY and 1 at [4] when the
+// normalisation was well defined.
+int prepare_inputs(Scratch& sc, const float* X, int64_t N, const float* Y, int64_t M,
+                   const float* mX, const float* mY, const fga_params* p, Prepared& out,
+                   int64_t& h2d, cudaStream_t s) {
+  int rc = 0;
+  auto stage = [&](const float* src, int64_t count, const float** dst) -> int {
+    if (!src) {
+      *dst = nullptr;
+      return FGA_OK;
+    }
+    if (is_device_ptr(src)) {
+      *dst = src;
+      return FGA_OK;
+    }
+    float* d = nullptr;
+    if (sc.alloc(&d, count)) return FGA_ENOMEM;
+    FGA_CUDA_TRY(cudaMemcpyAsync(d, src, sizeof(float) * count, cudaMemcpyHostToDevice, s));
+    h2d += (int64_t)sizeof(float) * count;
+    *dst = d;
+    return FGA_OK;
+  };
+  const float *dX = nullptr, *dY = nullptr, *dmX = nullptr, *dmY = nullptr;
+  if ((rc = stage(X, 3 * N, &dX)) || (rc = stage(Y, 3 * M, &dY)) || (rc = stage(mX, N, &dmX)) ||
+      (rc = stage(mY, M, &dmY)))
+    return rc;
+  if (sc.alloc(&out.Xn, 3 * N) || sc.alloc(&out.Yn, 3 * M) || sc.alloc(&out.mXn, N) ||
+      sc.alloc(&out.mYn, M) || sc.alloc(&out.info, 8) || sc.alloc(&out.flags, 8))
+    return FGA_ENOMEM;
+  FGA_CUDA_TRY(cudaMemsetAsync(out.flags, 0, 8 * sizeof(int), s));
+  if ((rc = check_finite(dX, 3 * N, out.flags, s)) || (rc = check_finite(dY, 3 * M, out.flags + 1, s)))
+    return rc;
+  if (dmX && (rc = check_masses(dmX, N, out.flags + 2, s))) return rc;
+  if (dmY && (rc = check_masses(dmY, M, out.flags + 3, s))) return rc;
+  if (p->normalize) {
+    if ((rc = normalize_device(dX, N, dY, M, p->a, p->b, out.Xn, out.Yn, out.info, out.flags + 4, s)))
+      return rc;
+  } else {
+    static const double ident[8] = {0, 0, 0, 0, 0, 0, 0, 1};
+    static const int one = 1;
+    FGA_CUDA_TRY(cudaMemcpyAsync(out.Xn, dX, sizeof(float) * 3 * N, cudaMemcpyDeviceToDevice, s));
+    FGA_CUDA_TRY(cudaMemcpyAsync(out.Yn, dY, sizeof(float) * 3 * M, cudaMemcpyDeviceToDevice, s));
+    FGA_CUDA_TRY(cudaMemcpyAsync(out.info, ident, sizeof(ident), cudaMemcpyHostToDevice, s));
+    FGA_CUDA_TRY(cudaMemcpyAsync(out.flags + 4, &one, sizeof(int), cudaMemcpyHostToDevice, s));
+  }
+  if (dmX)
+    rc = rescale_masses(dmX, N, 1.0, out.mXn, s);
+  else
+    rc = masses_device(out.Xn, N, p->mass_mode, p->lattice, p->a, p->b, 1.0, out.mXn, s);
+  if (rc) return rc;
+  if (dmY)
+    rc = rescale_masses(dmY, M, (double)p->dt * (double)M, out.mYn, s);
+  else
+    rc = masses_device(out.Yn, M, FGA_MASS_UNIFORM, 1, 0.f, 1.f, (double)p->dt * (double)M, out.mYn, s);
+  return rc;
 }
 
 }  // namespace fga
@@ -480,8 +556,11 @@ int fga_state_create(const float* Xn, const float* mX, int64_t N, const float* Y
     return FGA_EINVAL;
   }
   *out = nullptr;
-  int rc = check_params(p, p && p->method == FGA_BH && !tree);
+  int rc = check_params(p, p && p->method != FGA_DIRECT && !tree);
   if (rc) return rc;
+  fga_params resolved = *p;
+  resolved.method = resolve_method(p, N);
+  p = &resolved;
   Scratch sc(s);
   int* flags = nullptr;
   if (sc.alloc(&flags, 4)) return FGA_ENOMEM;
@@ -596,17 +675,6 @@ void fga_state_destroy(fga_state* st) {
   delete st;
 }
 
-// Device pointer or host pointer? Unregistered host memory reports
-// cudaMemoryTypeUnregistered; pinned host memory cudaMemoryTypeHost.
-static bool is_device_ptr(const void* p) {
-  cudaPointerAttributes a;
-  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
-}
-
 int fga_register(const float* X, int64_t N, const float* Y, int64_t M, const float* mX,
                  const float* mY, const fga_params* p, double R_out[9], double t_out[3],
                  fga_stats* stats, void* stream) {
@@ -617,75 +685,18 @@ int fga_register(const float* X, int64_t N, const float* Y, int64_t M, const flo
     set_error("fga_register: bad arguments");
     return FGA_EINVAL;
   }
-  int rc = check_params(p, p && p->method == FGA_BH);
+  int rc = check_register_params(p);
   if (rc) return rc;
-  if (p->normalize && !(p->b > p->a)) {
-    set_error("fga_register: b must exceed a");
-    return FGA_EINVAL;
-  }
-  if (p->mass_mode != FGA_MASS_UNIFORM && p->mass_mode != FGA_MASS_NIV) {
-    set_error("fga_register: bad mass_mode");
-    return FGA_EINVAL;
-  }
-  if (p->mass_mode == FGA_MASS_NIV && (p->lattice < 1 || p->lattice > 256)) {
-    set_error("fga_register: lattice must be in 1..256");
-    return FGA_EINVAL;
-  }
+  fga_params resolved = *p;
+  resolved.method = resolve_method(p, N);
+  p = &resolved;
   Scratch sc(s);
   int64_t h2d = 0, d2h = 0;
-  // stage inputs on the device
-  auto stage = [&](const float* src, int64_t count, const float** dst) -> int {
-    if (!src) {
-      *dst = nullptr;
-      return FGA_OK;
-    }
-    if (is_device_ptr(src)) {
-      *dst = src;
-      return FGA_OK;
-    }
-    float* d = nullptr;
-    if (sc.alloc(&d, count)) return FGA_ENOMEM;
-    FGA_CUDA_TRY(cudaMemcpyAsync(d, src, sizeof(float) * count, cudaMemcpyHostToDevice, s));
-    h2d += (int64_t)sizeof(float) * count;
-    *dst = d;
-    return FGA_OK;
-  };
-  const float *dX = nullptr, *dY = nullptr, *dmX = nullptr, *dmY = nullptr;
-  if ((rc = stage(X, 3 * N, &dX)) || (rc = stage(Y, 3 * M, &dY)) || (rc = stage(mX, N, &dmX)) ||
-      (rc = stage(mY, M, &dmY)))
-    return rc;
-  float *Xn = nullptr, *Yn = nullptr, *mXn = nullptr, *mYn = nullptr;
-  double* info = nullptr;
-  int* flags = nullptr;
-  if (sc.alloc(&Xn, 3 * N) || sc.alloc(&Yn, 3 * M) || sc.alloc(&mXn, N) || sc.alloc(&mYn, M) ||
-      sc.alloc(&info, 8) || sc.alloc(&flags, 8))
-    return FGA_ENOMEM;
-  FGA_CUDA_TRY(cudaMemsetAsync(flags, 0, 8 * sizeof(int), s));
-  if ((rc = check_finite(dX, 3 * N, flags, s)) || (rc = check_finite(dY, 3 * M, flags + 1, s)))
-    return rc;
-  if (dmX && (rc = check_masses(dmX, N, flags + 2, s))) return rc;
-  if (dmY && (rc = check_masses(dmY, M, flags + 3, s))) return rc;
-  if (p->normalize) {
-    if ((rc = normalize_device(dX, N, dY, M, p->a, p->b, Xn, Yn, info, flags + 4, s))) return rc;
-  } else {
-    const double ident[8] = {0, 0, 0, 0, 0, 0, 0, 1};
-    FGA_CUDA_TRY(cudaMemcpyAsync(Xn, dX, sizeof(float) * 3 * N, cudaMemcpyDeviceToDevice, s));
-    FGA_CUDA_TRY(cudaMemcpyAsync(Yn, dY, sizeof(float) * 3 * M, cudaMemcpyDeviceToDevice, s));
-    FGA_CUDA_TRY(cudaMemcpyAsync(info, ident, sizeof(ident), cudaMemcpyHostToDevice, s));
-    const int one = 1;
-    FGA_CUDA_TRY(cudaMemcpyAsync(flags + 4, &one, sizeof(int), cudaMemcpyHostToDevice, s));
-  }
-  // masses: reference sums to 1, template mean dt (see fga_state_create)
-  if (dmX)
-    rc = rescale_masses(dmX, N, 1.0, mXn, s);
-  else
-    rc = masses_device(Xn, N, p->mass_mode, p->lattice, p->a, p->b, 1.0, mXn, s);
-  if (rc) return rc;
-  if (dmY)
-    rc = rescale_masses(dmY, M, (double)p->dt * (double)M, mYn, s);
-  else
-    rc = masses_device(Yn, M, FGA_MASS_UNIFORM, 1, 0.f, 1.f, (double)p->dt * (double)M, mYn, s);
-  if (rc) return rc;
+  Prepared pr;
+  if ((rc = prepare_inputs(sc, X, N, Y, M, mX, mY, p, pr, h2d, s))) return rc;
+  float *Xn = pr.Xn, *Yn = pr.Yn, *mXn = pr.mXn, *mYn = pr.mYn;
+  double* info = pr.info;
+  int* flags = pr.flags;
   fga_state* st = nullptr;
   if ((rc = state_create_checked(Xn, mXn, N, Yn, mYn, M, nullptr, p, &st, s))) return rc;
   rc = step_impl(st, p->max_iter, s);

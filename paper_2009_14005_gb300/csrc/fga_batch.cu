@@ -1,0 +1,425 @@
+// Batched registration: many independent pairs of uneven size advance
+// together, one iteration of Algorithm 2 for all of them per pair of launches,
+// and the whole loop is captured in one CUDA graph.
+//
+// Force launch: a static list of warp tasks covers every pair; warps take
+// tasks from a device counter. A Barnes-Hut task is (pair, 32 template points,
+// frontier cell) and runs the same per-lane BHForce walk as the single-pair
+// kernel. An all-pairs task is (pair, 32 template points, chunk of up to
+// BATCH_CHUNK reference points): the warp stages 32 sources at a time in
+// shared memory and every lane adds them to its own point (Eq. 6).
+// Epilogue launch: blocks are assigned to pairs; each pair's blocks run the
+// ODE step and reductions, and the pair's last block runs its rigid fit, so
+// the rigid fits of all pairs run in parallel. A pair whose convergence test
+// has fired skips its tasks and blocks.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "fga_device.cuh"
+
+namespace fga {
+
+constexpr int BATCH_CHUNK = 2048;  // reference points per all-pairs task
+constexpr int BATCH_WARPS = 4;
+
+struct PairDev {
+  int method;                 // FGA_DIRECT or FGA_BH
+  int K;                      // BH: frontier cells; direct: source chunks
+  const float4* rec;          // BH: interleaved cell records
+  const float4* bodies;       // BH: bodies in Morton order
+  const FrontCell* front;     // BH: frontier
+  const float4* X4;           // direct: reference points and masses
+  int64_t N, M;
+  const float4* Y0;           // template points and masses
+  DevState* ds;
+  float4* hi;                 // K x M compensated partial sums
+  float4* lo;
+  float4* V;
+  double* partials;           // nblk x NRED
+  unsigned* counter;          // epilogue blocks finished
+  int nblk;                   // epilogue blocks of this pair
+  EpiParams ep;
+  unsigned long long inter_add;  // direct: N*M terms per iteration
+};
+
+__global__ void __launch_bounds__(BATCH_WARPS * 32, 8) k_batch_force(const PairDev* __restrict__ pairs,
+                                                                     const int4* __restrict__ tasks,
+                                                                     unsigned ntasks, unsigned* ctr,
+                                                                     float eps2, float theta2) {
+  __shared__ unsigned s_stack[BATCH_WARPS][BH_DEPTH][32];
+  __shared__ float4 s_tile[BATCH_WARPS][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned* const stk = &s_stack[w][0][lane];
+  bool overflow = false;
+  for (;;) {
+    unsigned task = 0;
+    if (lane == 0) task = atomicAdd(&ctr[0], 1u);
+    task = __shfl_sync(FULL, task, 0);
+    if (task >= ntasks) break;
+    const int4 t = tasks[task];
+    const PairDev& P = pairs[t.x];
+    DevState* ds = P.ds;
+    if (ds->done) continue;
+    const int64_t M = P.M;
+    const int64_t i = (int64_t)t.y * 32 + lane;
+    const bool valid = i < M;
+    const Xf xf = load_xf(ds);
+    const float3 y = place(xf, P.Y0[valid ? i : 0]);
+    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+    unsigned count = 0;
+    const unsigned f = (unsigned)t.z;
+    if (P.method == FGA_BH) {
+      bh_task(P.rec, P.bodies, P.front, f, y, valid, eps2, theta2, stk, overflow, hx, hy, hz, lx, ly,
+              lz, count);
+      if (__any_sync(FULL, overflow)) {
+        if (lane == 0) atomicOr(&ds->status, 1);
+        overflow = false;
+      }
+    } else {
+      const int64_t j0 = (int64_t)f * BATCH_CHUNK;
+      const int64_t j1 = min(P.N, j0 + BATCH_CHUNK);
+      for (int64_t b = j0; b < j1; b += 32) {
+        const int64_t j = b + lane;
+        s_tile[w][lane] = j < j1 ? P.X4[j] : make_float4(0.f, 0.f, 0.f, 0.f);  // m = 0 pads
+        __syncwarp();
+        float px = 0.f, py = 0.f, pz = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < 32; ++k) {
+          const float4 q = s_tile[w][k];
+          const float dx = q.x - y.x, dy = q.y - y.y, dz = q.z - y.z;
+          const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2))));
+          const float wgt = q.w * (inv * inv * inv);
+          px = fmaf(wgt, dx, px);
+          py = fmaf(wgt, dy, py);
+          pz = fmaf(wgt, dz, pz);
+        }
+        comp_add(hx, lx, px);
+        comp_add(hy, ly, py);
+        comp_add(hz, lz, pz);
+        __syncwarp();
+      }
+    }
+    if (valid) {
+      P.hi[(int64_t)f * M + i] = make_float4(hx, hy, hz, 0.f);
+      P.lo[(int64_t)f * M + i] = make_float4(lx, ly, lz, 0.f);
+    }
+    if (P.method == FGA_BH) {
+      unsigned long long c = valid ? count : 0u;
+      for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(FULL, c, off);
+      if (lane == 0 && c) atomicAdd(&ds->interactions, c);
+    }
+  }
+  if (lane == 0) {
+    // the last warp out resets the task counter for the next launch
+    __threadfence();
+    const unsigned out = atomicAdd(&ctr[1], 1u);
+    if (out == gridDim.x * BATCH_WARPS - 1) {
+      ctr[0] = 0u;
+      ctr[1] = 0u;
+      __threadfence();
+    }
+  }
+}
+
+// blockmap[b] = (pair, block index within the pair)
+__global__ void __launch_bounds__(EPI_BS) k_batch_epilogue(const PairDev* __restrict__ pairs,
+                                                           const int2* __restrict__ blockmap) {
+  const int2 bm = blockmap[blockIdx.x];
+  const PairDev& P = pairs[bm.x];
+  DevState* ds = P.ds;
+  if (ds->done) return;
+  __shared__ bool s_last;
+  __shared__ double s_red[NRED];
+  const EpiCtx c = load_epi(ds);
+  float r[NRED];
+#pragma unroll
+  for (int k = 0; k < NRED; ++k) r[k] = 0.f;
+  for (int64_t i = (int64_t)bm.y * EPI_BS + threadIdx.x; i < P.M; i += (int64_t)P.nblk * EPI_BS)
+    epi_point(i, P.Y0, P.hi, P.lo, P.K, P.M, P.V, P.ep, c, r);
+  epi_block_partial(r, P.partials + (int64_t)bm.y * NRED);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = (atomicAdd(P.counter, 1u) == (unsigned)P.nblk - 1u);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  epi_last_reduce(P.partials, P.nblk, s_red);
+  if (threadIdx.x == 0) {
+    double red[NRED];
+    for (int k = 0; k < NRED; ++k) red[k] = s_red[k];
+    rigid_step(red, P.M, ds, P.ep, nullptr, P.inter_add);
+    *P.counter = 0u;
+    __threadfence();
+  }
+}
+
+static int64_t g_direct_max_n = 32768;  // FGA_AUTO: all-pairs sum when N <= this
+
+int resolve_method(const fga_params* p, int64_t N) {
+  if (p->method != FGA_AUTO) return p->method;
+  return N <= g_direct_max_n ? FGA_DIRECT : FGA_BH;
+}
+
+static int occupancy_grid(const void* kernel, int threads, int64_t want) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, threads, 0) != cudaSuccess || b < 1) {
+    cudaGetLastError();
+    b = 1;
+  }
+  return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)b * sm_count()));
+}
+
+}  // namespace fga
+
+using namespace fga;
+
+extern "C" int64_t fga_direct_max_n(int64_t new_value) {
+  const int64_t old = g_direct_max_n;
+  if (new_value > 0) g_direct_max_n = new_value;
+  return old;
+}
+
+extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_params* p,
+                                  fga_pair_result* results, fga_stats* stats, void* stream) {
+  clear_error();
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!pairs || count <= 0 || !results) {
+    set_error("fga_register_batch: bad arguments");
+    return FGA_EINVAL;
+  }
+  int rc = check_register_params(p);
+  if (rc) return rc;
+  if (p->max_depth < 1 || p->max_depth > 20) {
+    set_error("fga_register_batch: max_depth must be in 1..20");
+    return FGA_EINVAL;
+  }
+  for (int k = 0; k < count; ++k) {
+    const fga_pair& q = pairs[k];
+    if (!q.X || !q.Y || q.N <= 0 || q.M <= 0 || q.N > ((int64_t)1 << 26) || q.M > ((int64_t)1 << 26)) {
+      set_error("fga_register_batch: bad sizes or null points in pair " + std::to_string(k));
+      return FGA_EINVAL;
+    }
+  }
+  Scratch sc(s);
+  std::vector<fga_tree*> trees;
+  struct Cleanup {
+    std::vector<fga_tree*>& trees;
+    ~Cleanup() {
+      for (fga_tree* t : trees) fga_tree_destroy(t);
+    }
+  } cleanup{trees};
+  int64_t h2d = 0;
+  std::vector<Prepared> prep(count);
+  std::vector<PairDev> host(count);
+  DevState* dsarr = nullptr;
+  double* mu0 = nullptr;
+  if (sc.alloc(&dsarr, (size_t)count) || sc.alloc(&mu0, (size_t)3 * count)) return FGA_ENOMEM;
+  for (int k = 0; k < count; ++k) {
+    const fga_pair& q = pairs[k];
+    if ((rc = prepare_inputs(sc, q.X, q.N, q.Y, q.M, q.mX, q.mY, p, prep[k], h2d, s))) return rc;
+  }
+  // all checks of all pairs with one synchronisation
+  std::vector<int> flags((size_t)8 * count);
+  for (int k = 0; k < count; ++k)
+    FGA_CUDA_TRY(cudaMemcpyAsync(&flags[8 * k], prep[k].flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  FGA_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int k = 0; k < count; ++k) {
+    const int* f = &flags[8 * k];
+    if (f[0] || f[1] || f[2] || f[3] || !f[4]) {
+      set_error("fga_register_batch: pair " + std::to_string(k) +
+                (f[4] ? " has a non-finite coordinate or a bad mass" : " is degenerate (all centred coordinates equal)"));
+      return FGA_EINVAL;
+    }
+  }
+  std::vector<int4> tasks_bh, tasks_direct;
+  std::vector<int2> blockmap;
+  for (int k = 0; k < count; ++k) {
+    const fga_pair& q = pairs[k];
+    const Prepared& pr = prep[k];
+    PairDev& P = host[k];
+    std::memset(&P, 0, sizeof(P));
+    P.method = resolve_method(p, q.N);
+    P.N = q.N;
+    P.M = q.M;
+    float4* Y0 = nullptr;
+    if (sc.alloc(&Y0, q.M)) return FGA_ENOMEM;
+    if (P.method == FGA_BH) {
+      fga_tree* t = nullptr;
+      if ((rc = tree_build(pr.Xn, pr.mXn, q.N, p->max_depth, &t, s))) return rc;
+      trees.push_back(t);
+      int* perm = nullptr;
+      if (sc.alloc(&perm, q.M)) return FGA_ENOMEM;
+      if ((rc = pack_template(pr.Yn, pr.mYn, p->dt, q.M, true, Y0, perm, s))) return rc;
+      P.rec = t->node_rec;
+      P.bodies = t->bodies;
+      P.front = t->front;
+      P.K = t->n_front;
+    } else {
+      float4* X4 = nullptr;
+      if (sc.alloc(&X4, q.N)) return FGA_ENOMEM;
+      if ((rc = pack_template(pr.Xn, pr.mXn, 0.f, q.N, false, X4, nullptr, s))) return rc;
+      if ((rc = pack_template(pr.Yn, pr.mYn, p->dt, q.M, false, Y0, nullptr, s))) return rc;
+      P.X4 = X4;
+      P.K = (int)((q.N + BATCH_CHUNK - 1) / BATCH_CHUNK);
+    }
+    P.Y0 = Y0;
+    P.ds = dsarr + k;
+    P.nblk = epilogue_blocks(q.M);
+    if (sc.alloc(&P.hi, (size_t)P.K * q.M) || sc.alloc(&P.lo, (size_t)P.K * q.M) ||
+        sc.alloc(&P.V, q.M) || sc.alloc(&P.partials, (size_t)P.nblk * NRED) || sc.alloc(&P.counter, 1))
+      return FGA_ENOMEM;
+    FGA_CUDA_TRY(cudaMemsetAsync(P.V, 0, sizeof(float4) * q.M, s));
+    FGA_CUDA_TRY(cudaMemsetAsync(P.counter, 0, sizeof(unsigned), s));
+    if ((rc = centroid4(Y0, q.M, mu0 + 3 * k, s))) return rc;
+    if ((rc = launch_state_init(P.ds, mu0 + 3 * k, s))) return rc;
+    P.ep = EpiParams{p->G, p->dt, p->eta, p->velocity_mode, (double)p->conv_tol, 0,
+                     1.0 / (double)q.M, 1.0 / (double)p->dt};
+    P.inter_add = P.method == FGA_BH ? 0ull : (unsigned long long)(q.N * q.M);
+    const int groups = (int)((q.M + 31) / 32);
+    auto& tl = P.method == FGA_BH ? tasks_bh : tasks_direct;
+    for (int g = 0; g < groups; ++g)
+      for (int f = 0; f < P.K; ++f) tl.push_back(make_int4(k, g, f, 0));
+    for (int b = 0; b < P.nblk; ++b) blockmap.push_back(make_int2(k, b));
+  }
+  // Barnes-Hut tasks (usually the heaviest) are handed out first
+  std::vector<int4> tasks(tasks_bh);
+  tasks.insert(tasks.end(), tasks_direct.begin(), tasks_direct.end());
+  PairDev* d_pairs = nullptr;
+  int4* d_tasks = nullptr;
+  int2* d_blockmap = nullptr;
+  unsigned* d_ctr = nullptr;
+  if (sc.alloc(&d_pairs, (size_t)count) || sc.alloc(&d_tasks, tasks.size()) ||
+      sc.alloc(&d_blockmap, blockmap.size()) || sc.alloc(&d_ctr, 2))
+    return FGA_ENOMEM;
+  FGA_CUDA_TRY(cudaMemcpyAsync(d_pairs, host.data(), sizeof(PairDev) * count, cudaMemcpyHostToDevice, s));
+  FGA_CUDA_TRY(cudaMemcpyAsync(d_tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice, s));
+  FGA_CUDA_TRY(cudaMemcpyAsync(d_blockmap, blockmap.data(), sizeof(int2) * blockmap.size(),
+                               cudaMemcpyHostToDevice, s));
+  FGA_CUDA_TRY(cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned), s));
+  const auto t_setup = std::chrono::steady_clock::now();
+  // the iteration loop as one CUDA graph on a private stream ordered after s
+  const unsigned ntasks = (unsigned)tasks.size();
+  const int fgrid = occupancy_grid((const void*)k_batch_force, BATCH_WARPS * 32,
+                                   ((int64_t)ntasks + BATCH_WARPS - 1) / BATCH_WARPS);
+  const float eps2 = p->eps * p->eps, theta2 = p->theta * p->theta;
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  struct GraphCleanup {
+    cudaStream_t& cs;
+    cudaEvent_t& a;
+    cudaEvent_t& b;
+    cudaGraph_t& g;
+    cudaGraphExec_t& e;
+    ~GraphCleanup() {
+      if (e) cudaGraphExecDestroy(e);
+      if (g) cudaGraphDestroy(g);
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+      if (cs) cudaStreamDestroy(cs);
+    }
+  } gclean{cs, ev_in, ev_out, graph, exec};
+  FGA_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  FGA_CUDA_TRY(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+  FGA_CUDA_TRY(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+  FGA_CUDA_TRY(cudaEventRecord(ev_in, s));
+  FGA_CUDA_TRY(cudaStreamWaitEvent(cs, ev_in, 0));
+  double prof_ms = 0.0;
+  int prof_launches = 0;
+  if (p->max_iter > 0 && p->profile) {
+    // profiling: plain launches with a pair of events around every force launch
+    std::vector<cudaEvent_t> evs((size_t)2 * p->max_iter, nullptr);
+    struct EvCleanup {
+      std::vector<cudaEvent_t>& v;
+      ~EvCleanup() {
+        for (cudaEvent_t e : v)
+          if (e) cudaEventDestroy(e);
+      }
+    } evclean{evs};
+    for (auto& e : evs) FGA_CUDA_TRY(cudaEventCreate(&e));
+    for (int it = 0; it < p->max_iter; ++it) {
+      FGA_CUDA_TRY(cudaEventRecord(evs[2 * it], cs));
+      k_batch_force<<<fgrid, BATCH_WARPS * 32, 0, cs>>>(d_pairs, d_tasks, ntasks, d_ctr, eps2, theta2);
+      count_launch();
+      FGA_LAUNCH_CHECK("batch force");
+      FGA_CUDA_TRY(cudaEventRecord(evs[2 * it + 1], cs));
+      k_batch_epilogue<<<(unsigned)blockmap.size(), EPI_BS, 0, cs>>>(d_pairs, d_blockmap);
+      count_launch();
+      FGA_LAUNCH_CHECK("batch epilogue");
+    }
+    FGA_CUDA_TRY(cudaStreamSynchronize(cs));
+    for (int it = 0; it < p->max_iter; ++it) {
+      float ms = 0.f;
+      FGA_CUDA_TRY(cudaEventElapsedTime(&ms, evs[2 * it], evs[2 * it + 1]));
+      prof_ms += ms;
+    }
+    prof_launches = p->max_iter;
+  } else if (p->max_iter > 0) {
+    FGA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int lrc = FGA_OK;
+    for (int it = 0; it < p->max_iter && lrc == FGA_OK; ++it) {
+      k_batch_force<<<fgrid, BATCH_WARPS * 32, 0, cs>>>(d_pairs, d_tasks, ntasks, d_ctr, eps2, theta2);
+      count_launch();
+      if (cudaPeekAtLastError() != cudaSuccess) lrc = FGA_ECUDA;
+      k_batch_epilogue<<<(unsigned)blockmap.size(), EPI_BS, 0, cs>>>(d_pairs, d_blockmap);
+      count_launch();
+      if (cudaPeekAtLastError() != cudaSuccess) lrc = FGA_ECUDA;
+    }
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (lrc != FGA_OK || ce != cudaSuccess) {
+      set_error(std::string("fga_register_batch: graph capture failed: ") +
+                cudaGetErrorString(ce != cudaSuccess ? ce : cudaGetLastError()));
+      return FGA_ECUDA;
+    }
+    FGA_CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
+    FGA_CUDA_TRY(cudaGraphLaunch(exec, cs));
+  }
+  FGA_CUDA_TRY(cudaEventRecord(ev_out, cs));
+  FGA_CUDA_TRY(cudaStreamWaitEvent(s, ev_out, 0));
+  std::vector<DevState> hs(count);
+  std::vector<double> infos((size_t)8 * count);
+  FGA_CUDA_TRY(cudaMemcpyAsync(hs.data(), dsarr, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s));
+  for (int k = 0; k < count; ++k)
+    FGA_CUDA_TRY(cudaMemcpyAsync(&infos[8 * k], prep[k].info, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  FGA_CUDA_TRY(cudaStreamSynchronize(s));
+  const auto t_end = std::chrono::steady_clock::now();
+  int code = FGA_OK;
+  int64_t total = 0;
+  for (int k = 0; k < count; ++k) {
+    const DevState& h = hs[k];
+    fga_pair_result& r = results[k];
+    std::memcpy(r.R, h.R, sizeof(r.R));
+    if (p->normalize)
+      fga_denormalize(h.R, h.t, &infos[8 * k], p->a, r.t);
+    else
+      std::memcpy(r.t, h.t, sizeof(r.t));
+    r.method = host[k].method;
+    r.iterations = h.iter;
+    r.converged = h.done && !(h.status & 2);
+    r.interactions = (int64_t)h.interactions;
+    r.status = h.status ? FGA_EINTERNAL : (h.degenerate ? FGA_EDEGENERATE : FGA_OK);
+    if (r.status == FGA_EINTERNAL) code = FGA_EINTERNAL;
+    else if (r.status == FGA_EDEGENERATE && code == FGA_OK) code = FGA_EDEGENERATE;
+    total += r.interactions;
+  }
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->iterations = p->max_iter;
+    stats->interactions = total;
+    stats->status = code;
+    stats->h2d_bytes = h2d;
+    stats->d2h_bytes = (int64_t)(sizeof(DevState) + 8 * sizeof(double) + 8 * sizeof(int)) * count;
+    stats->elapsed_ms = std::chrono::duration<double, std::milli>(t_end - t0).count();
+    // force time: summed event times of the force launches when profiling,
+    // else the host time of the whole iteration loop
+    stats->force_ms = p->profile ? prof_ms : std::chrono::duration<double, std::milli>(t_end - t_setup).count();
+    stats->force_launches = prof_launches;
+  }
+  if (code == FGA_EINTERNAL) set_error("fga_register_batch: a device check failed in some pair");
+  return code;
+}

@@ -6,6 +6,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "fga.h"
 
@@ -186,5 +187,42 @@ int launch_forces_out(const ForceBuffers& fb, int64_t M, const float4* Y0, int u
                       float G, const int* perm, float* acc_out, cudaStream_t s);
 // Initialise DevState (identity transform, mu0 from d_mu0).
 int launch_state_init(DevState* ds, const double* d_mu0, cudaStream_t s);
+
+// Scope guard for temporary device buffers of one call.
+struct Scratch {
+  cudaStream_t s;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t st) : s(st) {}
+  ~Scratch() {
+    for (void* p : ptrs) dev_free(p, s);
+  }
+  template <class T>
+  int alloc(T** p, size_t n) {
+    int rc = dev_alloc_n(p, n, s);
+    if (rc == FGA_OK) ptrs.push_back(*p);
+    return rc;
+  }
+};
+
+
+// Host helpers of fga_api.cu shared with the batch executor.
+int check_params(const fga_params* p, bool need_tree);
+int check_register_params(const fga_params* p);
+// FGA_AUTO -> FGA_DIRECT or FGA_BH by the reference size (fga_batch.cu).
+int resolve_method(const fga_params* p, int64_t N);
+int read_flags(const int* d_flags, int n, int* h, cudaStream_t s);
+unsigned grid_for(int64_t n);
+bool is_device_ptr(const void* p);
+int pack_template(const float* Y, const float* mY, float m_default, int64_t M, bool sort,
+                  float4* Y0, int* perm, cudaStream_t s);
+struct Prepared {
+  float *Xn = nullptr, *Yn = nullptr, *mXn = nullptr, *mYn = nullptr;
+  double* info = nullptr;
+  int* flags = nullptr;
+};
+int prepare_inputs(Scratch& sc, const float* X, int64_t N, const float* Y, int64_t M,
+                   const float* mX, const float* mY, const fga_params* p, Prepared& out,
+                   int64_t& h2d, cudaStream_t s);
+
 
 }  // namespace fga

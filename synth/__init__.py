@@ -276,3 +276,23 @@ def batch_sizes(seed: int, count: int = 256, lo: int = 500, hi: int = 50_000):
     rng = np.random.default_rng(seed)
     s = np.exp(rng.uniform(math.log(lo), math.log(hi), size=(count, 2)))
     return np.round(s).astype(np.int64)
+
+
+def batch_pairs(seed: int, count: int = 256, lo: int = 500, hi: int = 50_000,
+                max_deg: float = 60.0, t_max: float = 0.3):
+    """``count`` independent pairs with N and M log-uniform in [lo, hi].
+
+    Shapes alternate between unit-sphere clouds and piecewise-planar scenes;
+    each pair has its own rotation (<= max_deg) and translation (<= t_max).
+    Returns a list of (X, Y, R_gt, t_gt).
+    """
+    sizes = batch_sizes(seed, count, lo, hi)
+    out = []
+    for k, (n, m) in enumerate(sizes):
+        if k % 2 == 0:
+            out.append(sphere_pair(seed * 100_003 + k, n=int(n), m=int(m), max_deg=max_deg,
+                                   t_max=t_max))
+        else:
+            out.append(planar_scene_pair(seed * 100_003 + k, n=int(n), m=int(m), max_deg=max_deg,
+                                         t_max=t_max))
+    return out

@@ -1,0 +1,105 @@
+"""Batched registration (many pairs in one graph-captured loop) against the
+single-pair path and the FP64 oracle (needs a GPU)."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fga():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2009_14005_gb300 as m
+    return m
+
+
+def _cuda(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+def _close(R1, t1, R2, t2, X, tol_deg=0.01, tol_t=1e-4):
+    import oracle
+    diag = np.linalg.norm(X.max(0) - X.min(0))
+    return (oracle.rotation_error_deg(R1, R2) <= tol_deg
+            and np.linalg.norm(np.asarray(t1) - np.asarray(t2)) <= tol_t * diag)
+
+
+@pytest.fixture(scope="module")
+def mix():
+    return synth.batch_pairs(7, count=10, lo=300, hi=6000)
+
+
+def test_batch_matches_single_pair_path(fga, mix):
+    old = fga.fga_direct_max_n(2500)
+    try:
+        p = fga.params(method=fga.FGA_AUTO, max_iter=40, theta=0.5)
+        res, st = fga.fga_register_batch([(_cuda(X), _cuda(Y)) for X, Y, _, _ in mix], p)
+        assert st["status"] == fga.FGA_OK
+        assert {r["method"] for r in res} == {fga.FGA_DIRECT, fga.FGA_BH}
+        for (X, Y, _, _), r in zip(mix, res):
+            assert r["method"] == (fga.FGA_DIRECT if len(X) <= 2500 else fga.FGA_BH)
+            R, t, s1 = fga.fga_register(_cuda(X), _cuda(Y), fga.params(method=r["method"], max_iter=40,
+                                                                        theta=0.5))
+            assert _close(r["R"], r["t"], R, t, X)
+            assert r["iterations"] == 40
+            if r["method"] == fga.FGA_BH:
+                assert r["interactions"] == s1["interactions"]
+            else:
+                assert r["interactions"] == 40 * len(X) * len(Y)
+        assert st["interactions"] == sum(r["interactions"] for r in res)
+    finally:
+        fga.fga_direct_max_n(old)
+
+
+def test_batch_matches_oracle(fga, orc, mix):
+    old = fga.fga_direct_max_n(2500)
+    try:
+        sub = mix[:4]
+        p = fga.params(method=fga.FGA_AUTO, max_iter=30, theta=0.5)
+        res, _ = fga.fga_register_batch([(X, Y) for X, Y, _, _ in sub], p)  # host inputs
+        for (X, Y, _, _), r in zip(sub, res):
+            po = orc.Params(method=orc.FGA_DIRECT if r["method"] == fga.FGA_DIRECT else orc.FGA_BH,
+                            theta=0.5, max_iter=30)
+            o = orc.register_full(X, Y, po)
+            assert _close(r["R"], r["t"], o["R"], o["t"], X)
+    finally:
+        fga.fga_direct_max_n(old)
+
+
+def test_same_alone_and_in_the_mix(fga, mix):
+    p = fga.params(method=fga.FGA_AUTO, max_iter=25, theta=0.5)
+    pairs = [(_cuda(X), _cuda(Y)) for X, Y, _, _ in mix]
+    res_mix, _ = fga.fga_register_batch(pairs, p)
+    for k in [0, 3, 7]:
+        alone, _ = fga.fga_register_batch([pairs[k]], p)
+        assert np.array_equal(alone[0]["R"], res_mix[k]["R"])
+        assert np.array_equal(alone[0]["t"], res_mix[k]["t"])
+        assert alone[0]["interactions"] == res_mix[k]["interactions"]
+
+
+def test_per_pair_early_exit(fga):
+    pairs = [synth.box_pair(s, 400, deg) for s, deg in [(0, 5.0), (1, 15.0), (2, 30.0)]]
+    p = fga.params(method=fga.FGA_DIRECT, max_iter=300, conv_tol=1e-6)
+    res, _ = fga.fga_register_batch([(_cuda(X), _cuda(Y)) for X, Y, _, _ in pairs], p)
+    for (X, Y, R_gt, t_gt), r in zip(pairs, res):
+        R, t, s1 = fga.fga_register(_cuda(X), _cuda(Y), p)
+        assert r["converged"] and s1["converged"]
+        assert abs(r["iterations"] - s1["iterations"]) <= 1
+        assert r["interactions"] == r["iterations"] * len(X) * len(Y)
+    assert len({r["iterations"] for r in res}) > 1
+
+
+def test_bad_pair_is_rejected(fga, mix):
+    X, Y, _, _ = mix[0]
+    bad = Y.copy()
+    bad[5, 2] = np.inf
+    with pytest.raises(fga.FGAError) as e:
+        fga.fga_register_batch([(X, Y), (X, bad)], fga.params(max_iter=3))
+    assert e.value.code == fga.FGA_EINVAL and "pair 1" in str(e.value)
