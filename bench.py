@@ -196,6 +196,10 @@ WORKLOADS = {
     # one graph-captured loop per step; n = number of pairs
     "batch": dict(gen="batch", n=256, iters=100, method="auto", theta=0.5, niv=False,
                   G=66.7, eps=0.2, eta=0.2),
+    # served requests: Poisson arrivals at 200/s, N and M log-uniform in
+    # [1k, 500k], overlap 30-100 %; one step = one request of the trace
+    "serve": dict(gen="serve", n=500_000, iters=100, method="auto", theta=0.5, niv=False,
+                  G=66.7, eps=0.2, eta=0.2, rate=200.0, lo=1000),
 }
 
 
@@ -210,19 +214,13 @@ def workload(a):
 
 def workload_config(a):
     w = workload(a)
+    if w["gen"] in ("batch", "serve"):
+        return special_config(a, w)
     name = "%s-%dk-%s%s-%dit" % (
         {"lidar": "lidar-sweeps", "sphere": "unit-sphere", "planar": "planar-scene",
          "batch": "batch"}[w["gen"]],
         max(w["n"] // 1000, 1), "bh-theta%.1f" % w["theta"] if w["method"] == "bh" else "direct",
         "", w["iters"])
-    if w["gen"] == "batch":
-        return {"workload": "batch-%d-pairs-500-50k-%dit" % (w["n"], w["iters"]), "pairs": w["n"],
-                "N_M": "log-uniform in [500, 50000], independently", "iterations": w["iters"],
-                "method": "per pair: all-pairs if N <= 32768 else barnes-hut (theta %.1f)" % w["theta"],
-                "masses": "uniform", "eps": w["eps"], "eta": w["eta"], "dt": 0.1, "G": w["G"],
-                "pairs_per_rank": a.pairs,
-                "l2": "flushed between steps (256 MB device write outside the timed events)",
-                "inputs": "resident in HBM at the start of each timed step"}
     return {"workload": name, "N": w["n"], "M": w["n"], "iterations": w["iters"],
             "method": "barnes-hut" if w["method"] == "bh" else "all-pairs",
             "theta": w["theta"] if w["method"] == "bh" else None,
@@ -232,10 +230,37 @@ def workload_config(a):
             "inputs": "resident in HBM at the start of each timed step"}
 
 
+def special_config(a, w):
+    if w["gen"] == "serve":
+        return {"workload": "serve-poisson%d-%dk-%dk-%dit" % (w["rate"], w["lo"] // 1000, w["n"] // 1000,
+                                                                w["iters"]),
+                "requests": a.steps, "arrival_rate_per_s": w["rate"],
+                "N_M": "log-uniform in [%d, %d], independently" % (w["lo"], w["n"]),
+                "overlap": "uniform in [0.3, 1.0] (cropped piecewise-planar scenes)",
+                "iterations": w["iters"],
+                "method": "per pair: all-pairs if N <= 32768 else barnes-hut (theta %.1f)" % w["theta"],
+                "masses": "uniform", "eps": w["eps"], "eta": w["eta"], "dt": 0.1, "G": w["G"],
+                "timing": "host clock: first arrival to last result; latency = submit to result on host",
+                "l2": "not flushed: the trace's inputs (hundreds of MB) exceed L2",
+                "inputs": "device-resident at submit (value); pinned host (e2e)"}
+    if w["gen"] == "batch":
+        return {"workload": "batch-%d-pairs-500-50k-%dit" % (w["n"], w["iters"]), "pairs": w["n"],
+                "N_M": "log-uniform in [500, 50000], independently", "iterations": w["iters"],
+                "method": "per pair: all-pairs if N <= 32768 else barnes-hut (theta %.1f)" % w["theta"],
+                "masses": "uniform", "eps": w["eps"], "eta": w["eta"], "dt": 0.1, "G": w["G"],
+                "pairs_per_rank": a.pairs,
+                "l2": "flushed between steps (256 MB device write outside the timed events)",
+                "inputs": "resident in HBM at the start of each timed step"}
+    raise ValueError(w["gen"])
+
+
 def make_pairs(seeds, a):
     w = workload(a)
     if w["gen"] == "batch":
         return [synth.batch_pairs(s, count=w["n"]) for s in seeds]
+    if w["gen"] == "serve":
+        tr = synth.serve_trace(seeds[0], max(a.steps, 1), rate=w["rate"], lo=w["lo"], hi=w["n"])
+        return [[(X, Y, R, t) for _, X, Y, R, t in tr]]
     gen = {"lidar": synth.lidar_pair, "sphere": synth.sphere_pair,
            "planar": synth.planar_scene_pair}[w["gen"]]
     return [gen(s, n=w["n"]) for s in seeds]
@@ -257,7 +282,7 @@ def cpu_sample(pair, a, iters):
     import oracle
     oracle.build()
     w = workload(a)
-    if w["gen"] == "batch":
+    if w["gen"] in ("batch", "serve"):
         pair = pair[0]
         w = dict(w, method="direct" if len(pair[0]) <= 32768 else "bh")
     X, Y, _, _ = pair
@@ -534,12 +559,157 @@ def run_ours_batch(a):
     return 0
 
 
+def replay_served(fga, p, trace, inputs, warm):
+    """Replays a request trace through a server in real time; returns
+    (results, wall seconds from the first arrival to the last result)."""
+    with fga.Server(p, iters_per_tick=4) as srv:
+        for X, Y in warm:
+            srv.submit(X, Y)
+        srv.drain()
+        results = []
+        t0 = time.perf_counter()
+        for (t_arr, *_), (X, Y) in zip(trace, inputs):
+            while time.perf_counter() - t0 < t_arr:
+                results.extend(srv.poll(256, wait_ms=1))
+            srv.submit(X, Y)
+            results.extend(srv.poll(256, wait_ms=0))
+        results.extend(srv.drain())
+        wall = time.perf_counter() - t0
+        st = srv.stats()
+    return results, wall, st
+
+
+def replay_one_pair(fga, p, trace, inputs, stream):
+    """The same trace through the one-pair path: FIFO, one fga_register call
+    per request. Returns (latencies ms, wall seconds, interactions)."""
+    lat, inter = [], 0
+    t0 = time.perf_counter()
+    for (t_arr, *_), (X, Y) in zip(trace, inputs):
+        while time.perf_counter() - t0 < t_arr:
+            time.sleep(0.0002)
+        R, t, st = fga.fga_register(X, Y, p, stream=stream)
+        inter += st["interactions"]
+        lat.append(1e3 * (time.perf_counter() - t0 - t_arr))
+    return lat, time.perf_counter() - t0, inter
+
+
+def run_ours_serve(a):
+    """One step = one request of a Poisson trace replayed through the server."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2009_14005_gb300 as fga
+
+    w = workload(a)
+    trace = synth.serve_trace(shard_seeds(rank, world, 1)[0], a.steps + a.warmup, rate=w["rate"],
+                              lo=w["lo"], hi=w["n"])
+    warm_tr, trace = trace[:a.warmup], trace[a.warmup:]
+    t_first = trace[0][0]
+    trace = [(t - t_first, X, Y, R, tt) for t, X, Y, R, tt in trace]
+    dev = [(torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda")) for _, X, Y, _, _ in trace]
+    warm = [(torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda")) for _, X, Y, _, _ in warm_tr]
+    host = [(torch.from_numpy(X).pin_memory(), torch.from_numpy(Y).pin_memory()) for _, X, Y, _, _ in trace]
+    torch.cuda.synchronize()
+    p = lib_params(fga, a)
+    p.profile = 0
+    stream = torch.cuda.current_stream()
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    clocks.start()
+    launches0 = fga.fga_launch_count()
+    res, wall, sst = replay_served(fga, p, trace, dev, warm)
+    launches = fga.fga_launch_count() - launches0
+    clk = clocks.stop()
+    ok = [r for r in res if r["status"] in (fga.FGA_OK, fga.FGA_EDEGENERATE)]
+    lat = [r["done_ms"] - r["submit_ms"] for r in ok]
+    inter = sum(r["interactions"] for r in ok)
+    t_max, inter_all = reduce_max_sum(1e3 * wall, float(inter), world)
+    _, regs_all = reduce_max_sum(1e3 * wall, float(len(ok)), world)
+    value = inter_all / (t_max / 1e3)
+
+    # e2e: the same trace with pinned host inputs (copies inside the server)
+    res_h, wall_h, _ = replay_served(fga, p, trace, host, warm)
+    inter_h = sum(r["interactions"] for r in res_h)
+    e2e_tmax, e2e_iall = reduce_max_sum(1e3 * wall_h, float(inter_h), world)
+    h2d = sum(4 * (X.numel() + Y.numel()) for X, Y in host) // max(len(host), 1)
+
+    # the one-pair-per-launch path on the same trace
+    base_lat, base_wall, base_inter = replay_one_pair(fga, p, trace, dev, stream)
+
+    # the dominant kernel timed alone: one profiled batch of the trace's first pairs
+    pp = lib_params(fga, a)
+    pp.profile = 1
+    sample = dev[:min(32, len(dev))]
+    _, pst = fga.fga_register_batch(sample, pp, stream=stream)
+    torch.cuda.synchronize()
+
+    if rank != 0:
+        return 0
+    peaks, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_rate = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / FP32_INSTR_PER_INTERACTION
+    launch_inter = pst["interactions"] / max(pst["force_launches"], 1)
+    launch_s = pst["force_ms"] / 1e3 / max(pst["force_launches"], 1)
+    achieved = launch_inter / launch_s if launch_s > 0 else 0.0
+    roof = {"bound": "alu", "kernel": "k_batch_force", "achieved": achieved / 1e9,
+            "peak": peak_rate / 1e9, "unit": "Ginteractions/s", "frac": achieved / peak_rate,
+            "traffic": recorded_traffic("paper_2009_14005_gb300/csrc/fga_batch.cu",
+                                        "k_batch_force_%s.md" % a.workload),
+            "peak_source": "%d SMs x %d FP32 lanes x %.0f MHz (sm_max_mhz, %s) / %d FP32 "
+                           "instructions per interaction" % (sms, FP32_LANES_PER_SM, sm_mhz, peak_src,
+                                                             FP32_INSTR_PER_INTERACTION),
+            "launches": pst["force_launches"], "interactions_per_launch": launch_inter,
+            "mean_launch_ms": 1e3 * launch_s,
+            "measured_on": "fga_register_batch of the trace's first %d pairs, events around each "
+                           "force launch" % len(sample)}
+    line = {"metric": "pair-interactions/s", "value": value, "unit": "interactions/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(a),
+            "registrations_per_s": regs_all / (t_max / 1e3),
+            "p50_ms": float(np.percentile(lat, 50)) if lat else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat else None,
+            "failed": len(res) - len(ok),
+            "server": {k: sst[k] for k in ("ticks", "pair_iterations", "busy_ms")},
+            "one_pair_path": {"registrations_per_s": len(trace) / base_wall,
+                              "interactions_per_s": base_inter / base_wall,
+                              "p50_ms": float(np.percentile(base_lat, 50)),
+                              "p99_ms": float(np.percentile(base_lat, 99)),
+                              "note": "same trace, FIFO, one fga_register call per request"},
+            "e2e": {"value": e2e_iall / (e2e_tmax / 1e3) if e2e_tmax > 0 else None,
+                    "unit": "interactions/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": 8 * 12 + 64,
+                    "ms_per_step": e2e_tmax / max(a.steps, 1),
+                    "p50_ms": float(np.percentile([r["done_ms"] - r["submit_ms"] for r in res_h], 50)),
+                    "p99_ms": float(np.percentile([r["done_ms"] - r["submit_ms"] for r in res_h], 99))},
+            "gpu_launches": launches, "roofline": roof, "clocks": clk}
+    if world == 1 and not a.no_cpu_baseline:
+        X, Y = trace[0][1], trace[0][2]
+        i, t, cores = cpu_sample([(X, Y, None, None)], a, a.cpu_iters)
+        line["cpu_baseline"] = {"value": i / t, "unit": "interactions/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": "FP64 C oracle (OpenMP), normalisation + tree + %d of %d "
+                                          "iterations on the trace's first request (%d x %d, %.1f s)"
+                                          % (a.cpu_iters, w["iters"], len(X), len(Y), t)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     a = parse_args(argv)
     if a.impl == "reference":
         return run_reference(a)
     if workload(a)["gen"] == "batch":
         return run_ours_batch(a)
+    if workload(a)["gen"] == "serve":
+        return run_ours_serve(a)
     return run_ours(a)
 
 

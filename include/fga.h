@@ -295,6 +295,82 @@ int fga_register_batch(const fga_pair* pairs, int count, const fga_params* p,
  * and, if new_value > 0, sets it (process-wide). */
 int64_t fga_direct_max_n(int64_t new_value);
 
+/* ------------------------------------------------------------------ serving
+ * A registration server: a continuous-batching engine on one GPU. Requests
+ * (pairs, Algorithm 2 with the server's parameters) are submitted at any
+ * time. An admission thread prepares each request on its own stream as soon
+ * as the pair fits in the device-memory budget and a slot is free (FIFO:
+ * a request waits for all requests submitted before it). The prepared pair
+ * (normalised template, velocities, tree or packed reference, state) stays
+ * resident on the device. A runner thread advances all resident pairs
+ * together, `iters_per_tick` iterations of every pair per tick (the batch
+ * kernels of fga_register_batch), and between ticks adds newly prepared
+ * pairs and retires the ones whose iteration limit or stop test was reached,
+ * so pairs that arrive while others run join them on the device. Each pair
+ * stops after exactly p->max_iter iterations (or when its stop test fires);
+ * its result is the same whichever pairs it shared the device with.
+ * Thread safety: submit, poll and stats may be called from any threads. */
+typedef struct fga_server fga_server;
+
+typedef struct fga_server_config {
+  int64_t mem_budget;  /* device bytes resident and in-preparation pairs may hold
+                          (an upper bound per pair is charged); <= 0: 3/4 of the
+                          device memory free at creation                        */
+  int max_pairs;       /* resident pairs at most; <= 0: 4096                      */
+  int iters_per_tick;  /* iterations per tick; <= 0: 4                            */
+  int device;          /* CUDA device; < 0: the calling thread's current device  */
+} fga_server_config;
+
+typedef struct fga_served {
+  int64_t ticket;           /* as returned by fga_server_submit                   */
+  fga_pair_result result;   /* R, t (original frames), method, iterations, ...     */
+  double submit_ms;         /* host clock, ms since the server was created        */
+  double admit_ms;          /* preparation started (memory and slot granted)      */
+  double start_ms;          /* first tick that ran the pair                       */
+  double done_ms;           /* result available to fga_server_poll                */
+  char error[160];          /* message when result.status is an error, else ""    */
+} fga_served;
+
+typedef struct fga_server_stats {
+  int64_t submitted, completed, failed;
+  int pending;              /* waiting for admission                               */
+  int preparing;            /* being prepared                                      */
+  int resident;             /* on the device, iterating                            */
+  int64_t bytes_charged;    /* sum of the bounds of admitted pairs                 */
+  int64_t mem_budget;
+  int64_t ticks;            /* ticks run                                           */
+  int64_t pair_iterations;  /* sum over ticks of resident pairs x iterations       */
+  double busy_ms;           /* host time the runner spent with pairs resident      */
+} fga_server_stats;
+
+/* Creates a server with parameters *p (copied; p->method may be FGA_AUTO) and
+ * configuration *cfg (NULL: all defaults). Starts its two threads.
+ * Errors: FGA_EINVAL (bad parameters), FGA_ECUDA, FGA_ENOMEM. */
+int fga_server_create(const fga_params* p, const fga_server_config* cfg, fga_server** out);
+
+/* Queues one request and returns its ticket (> 0) in *ticket. X, Y, mX, mY
+ * may be host or device pointers; they are read during preparation (on the
+ * server's own stream, so device data must be complete when submitted) and
+ * must stay valid until the request's result has been polled. Never waits
+ * for the GPU. Errors: FGA_EINVAL (null pointers, sizes outside 1..2^26, a pair
+ * larger than the whole memory budget, server stopping). Bad point values
+ * (NaN, zero extent) are reported in the request's result instead. */
+int fga_server_submit(fga_server* srv, const fga_pair* req, int64_t* ticket);
+
+/* Moves up to `max` finished requests (in completion order) into out[] and
+ * their number into *n. If none is ready, waits up to wait_ms milliseconds
+ * (0: return at once; < 0: until one is ready or nothing is outstanding). */
+int fga_server_poll(fga_server* srv, fga_served* out, int max, int* n, int wait_ms);
+
+/* Counters of the server (consistent snapshot). */
+int fga_server_stats_get(fga_server* srv, fga_server_stats* out);
+
+/* Stops the server: pending requests are dropped, the runner stops after the
+ * tick it is running (pairs still resident are dropped unfinished), both
+ * threads are joined and all device memory of the server is freed. Results
+ * not yet polled are dropped. */
+int fga_server_destroy(fga_server* srv);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,6 +50,8 @@ SYMBOLS = [
     "fga_tree_node_count", "fga_tree_export", "fga_forces", "fga_state_create", "fga_step",
     "fga_state_get", "fga_state_trajectory", "fga_state_destroy", "fga_register",
     "fga_forces_direct_static", "fga_register_batch", "fga_direct_max_n",
+    "fga_server_create", "fga_server_submit", "fga_server_poll", "fga_server_stats_get",
+    "fga_server_destroy",
 ]
 FGA_STATIC_SCRATCH_FLOAT4 = 524288
 
@@ -96,6 +98,29 @@ class fga_pair_result(ctypes.Structure):
                 ("interactions", ctypes.c_int64)]
 
 
+class fga_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_int64), ("max_pairs", ctypes.c_int),
+                ("iters_per_tick", ctypes.c_int), ("device", ctypes.c_int)]
+
+
+class fga_served(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_int64), ("result", fga_pair_result),
+                ("submit_ms", ctypes.c_double), ("admit_ms", ctypes.c_double),
+                ("start_ms", ctypes.c_double), ("done_ms", ctypes.c_double),
+                ("error", ctypes.c_char * 160)]
+
+
+class fga_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("pending", ctypes.c_int), ("preparing", ctypes.c_int),
+                ("resident", ctypes.c_int), ("bytes_charged", ctypes.c_int64),
+                ("mem_budget", ctypes.c_int64), ("ticks", ctypes.c_int64),
+                ("pair_iterations", ctypes.c_int64), ("busy_ms", ctypes.c_double)]
+
+    def to_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class FGAError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("libfga error %d: %s" % (code, msg))
@@ -135,6 +160,13 @@ def _load():
                                               ctypes.POINTER(fga_pair_result),
                                               ctypes.POINTER(fga_stats), VP]),
         "fga_direct_max_n": (I64, [I64]),
+        "fga_server_create": (ctypes.c_int, [PP, ctypes.POINTER(fga_server_config),
+                                             ctypes.POINTER(ctypes.c_void_p)]),
+        "fga_server_submit": (ctypes.c_int, [P, ctypes.POINTER(fga_pair), ctypes.POINTER(I64)]),
+        "fga_server_poll": (ctypes.c_int, [P, ctypes.POINTER(fga_served), ctypes.c_int,
+                                           ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
+        "fga_server_stats_get": (ctypes.c_int, [P, ctypes.POINTER(fga_server_stats)]),
+        "fga_server_destroy": (ctypes.c_int, [P]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -476,3 +508,95 @@ def fga_register_batch(pairs, p: fga_params | None = None, stream=None):
     d["status"] = code
     return out, d
 
+
+def _served_dict(o: fga_served) -> dict:
+    r = o.result
+    return dict(ticket=int(o.ticket), R=np.array(r.R[:]).reshape(3, 3), t=np.array(r.t[:]),
+                method=r.method, iterations=r.iterations, converged=bool(r.converged),
+                status=r.status, interactions=int(r.interactions), submit_ms=o.submit_ms,
+                admit_ms=o.admit_ms, start_ms=o.start_ms, done_ms=o.done_ms,
+                error=o.error.decode(errors="replace"))
+
+
+class Server:
+    """Registration server (``fga_server_*``): continuous batching on one GPU.
+
+    ``submit(X, Y, mX=None, mY=None)`` returns a ticket; the arrays (CUDA
+    tensors or host arrays) are held until the request's result is polled.
+    ``poll(max=256, wait_ms=0)`` returns finished requests as dicts (ticket,
+    R, t, method, iterations, converged, status, interactions, and the host
+    times submit_ms, admit_ms, start_ms, done_ms in ms since creation)."""
+
+    def __init__(self, p: fga_params | None = None, mem_budget: int = 0, max_pairs: int = 0,
+                 iters_per_tick: int = 0, device: int = -1):
+        self._h = ctypes.c_void_p()
+        cfg = fga_server_config(int(mem_budget), int(max_pairs), int(iters_per_tick), int(device))
+        _err(lib.fga_server_create(ctypes.byref(p or params()), ctypes.byref(cfg), ctypes.byref(self._h)))
+        self._keep = {}
+
+    def submit(self, X, Y, mX=None, mY=None) -> int:
+        torch = _torch()
+        held = []
+
+        def arr(a, cols):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                t = _dev(a, cols) if a.is_cuda else a.to(torch.float32).contiguous()
+            else:
+                t = torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32)))
+            held.append(t)
+            return t
+
+        Xt, Yt, mXt, mYt = arr(X, 3), arr(Y, 3), arr(mX, None), arr(mY, None)
+        if any(t.is_cuda for t in held):
+            # the server reads device inputs on its own stream: they must be complete
+            torch.cuda.current_stream(Xt.device if Xt.is_cuda else Yt.device).synchronize()
+        q = fga_pair(Xt.data_ptr(), Xt.shape[0], Yt.data_ptr(), Yt.shape[0],
+                     mXt.data_ptr() if mXt is not None else None,
+                     mYt.data_ptr() if mYt is not None else None)
+        ticket = ctypes.c_int64()
+        _err(lib.fga_server_submit(self._h, ctypes.byref(q), ctypes.byref(ticket)))
+        self._keep[int(ticket.value)] = held
+        return int(ticket.value)
+
+    def poll(self, max: int = 256, wait_ms: int = 0) -> list:
+        out = (fga_served * max)()
+        n = ctypes.c_int()
+        _err(lib.fga_server_poll(self._h, out, max, ctypes.byref(n), int(wait_ms)))
+        res = [_served_dict(out[k]) for k in range(n.value)]
+        for r in res:
+            self._keep.pop(r["ticket"], None)
+        return res
+
+    def drain(self, wait_ms: int = -1) -> list:
+        """All results of the requests submitted so far (waits for them)."""
+        res = []
+        while True:
+            got = self.poll(256, wait_ms)
+            if not got:
+                return res
+            res.extend(got)
+
+    def stats(self) -> dict:
+        st = fga_server_stats()
+        _err(lib.fga_server_stats_get(self._h, ctypes.byref(st)))
+        return st.to_dict()
+
+    def close(self):
+        if self._h:
+            lib.fga_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

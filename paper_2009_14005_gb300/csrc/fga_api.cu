@@ -44,6 +44,11 @@ static cudaMemPool_t pool_for(int dev) {
   }
   uint64_t keep = UINT64_MAX;  // keep freed blocks cached for the next call
   cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  // a block freed on one stream is reused by another only once the free has
+  // completed, never by making the other stream wait (the serving engine
+  // prepares pairs on one stream while another runs)
+  int no = 0;
+  cudaMemPoolSetAttribute(pool, cudaMemPoolReuseAllowInternalDependencies, &no);
   g_pools[dev] = pool;
   return pool;
 }
@@ -603,7 +608,7 @@ int fga_state_get(fga_state* st, double R[9], double t[3], fga_stats* stats, voi
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->iterations = h.iter;
-    stats->converged = h.done && !(h.status & 2);
+    stats->converged = h.converged;
     stats->degenerate_fits = h.degenerate;
     stats->interactions = (int64_t)h.interactions;
     stats->last_conv = h.last_conv;

@@ -2,51 +2,45 @@
 // together, one iteration of Algorithm 2 for all of them per pair of launches,
 // and the whole loop is captured in one CUDA graph.
 //
-// Force launch: a static list of warp tasks covers every pair; warps take
-// tasks from a device counter. A Barnes-Hut task is (pair, 32 template points,
+// Force launch: the warp tasks of all pairs are numbered consecutively, pair
+// by pair (a prefix sum over the pairs maps a task to its pair by binary
+// search); warps take tasks from a device counter. A Barnes-Hut task is (pair, 32 template points,
 // frontier cell) and runs the same per-lane BHForce walk as the single-pair
 // kernel. An all-pairs task is (pair, 32 template points, chunk of up to
 // BATCH_CHUNK reference points): the warp stages 32 sources at a time in
 // shared memory and every lane adds them to its own point (Eq. 6).
-// Epilogue launch: blocks are assigned to pairs; each pair's blocks run the
+// Epilogue launch: blocks are assigned to pairs the same way; each pair's blocks run the
 // ODE step and reductions, and the pair's last block runs its rigid fit, so
 // the rigid fits of all pairs run in parallel. A pair whose convergence test
 // has fired skips its tasks and blocks.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstring>
 #include <vector>
 
+#include "fga_batch.cuh"
 #include "fga_device.cuh"
 
 namespace fga {
 
-constexpr int BATCH_CHUNK = 2048;  // reference points per all-pairs task
-constexpr int BATCH_WARPS = 4;
-
-struct PairDev {
-  int method;                 // FGA_DIRECT or FGA_BH
-  int K;                      // BH: frontier cells; direct: source chunks
-  const float4* rec;          // BH: interleaved cell records
-  const float4* bodies;       // BH: bodies in Morton order
-  const FrontCell* front;     // BH: frontier
-  const float4* X4;           // direct: reference points and masses
-  int64_t N, M;
-  const float4* Y0;           // template points and masses
-  DevState* ds;
-  float4* hi;                 // K x M compensated partial sums
-  float4* lo;
-  float4* V;
-  double* partials;           // nblk x NRED
-  unsigned* counter;          // epilogue blocks finished
-  int nblk;                   // epilogue blocks of this pair
-  EpiParams ep;
-  unsigned long long inter_add;  // direct: N*M terms per iteration
-};
+// The k with start[k] <= x < start[k + 1], for start[0] <= x < start[n].
+__device__ __forceinline__ int owner_of(const unsigned* __restrict__ start, int n, unsigned x) {
+  int lo = 0, hi = n;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (start[mid] <= x)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
 
 __global__ void __launch_bounds__(BATCH_WARPS * 32, 8) k_batch_force(const PairDev* __restrict__ pairs,
-                                                                     const int4* __restrict__ tasks,
+                                                                     int npairs,
+                                                                     const unsigned* __restrict__ task_start,
                                                                      unsigned ntasks, unsigned* ctr,
                                                                      float eps2, float theta2) {
   __shared__ unsigned s_stack[BATCH_WARPS][BH_DEPTH][32];
@@ -59,18 +53,20 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, 8) k_batch_force(const PairD
     if (lane == 0) task = atomicAdd(&ctr[0], 1u);
     task = __shfl_sync(FULL, task, 0);
     if (task >= ntasks) break;
-    const int4 t = tasks[task];
-    const PairDev& P = pairs[t.x];
+    const int k = owner_of(task_start, npairs, task);
+    const PairDev& P = pairs[k];
     DevState* ds = P.ds;
     if (ds->done) continue;
     const int64_t M = P.M;
-    const int64_t i = (int64_t)t.y * 32 + lane;
+    const unsigned local = task - task_start[k];
+    const unsigned grp = local / (unsigned)P.K;
+    const int64_t i = (int64_t)grp * 32 + lane;
     const bool valid = i < M;
     const Xf xf = load_xf(ds);
     const float3 y = place(xf, P.Y0[valid ? i : 0]);
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
     unsigned count = 0;
-    const unsigned f = (unsigned)t.z;
+    const unsigned f = local - grp * (unsigned)P.K;
     if (P.method == FGA_BH) {
       bh_task(P.rec, P.bodies, P.front, f, y, valid, eps2, theta2, stk, overflow, hx, hy, hz, lx, ly,
               lz, count);
@@ -124,11 +120,12 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, 8) k_batch_force(const PairD
   }
 }
 
-// blockmap[b] = (pair, block index within the pair)
-__global__ void __launch_bounds__(EPI_BS) k_batch_epilogue(const PairDev* __restrict__ pairs,
-                                                           const int2* __restrict__ blockmap) {
-  const int2 bm = blockmap[blockIdx.x];
-  const PairDev& P = pairs[bm.x];
+// Block b belongs to pair k with block_start[k] <= b < block_start[k + 1].
+__global__ void __launch_bounds__(EPI_BS) k_batch_epilogue(const PairDev* __restrict__ pairs, int npairs,
+                                                           const unsigned* __restrict__ block_start) {
+  const int k = owner_of(block_start, npairs, blockIdx.x);
+  const int2 bm = make_int2(k, (int)(blockIdx.x - block_start[k]));
+  const PairDev& P = pairs[k];
   DevState* ds = P.ds;
   if (ds->done) return;
   __shared__ bool s_last;
@@ -156,7 +153,12 @@ __global__ void __launch_bounds__(EPI_BS) k_batch_epilogue(const PairDev* __rest
   }
 }
 
-static int64_t g_direct_max_n = 32768;  // FGA_AUTO: all-pairs sum when N <= this
+__global__ void k_done_flags(const PairDev* __restrict__ pairs, int n, int* __restrict__ out) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = pairs[k].ds->done;
+}
+
+static std::atomic<int64_t> g_direct_max_n{32768};  // FGA_AUTO: all-pairs sum when N <= this
 
 int resolve_method(const fga_params* p, int64_t N) {
   if (p->method != FGA_AUTO) return p->method;
@@ -172,14 +174,146 @@ static int occupancy_grid(const void* kernel, int threads, int64_t want) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)b * sm_count()));
 }
 
+int batch_force_grid(unsigned ntasks) {
+  return occupancy_grid((const void*)k_batch_force, BATCH_WARPS * 32,
+                        ((int64_t)ntasks + BATCH_WARPS - 1) / BATCH_WARPS);
+}
+
+int launch_batch_iteration(const PairDev* d_pairs, int npairs, const unsigned* d_task_start,
+                           unsigned ntasks, const unsigned* d_block_start, unsigned nblocks,
+                           unsigned* d_ctr, float eps2, float theta2, int fgrid, cudaStream_t s) {
+  if (npairs <= 0) return FGA_OK;
+  if (ntasks > 0) {
+    k_batch_force<<<fgrid, BATCH_WARPS * 32, 0, s>>>(d_pairs, npairs, d_task_start, ntasks, d_ctr, eps2,
+                                                     theta2);
+    FGA_LAUNCH_CHECK("batch force");
+  }
+  if (nblocks > 0) {
+    k_batch_epilogue<<<nblocks, EPI_BS, 0, s>>>(d_pairs, npairs, d_block_start);
+    FGA_LAUNCH_CHECK("batch epilogue");
+  }
+  return FGA_OK;
+}
+
+int launch_done_flags(const PairDev* d_pairs, int n, int* d_out, cudaStream_t s) {
+  if (n <= 0) return FGA_OK;
+  k_done_flags<<<(n + 127) / 128, 128, 0, s>>>(d_pairs, n, d_out);
+  FGA_LAUNCH_CHECK("done flags");
+  return FGA_OK;
+}
+
+int check_pair_flags(const int* f, const char* who, int64_t k) {
+  if (f[0] || f[1] || f[2] || f[3] || !f[4]) {
+    set_error(std::string(who) + ": pair " + std::to_string(k) +
+              (f[4] ? " has a non-finite coordinate or a bad mass"
+                    : " is degenerate (all centred coordinates equal)"));
+    return FGA_EINVAL;
+  }
+  return FGA_OK;
+}
+
+int64_t pair_bytes_bound(int64_t N, int64_t M, int method, const fga_params* p) {
+  const int64_t f4 = 16, pad = 4096;
+  // preparation: staged inputs, normalised copies, masses (freed after setup)
+  int64_t prep = 2 * (12 * (N + M)) + 4 * (N + M) + 8 * pad;
+  int64_t keep = 3 * f4 * M + 8 * (int64_t)epilogue_blocks(M) * NRED + (int64_t)sizeof(DevState) + 8 * pad;
+  if (method == FGA_BH) {
+    // tree: bodies, index, keys, node arrays (<= 2N nodes), records, sort scratch
+    const int64_t nodes = 2 * N + 64;
+    int64_t tree = f4 * N + 4 * N + 8 * N + nodes * (f4 + 16 + 2 * f4) + 2 * 16 * N +
+                   (int64_t)FRONT_TARGET * (int64_t)sizeof(FrontCell) + 32 * pad;
+    keep += tree + 4 * M + 2 * f4 * (int64_t)FRONT_TARGET * M;
+  } else {
+    const int64_t K = (N + BATCH_CHUNK - 1) / BATCH_CHUNK;
+    keep += f4 * N + 2 * f4 * K * M;
+  }
+  (void)p;
+  return prep + keep;
+}
+
+int build_pair(const fga_pair& q, const Prepared& pr, const fga_params* p, Scratch& sc,
+               fga_tree** tree, DevState* ds, PairDev& P, cudaStream_t s) {
+  int rc = 0;
+  *tree = nullptr;
+  std::memset(&P, 0, sizeof(P));
+  P.method = resolve_method(p, q.N);
+  P.N = q.N;
+  P.M = q.M;
+  float4* Y0 = nullptr;
+  if (sc.alloc(&Y0, q.M)) return FGA_ENOMEM;
+  if (P.method == FGA_BH) {
+    fga_tree* t = nullptr;
+    if ((rc = tree_build(pr.Xn, pr.mXn, q.N, p->max_depth, &t, s))) return rc;
+    *tree = t;
+    int* perm = nullptr;
+    if (sc.alloc(&perm, q.M)) return FGA_ENOMEM;
+    if ((rc = pack_template(pr.Yn, pr.mYn, p->dt, q.M, true, Y0, perm, s))) return rc;
+    P.rec = t->node_rec;
+    P.bodies = t->bodies;
+    P.front = t->front;
+    P.K = t->n_front;
+  } else {
+    float4* X4 = nullptr;
+    if (sc.alloc(&X4, q.N)) return FGA_ENOMEM;
+    if ((rc = pack_template(pr.Xn, pr.mXn, 0.f, q.N, false, X4, nullptr, s))) return rc;
+    if ((rc = pack_template(pr.Yn, pr.mYn, p->dt, q.M, false, Y0, nullptr, s))) return rc;
+    P.X4 = X4;
+    P.K = (int)((q.N + BATCH_CHUNK - 1) / BATCH_CHUNK);
+  }
+  P.Y0 = Y0;
+  P.ds = ds;
+  P.nblk = epilogue_blocks(q.M);
+  double* mu0 = nullptr;
+  if (sc.alloc(&P.hi, (size_t)P.K * q.M) || sc.alloc(&P.lo, (size_t)P.K * q.M) ||
+      sc.alloc(&P.V, q.M) || sc.alloc(&P.partials, (size_t)P.nblk * NRED) || sc.alloc(&P.counter, 1) ||
+      sc.alloc(&mu0, 3))
+    return FGA_ENOMEM;
+  FGA_CUDA_TRY(cudaMemsetAsync(P.V, 0, sizeof(float4) * q.M, s));
+  FGA_CUDA_TRY(cudaMemsetAsync(P.counter, 0, sizeof(unsigned), s));
+  if ((rc = centroid4(Y0, q.M, mu0, s))) return rc;
+  if ((rc = launch_state_init(ds, mu0, s))) return rc;
+  P.ep = EpiParams{p->G, p->dt, p->eta, p->velocity_mode, (double)p->conv_tol, 0,
+                   1.0 / (double)q.M, 1.0 / (double)p->dt, p->max_iter};
+  P.inter_add = P.method == FGA_BH ? 0ull : (unsigned long long)(q.N * q.M);
+  return FGA_OK;
+}
+
+void fill_pair_result(const DevState& h, const double* info, int method, const fga_params* p,
+                      fga_pair_result& r) {
+  std::memset(&r, 0, sizeof(r));
+  std::memcpy(r.R, h.R, sizeof(r.R));
+  if (p->normalize)
+    fga_denormalize(h.R, h.t, info, p->a, r.t);
+  else
+    std::memcpy(r.t, h.t, sizeof(r.t));
+  r.method = method;
+  r.iterations = h.iter;
+  r.converged = h.converged;
+  r.interactions = (int64_t)h.interactions;
+  r.status = h.status ? FGA_EINTERNAL : (h.degenerate ? FGA_EDEGENERATE : FGA_OK);
+}
+
+bool batch_layout(const std::vector<PairDev>& pairs, std::vector<unsigned>& task_start,
+                  std::vector<unsigned>& block_start) {
+  task_start.assign(pairs.size() + 1, 0u);
+  block_start.assign(pairs.size() + 1, 0u);
+  int64_t nt = 0, nb = 0;
+  for (size_t k = 0; k < pairs.size(); ++k) {
+    nt += (pairs[k].M + 31) / 32 * (int64_t)pairs[k].K;
+    nb += pairs[k].nblk;
+    if (nt >= ((int64_t)1 << 31) || nb >= ((int64_t)1 << 31)) return false;
+    task_start[k + 1] = (unsigned)nt;
+    block_start[k + 1] = (unsigned)nb;
+  }
+  return true;
+}
+
 }  // namespace fga
 
 using namespace fga;
 
 extern "C" int64_t fga_direct_max_n(int64_t new_value) {
-  const int64_t old = g_direct_max_n;
-  if (new_value > 0) g_direct_max_n = new_value;
-  return old;
+  return new_value > 0 ? g_direct_max_n.exchange(new_value) : g_direct_max_n.load();
 }
 
 extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_params* p,
@@ -193,10 +327,6 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
   }
   int rc = check_register_params(p);
   if (rc) return rc;
-  if (p->max_depth < 1 || p->max_depth > 20) {
-    set_error("fga_register_batch: max_depth must be in 1..20");
-    return FGA_EINVAL;
-  }
   for (int k = 0; k < count; ++k) {
     const fga_pair& q = pairs[k];
     if (!q.X || !q.Y || q.N <= 0 || q.M <= 0 || q.N > ((int64_t)1 << 26) || q.M > ((int64_t)1 << 26)) {
@@ -216,8 +346,7 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
   std::vector<Prepared> prep(count);
   std::vector<PairDev> host(count);
   DevState* dsarr = nullptr;
-  double* mu0 = nullptr;
-  if (sc.alloc(&dsarr, (size_t)count) || sc.alloc(&mu0, (size_t)3 * count)) return FGA_ENOMEM;
+  if (sc.alloc(&dsarr, (size_t)count)) return FGA_ENOMEM;
   for (int k = 0; k < count; ++k) {
     const fga_pair& q = pairs[k];
     if ((rc = prepare_inputs(sc, q.X, q.N, q.Y, q.M, q.mX, q.mY, p, prep[k], h2d, s))) return rc;
@@ -227,84 +356,39 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
   for (int k = 0; k < count; ++k)
     FGA_CUDA_TRY(cudaMemcpyAsync(&flags[8 * k], prep[k].flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaStreamSynchronize(s));
+  for (int k = 0; k < count; ++k)
+    if ((rc = check_pair_flags(&flags[8 * k], "fga_register_batch", k))) return rc;
   for (int k = 0; k < count; ++k) {
-    const int* f = &flags[8 * k];
-    if (f[0] || f[1] || f[2] || f[3] || !f[4]) {
-      set_error("fga_register_batch: pair " + std::to_string(k) +
-                (f[4] ? " has a non-finite coordinate or a bad mass" : " is degenerate (all centred coordinates equal)"));
-      return FGA_EINVAL;
-    }
+    fga_tree* t = nullptr;
+    rc = build_pair(pairs[k], prep[k], p, sc, &t, dsarr + k, host[k], s);
+    if (t) trees.push_back(t);
+    if (rc) return rc;
   }
-  std::vector<int4> tasks_bh, tasks_direct;
-  std::vector<int2> blockmap;
-  for (int k = 0; k < count; ++k) {
-    const fga_pair& q = pairs[k];
-    const Prepared& pr = prep[k];
-    PairDev& P = host[k];
-    std::memset(&P, 0, sizeof(P));
-    P.method = resolve_method(p, q.N);
-    P.N = q.N;
-    P.M = q.M;
-    float4* Y0 = nullptr;
-    if (sc.alloc(&Y0, q.M)) return FGA_ENOMEM;
-    if (P.method == FGA_BH) {
-      fga_tree* t = nullptr;
-      if ((rc = tree_build(pr.Xn, pr.mXn, q.N, p->max_depth, &t, s))) return rc;
-      trees.push_back(t);
-      int* perm = nullptr;
-      if (sc.alloc(&perm, q.M)) return FGA_ENOMEM;
-      if ((rc = pack_template(pr.Yn, pr.mYn, p->dt, q.M, true, Y0, perm, s))) return rc;
-      P.rec = t->node_rec;
-      P.bodies = t->bodies;
-      P.front = t->front;
-      P.K = t->n_front;
-    } else {
-      float4* X4 = nullptr;
-      if (sc.alloc(&X4, q.N)) return FGA_ENOMEM;
-      if ((rc = pack_template(pr.Xn, pr.mXn, 0.f, q.N, false, X4, nullptr, s))) return rc;
-      if ((rc = pack_template(pr.Yn, pr.mYn, p->dt, q.M, false, Y0, nullptr, s))) return rc;
-      P.X4 = X4;
-      P.K = (int)((q.N + BATCH_CHUNK - 1) / BATCH_CHUNK);
-    }
-    P.Y0 = Y0;
-    P.ds = dsarr + k;
-    P.nblk = epilogue_blocks(q.M);
-    if (sc.alloc(&P.hi, (size_t)P.K * q.M) || sc.alloc(&P.lo, (size_t)P.K * q.M) ||
-        sc.alloc(&P.V, q.M) || sc.alloc(&P.partials, (size_t)P.nblk * NRED) || sc.alloc(&P.counter, 1))
-      return FGA_ENOMEM;
-    FGA_CUDA_TRY(cudaMemsetAsync(P.V, 0, sizeof(float4) * q.M, s));
-    FGA_CUDA_TRY(cudaMemsetAsync(P.counter, 0, sizeof(unsigned), s));
-    if ((rc = centroid4(Y0, q.M, mu0 + 3 * k, s))) return rc;
-    if ((rc = launch_state_init(P.ds, mu0 + 3 * k, s))) return rc;
-    P.ep = EpiParams{p->G, p->dt, p->eta, p->velocity_mode, (double)p->conv_tol, 0,
-                     1.0 / (double)q.M, 1.0 / (double)p->dt};
-    P.inter_add = P.method == FGA_BH ? 0ull : (unsigned long long)(q.N * q.M);
-    const int groups = (int)((q.M + 31) / 32);
-    auto& tl = P.method == FGA_BH ? tasks_bh : tasks_direct;
-    for (int g = 0; g < groups; ++g)
-      for (int f = 0; f < P.K; ++f) tl.push_back(make_int4(k, g, f, 0));
-    for (int b = 0; b < P.nblk; ++b) blockmap.push_back(make_int2(k, b));
+  // Barnes-Hut pairs (usually the heaviest tasks) are handed out first
+  std::vector<PairDev> order;
+  for (int pass = 0; pass < 2; ++pass)
+    for (int k = 0; k < count; ++k)
+      if ((host[k].method == FGA_BH) == (pass == 0)) order.push_back(host[k]);
+  std::vector<unsigned> task_start, block_start;
+  if (!batch_layout(order, task_start, block_start)) {
+    set_error("fga_register_batch: too many tasks in one batch (2^31)");
+    return FGA_EINVAL;
   }
-  // Barnes-Hut tasks (usually the heaviest) are handed out first
-  std::vector<int4> tasks(tasks_bh);
-  tasks.insert(tasks.end(), tasks_direct.begin(), tasks_direct.end());
   PairDev* d_pairs = nullptr;
-  int4* d_tasks = nullptr;
-  int2* d_blockmap = nullptr;
-  unsigned* d_ctr = nullptr;
-  if (sc.alloc(&d_pairs, (size_t)count) || sc.alloc(&d_tasks, tasks.size()) ||
-      sc.alloc(&d_blockmap, blockmap.size()) || sc.alloc(&d_ctr, 2))
+  unsigned *d_tstart = nullptr, *d_bstart = nullptr, *d_ctr = nullptr;
+  if (sc.alloc(&d_pairs, (size_t)count) || sc.alloc(&d_tstart, (size_t)count + 1) ||
+      sc.alloc(&d_bstart, (size_t)count + 1) || sc.alloc(&d_ctr, 2))
     return FGA_ENOMEM;
-  FGA_CUDA_TRY(cudaMemcpyAsync(d_pairs, host.data(), sizeof(PairDev) * count, cudaMemcpyHostToDevice, s));
-  FGA_CUDA_TRY(cudaMemcpyAsync(d_tasks, tasks.data(), sizeof(int4) * tasks.size(), cudaMemcpyHostToDevice, s));
-  FGA_CUDA_TRY(cudaMemcpyAsync(d_blockmap, blockmap.data(), sizeof(int2) * blockmap.size(),
+  FGA_CUDA_TRY(cudaMemcpyAsync(d_pairs, order.data(), sizeof(PairDev) * count, cudaMemcpyHostToDevice, s));
+  FGA_CUDA_TRY(cudaMemcpyAsync(d_tstart, task_start.data(), sizeof(unsigned) * (count + 1),
+                               cudaMemcpyHostToDevice, s));
+  FGA_CUDA_TRY(cudaMemcpyAsync(d_bstart, block_start.data(), sizeof(unsigned) * (count + 1),
                                cudaMemcpyHostToDevice, s));
   FGA_CUDA_TRY(cudaMemsetAsync(d_ctr, 0, 2 * sizeof(unsigned), s));
   const auto t_setup = std::chrono::steady_clock::now();
   // the iteration loop as one CUDA graph on a private stream ordered after s
-  const unsigned ntasks = (unsigned)tasks.size();
-  const int fgrid = occupancy_grid((const void*)k_batch_force, BATCH_WARPS * 32,
-                                   ((int64_t)ntasks + BATCH_WARPS - 1) / BATCH_WARPS);
+  const unsigned ntasks = task_start[count], nblocks = block_start[count];
+  const int fgrid = batch_force_grid(ntasks);
   const float eps2 = p->eps * p->eps, theta2 = p->theta * p->theta;
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -344,13 +428,14 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
     for (auto& e : evs) FGA_CUDA_TRY(cudaEventCreate(&e));
     for (int it = 0; it < p->max_iter; ++it) {
       FGA_CUDA_TRY(cudaEventRecord(evs[2 * it], cs));
-      k_batch_force<<<fgrid, BATCH_WARPS * 32, 0, cs>>>(d_pairs, d_tasks, ntasks, d_ctr, eps2, theta2);
-      count_launch();
-      FGA_LAUNCH_CHECK("batch force");
+      if ((rc = launch_batch_iteration(d_pairs, count, d_tstart, ntasks, d_bstart, 0, d_ctr, eps2,
+                                       theta2, fgrid, cs)))
+        return rc;
       FGA_CUDA_TRY(cudaEventRecord(evs[2 * it + 1], cs));
-      k_batch_epilogue<<<(unsigned)blockmap.size(), EPI_BS, 0, cs>>>(d_pairs, d_blockmap);
-      count_launch();
-      FGA_LAUNCH_CHECK("batch epilogue");
+      if ((rc = launch_batch_iteration(d_pairs, count, d_tstart, 0, d_bstart, nblocks, d_ctr, eps2,
+                                       theta2, fgrid, cs)))
+        return rc;
+      count_launch(2);
     }
     FGA_CUDA_TRY(cudaStreamSynchronize(cs));
     for (int it = 0; it < p->max_iter; ++it) {
@@ -363,12 +448,9 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
     FGA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int lrc = FGA_OK;
     for (int it = 0; it < p->max_iter && lrc == FGA_OK; ++it) {
-      k_batch_force<<<fgrid, BATCH_WARPS * 32, 0, cs>>>(d_pairs, d_tasks, ntasks, d_ctr, eps2, theta2);
-      count_launch();
-      if (cudaPeekAtLastError() != cudaSuccess) lrc = FGA_ECUDA;
-      k_batch_epilogue<<<(unsigned)blockmap.size(), EPI_BS, 0, cs>>>(d_pairs, d_blockmap);
-      count_launch();
-      if (cudaPeekAtLastError() != cudaSuccess) lrc = FGA_ECUDA;
+      lrc = launch_batch_iteration(d_pairs, count, d_tstart, ntasks, d_bstart, nblocks, d_ctr, eps2,
+                                   theta2, fgrid, cs);
+      count_launch(2);
     }
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
     if (lrc != FGA_OK || ce != cudaSuccess) {
@@ -391,21 +473,10 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
   int code = FGA_OK;
   int64_t total = 0;
   for (int k = 0; k < count; ++k) {
-    const DevState& h = hs[k];
-    fga_pair_result& r = results[k];
-    std::memcpy(r.R, h.R, sizeof(r.R));
-    if (p->normalize)
-      fga_denormalize(h.R, h.t, &infos[8 * k], p->a, r.t);
-    else
-      std::memcpy(r.t, h.t, sizeof(r.t));
-    r.method = host[k].method;
-    r.iterations = h.iter;
-    r.converged = h.done && !(h.status & 2);
-    r.interactions = (int64_t)h.interactions;
-    r.status = h.status ? FGA_EINTERNAL : (h.degenerate ? FGA_EDEGENERATE : FGA_OK);
-    if (r.status == FGA_EINTERNAL) code = FGA_EINTERNAL;
-    else if (r.status == FGA_EDEGENERATE && code == FGA_OK) code = FGA_EDEGENERATE;
-    total += r.interactions;
+    fill_pair_result(hs[k], &infos[8 * k], host[k].method, p, results[k]);
+    if (results[k].status == FGA_EINTERNAL) code = FGA_EINTERNAL;
+    else if (results[k].status == FGA_EDEGENERATE && code == FGA_OK) code = FGA_EDEGENERATE;
+    total += results[k].interactions;
   }
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));

@@ -244,7 +244,10 @@ static __device__ void rigid_step(const double* red, int64_t M, DevState* ds, co
     double d2 = 0;
     for (int q = 0; q < 12; ++q) d2 += (T[q] - ds->Tm2[q]) * (T[q] - ds->Tm2[q]);
     ds->last_conv = d2;
-    if (ep.conv_tol > 0 && d2 <= ep.conv_tol) ds->done = 1;
+    if (ep.conv_tol > 0 && d2 <= ep.conv_tol) {
+      ds->done = 1;
+      ds->converged = 1;
+    }
   } else {
     ds->last_conv = -1.0;
   }
@@ -285,6 +288,7 @@ static __device__ void rigid_step(const double* red, int64_t M, DevState* ds, co
     for (int q = 0; q < 12; ++q) traj[12 * (int64_t)k_it + q] = T[q];
   ds->interactions += inter_add;
   ds->iter = k_it + 1;
+  if (ep.max_iter > 0 && k_it + 1 >= ep.max_iter) ds->done = 1;
 }
 
 

@@ -7,6 +7,7 @@
 // The template is placed on the fly as y = R y0 + t from the accumulated
 // transform, so it never drifts from repeated FP32 updates.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 
 #include "fga_device.cuh"
@@ -201,7 +202,8 @@ __global__ void __launch_bounds__(BH_WARPS * 32, 8) k_bh(const float4* __restric
 }
 
 static int bh_grid(int64_t M, int K) {
-  static int per_sm = 0;
+  static std::atomic<int> cached{0};
+  int per_sm = cached.load();
   if (per_sm == 0) {
     int b = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bh, BH_WARPS * 32, 0) != cudaSuccess || b < 1) {
@@ -209,6 +211,7 @@ static int bh_grid(int64_t M, int K) {
       b = 1;
     }
     per_sm = b;
+    cached.store(b);
   }
   const int64_t tasks = (M + 31) / 32 * K;
   const int64_t need = (tasks + BH_WARPS - 1) / BH_WARPS;
@@ -334,6 +337,7 @@ __global__ void k_state_init(DevState* ds, const double* __restrict__ mu0) {
   z.interactions = 0ull;
   z.iter = 0;
   z.done = 0;
+  z.converged = 0;
   z.status = 0;
   z.degenerate = 0;
   z.bh_next = 0u;

@@ -69,7 +69,8 @@ struct DevState {
   double netF[3], torque[3];
   unsigned long long interactions;
   int iter;               // iterations completed
-  int done;               // convergence test fired
+  int done;               // stop: convergence, non-finite fit or iteration limit
+  int converged;          // the convergence test fired
   int status;             // bit 0: stack overflow in BH traversal; bit 1: non-finite fit
   int degenerate;         // rigid fits with rank(C) < 2
   unsigned bh_next;       // BH traversal: next 32-point group to hand out
@@ -177,6 +178,7 @@ struct EpiParams {
   double conv_tol;
   int max_traj;
   double inv_M, inv_dt;  // 1/M and 1/dt, FP64, computed on the host
+  int max_iter;          // > 0: the pair stops by itself after this many iterations
 };
 int launch_epilogue(const float4* Y0, int64_t M, const ForceBuffers& fb, float4* V,
                     DevState* ds, double* d_partials, unsigned* d_counter, double* d_traj,

@@ -296,3 +296,60 @@ def batch_pairs(seed: int, count: int = 256, lo: int = 500, hi: int = 50_000,
             out.append(planar_scene_pair(seed * 100_003 + k, n=int(n), m=int(m), max_deg=max_deg,
                                          t_max=t_max))
     return out
+
+
+def cropped_scene_pair(seed: int, n: int, m: int, overlap: float, max_deg: float = 30.0,
+                       t_max: float = 0.2, sigma: float = 0.01, outlier_frac: float = 0.05):
+    """Two partial views of one piecewise-planar scene with a given overlap.
+
+    The scene (as in ``planar_scene_pair``) is cut along its longest axis into
+    two windows of equal width whose shared part is ``overlap`` of each window;
+    X keeps ``n`` points of the first window, Y ``m`` points of the second
+    (uniform subsamples of denser draws), and Y is then moved by
+    ``(R_gt, t_gt)^-1``. Returns ``(X, Y, R_gt, t_gt)``."""
+    rng = np.random.default_rng(seed)
+    patches = _planar_scene(rng)
+    r_gt = random_rotation(rng, max_deg)
+    t_gt = random_translation(rng, t_max)
+    probe = _sample_scene(rng, patches, 4096, sigma, 0.0)
+    lo, hi = probe.min(0), probe.max(0)
+    axis = int(np.argmax(hi - lo))
+    span = float(hi[axis] - lo[axis])
+    width = span / (2.0 - overlap)
+    win_x = (lo[axis], lo[axis] + width)
+    win_y = (lo[axis] + width * (1.0 - overlap), hi[axis])
+
+    def view(count, win):
+        frac = max((win[1] - win[0]) / span, 0.05)
+        draw = int(count / frac * 1.3) + 64
+        while True:
+            pts = _sample_scene(rng, patches, draw, sigma, outlier_frac)
+            keep = pts[(pts[:, axis] >= win[0]) & (pts[:, axis] <= win[1])]
+            if keep.shape[0] >= count:
+                return keep[rng.choice(keep.shape[0], size=count, replace=False)]
+            draw = int(draw * 1.5)
+
+    x = view(n, win_x)
+    y = (view(m, win_y) - t_gt) @ r_gt
+    return _f32(x), _f32(y), r_gt, t_gt
+
+
+def serve_trace(seed: int, count: int, rate: float = 200.0, lo: int = 1000, hi: int = 500_000,
+                overlap_lo: float = 0.3, overlap_hi: float = 1.0):
+    """A request trace: Poisson arrivals at ``rate`` per second.
+
+    Request k arrives at ``t_k`` (seconds, exponential gaps) and carries a
+    cropped-scene pair with N and M log-uniform in [lo, hi] and overlap
+    uniform in [overlap_lo, overlap_hi]. Returns a list of
+    ``(t_k, X, Y, R_gt, t_gt)``."""
+    rng = np.random.default_rng(seed)
+    gaps = rng.exponential(1.0 / rate, size=count)
+    times = np.cumsum(gaps) - gaps[0]
+    sizes = np.round(np.exp(rng.uniform(math.log(lo), math.log(hi), size=(count, 2)))).astype(np.int64)
+    overlaps = rng.uniform(overlap_lo, overlap_hi, size=count)
+    out = []
+    for k in range(count):
+        X, Y, R, t = cropped_scene_pair(seed * 1_000_003 + k, int(sizes[k, 0]), int(sizes[k, 1]),
+                                        float(overlaps[k]))
+        out.append((float(times[k]), X, Y, R, t))
+    return out
