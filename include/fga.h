@@ -295,6 +295,45 @@ int fga_register_batch(const fga_pair* pairs, int count, const fga_params* p,
  * and, if new_value > 0, sets it (process-wide). */
 int64_t fga_direct_max_n(int64_t new_value);
 
+/* ------------------------------------------------------------------ autotuning
+ * The executors take their launch shapes and the FGA_AUTO crossover from
+ * process-wide tables with built-in defaults; fga_autotune measures them on
+ * this GPU (synthetic clouds generated on the device) and replaces them. */
+#define FGA_TUNE_DIRECT_TILES 1 /* tile shape of the all-pairs kernel, per size class */
+#define FGA_TUNE_CROSSOVER 2    /* FGA_AUTO crossover (fga_direct_max_n)              */
+#define FGA_TUNE_ALL 3
+#define FGA_TUNE_NSIZES 7       /* crossover probe sizes N = 1024 << k, k < 7         */
+
+typedef struct fga_tune_report {
+  int direct_bs[3], direct_qpt[3]; /* tile per template-size class: M < 8192,
+                                      M < 65536, M >= 65536 (threads per block,
+                                      template points per thread)             */
+  double direct_gips[3];           /* G terms/s of the chosen tile (class probe) */
+  int64_t direct_max_n;            /* FGA_AUTO crossover in force after the call */
+  int64_t sizes[FGA_TUNE_NSIZES];  /* probed reference sizes N                  */
+  double direct_us_per_point[FGA_TUNE_NSIZES]; /* all-pairs force, us per template
+                                                  point and iteration            */
+  double bh_us_per_point[FGA_TUNE_NSIZES];     /* Barnes-Hut force + tree build
+                                                  spread over p->max_iter
+                                                  iterations with M = N          */
+  double bh_build_ms[FGA_TUNE_NSIZES];
+  double elapsed_ms;
+} fga_tune_report;
+
+/* Measures what `flags` selects with the parameters *p (NULL: defaults; eps,
+ * theta, dt and max_iter matter) and installs the result process-wide:
+ * the fastest all-pairs tile for each template-size class, and the largest
+ * probe N for which the all-pairs sum per template point is not slower than
+ * Barnes-Hut. Takes about a second; synchronises `stream`.
+ * Errors: FGA_EINVAL, FGA_ENOMEM, FGA_ECUDA. */
+int fga_autotune(const fga_params* p, int flags, void* stream, fga_tune_report* out);
+
+/* The all-pairs tile table itself: size class 0..2 as above, bs 128 or 256,
+ * qpt 1, 2 or 4 (FGA_EINVAL otherwise). New states and calls use it;
+ * existing states keep the plan they were created with. */
+int fga_set_direct_tile(int size_class, int bs, int qpt);
+int fga_get_direct_tile(int size_class, int* bs, int* qpt);
+
 /* ------------------------------------------------------------------ serving
  * A registration server: a continuous-batching engine on one GPU. Requests
  * (pairs, Algorithm 2 with the server's parameters) are submitted at any
@@ -319,6 +358,12 @@ typedef struct fga_server_config {
   int max_pairs;       /* resident pairs at most; <= 0: 4096                      */
   int iters_per_tick;  /* iterations per tick; <= 0: 4                            */
   int device;          /* CUDA device; < 0: the calling thread's current device  */
+  double max_work;     /* force terms per iteration that admitted pairs may need
+                          together, estimated N*M (all-pairs) or
+                          64*M*log2(N+1) (Barnes-Hut); a pair is always admitted
+                          when none is held. 0: 4e9 (about 2 ms of GPU time per
+                          iteration); < 0: no limit. Fewer pairs sharing the GPU
+                          finish sooner; enough of them keep it busy          */
 } fga_server_config;
 
 typedef struct fga_served {
@@ -337,6 +382,7 @@ typedef struct fga_server_stats {
   int preparing;            /* being prepared                                      */
   int resident;             /* on the device, iterating                            */
   int64_t bytes_charged;    /* sum of the bounds of admitted pairs                 */
+  double work_admitted;     /* sum of the work estimates of admitted pairs         */
   int64_t mem_budget;
   int64_t ticks;            /* ticks run                                           */
   int64_t pair_iterations;  /* sum over ticks of resident pairs x iterations       */

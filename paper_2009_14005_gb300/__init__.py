@@ -51,7 +51,7 @@ SYMBOLS = [
     "fga_state_get", "fga_state_trajectory", "fga_state_destroy", "fga_register",
     "fga_forces_direct_static", "fga_register_batch", "fga_direct_max_n",
     "fga_server_create", "fga_server_submit", "fga_server_poll", "fga_server_stats_get",
-    "fga_server_destroy",
+    "fga_server_destroy", "fga_autotune", "fga_set_direct_tile", "fga_get_direct_tile",
 ]
 FGA_STATIC_SCRATCH_FLOAT4 = 524288
 
@@ -100,7 +100,8 @@ class fga_pair_result(ctypes.Structure):
 
 class fga_server_config(ctypes.Structure):
     _fields_ = [("mem_budget", ctypes.c_int64), ("max_pairs", ctypes.c_int),
-                ("iters_per_tick", ctypes.c_int), ("device", ctypes.c_int)]
+                ("iters_per_tick", ctypes.c_int), ("device", ctypes.c_int),
+                ("max_work", ctypes.c_double)]
 
 
 class fga_served(ctypes.Structure):
@@ -114,11 +115,31 @@ class fga_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
                 ("failed", ctypes.c_int64), ("pending", ctypes.c_int), ("preparing", ctypes.c_int),
                 ("resident", ctypes.c_int), ("bytes_charged", ctypes.c_int64),
+                ("work_admitted", ctypes.c_double),
                 ("mem_budget", ctypes.c_int64), ("ticks", ctypes.c_int64),
                 ("pair_iterations", ctypes.c_int64), ("busy_ms", ctypes.c_double)]
 
     def to_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+FGA_TUNE_DIRECT_TILES, FGA_TUNE_CROSSOVER, FGA_TUNE_ALL, FGA_TUNE_NSIZES = 1, 2, 3, 7
+
+
+class fga_tune_report(ctypes.Structure):
+    _fields_ = [("direct_bs", ctypes.c_int * 3), ("direct_qpt", ctypes.c_int * 3),
+                ("direct_gips", ctypes.c_double * 3), ("direct_max_n", ctypes.c_int64),
+                ("sizes", ctypes.c_int64 * FGA_TUNE_NSIZES),
+                ("direct_us_per_point", ctypes.c_double * FGA_TUNE_NSIZES),
+                ("bh_us_per_point", ctypes.c_double * FGA_TUNE_NSIZES),
+                ("bh_build_ms", ctypes.c_double * FGA_TUNE_NSIZES), ("elapsed_ms", ctypes.c_double)]
+
+    def to_dict(self):
+        d = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            d[k] = list(v) if hasattr(v, "__len__") else v
+        return d
 
 
 class FGAError(RuntimeError):
@@ -167,6 +188,10 @@ def _load():
                                            ctypes.POINTER(ctypes.c_int), ctypes.c_int]),
         "fga_server_stats_get": (ctypes.c_int, [P, ctypes.POINTER(fga_server_stats)]),
         "fga_server_destroy": (ctypes.c_int, [P]),
+        "fga_autotune": (ctypes.c_int, [PP, ctypes.c_int, VP, ctypes.POINTER(fga_tune_report)]),
+        "fga_set_direct_tile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+        "fga_get_direct_tile": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                               ctypes.POINTER(ctypes.c_int)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -509,6 +534,25 @@ def fga_register_batch(pairs, p: fga_params | None = None, stream=None):
     return out, d
 
 
+def autotune(p: fga_params | None = None, flags: int = FGA_TUNE_ALL, stream=None) -> dict:
+    """Measures and installs the all-pairs tiles and the FGA_AUTO crossover
+    (``fga_autotune``); returns the report as a dict."""
+    rep = fga_tune_report()
+    _err(lib.fga_autotune(ctypes.byref(p) if p is not None else None, int(flags), _stream(stream),
+                          ctypes.byref(rep)))
+    return rep.to_dict()
+
+
+def set_direct_tile(size_class: int, bs: int, qpt: int):
+    _err(lib.fga_set_direct_tile(int(size_class), int(bs), int(qpt)))
+
+
+def get_direct_tile(size_class: int):
+    bs, q = ctypes.c_int(), ctypes.c_int()
+    _err(lib.fga_get_direct_tile(int(size_class), ctypes.byref(bs), ctypes.byref(q)))
+    return bs.value, q.value
+
+
 def _served_dict(o: fga_served) -> dict:
     r = o.result
     return dict(ticket=int(o.ticket), R=np.array(r.R[:]).reshape(3, 3), t=np.array(r.t[:]),
@@ -528,9 +572,10 @@ class Server:
     times submit_ms, admit_ms, start_ms, done_ms in ms since creation)."""
 
     def __init__(self, p: fga_params | None = None, mem_budget: int = 0, max_pairs: int = 0,
-                 iters_per_tick: int = 0, device: int = -1):
+                 iters_per_tick: int = 0, device: int = -1, max_work: float = 0.0):
         self._h = ctypes.c_void_p()
-        cfg = fga_server_config(int(mem_budget), int(max_pairs), int(iters_per_tick), int(device))
+        cfg = fga_server_config(int(mem_budget), int(max_pairs), int(iters_per_tick), int(device),
+                                float(max_work))
         _err(lib.fga_server_create(ctypes.byref(p or params()), ctypes.byref(cfg), ctypes.byref(self._h)))
         self._keep = {}
 

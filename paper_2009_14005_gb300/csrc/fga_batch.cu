@@ -86,7 +86,7 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, 8) k_batch_force(const PairD
         for (int k = 0; k < 32; ++k) {
           const float4 q = s_tile[w][k];
           const float dx = q.x - y.x, dy = q.y - y.y, dz = q.z - y.z;
-          const float inv = rsqrtf(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2))));
+          const float inv = rsqrt_fast(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2))));
           const float wgt = q.w * (inv * inv * inv);
           px = fmaf(wgt, dx, px);
           py = fmaf(wgt, dy, py);

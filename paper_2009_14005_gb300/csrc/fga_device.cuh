@@ -10,6 +10,16 @@ namespace fga {
 
 static constexpr unsigned FULL = 0xffffffffu;
 
+// 1/sqrt(x) from the SFU (PTX rsqrt.approx.ftz.f32). Every argument on the
+// force path is r^2 + eps^2 >= eps^2 > 0, a normal number, where flushing
+// subnormals changes nothing; the non-flushing form costs extra instructions
+// that guard subnormal inputs.
+__device__ __forceinline__ float rsqrt_fast(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 // Knuth's TwoSum: s + e == a + b exactly.
 __device__ __forceinline__ void comp_add(float& hi, float& lo, float x) {
   const float s = hi + x;
@@ -320,7 +330,7 @@ __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const fl
       const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       const bool accept = live && l2 < theta2 * d2;
       if ((first_mask >> j) & 1u) {
-        const float inv = rsqrtf(d2 + eps2);
+        const float inv = rsqrt_fast(d2 + eps2);
         const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
         px = fmaf(wgt, dx, px);
         py = fmaf(wgt, dy, py);
@@ -346,7 +356,7 @@ __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const fl
       const float dx = cm.x - y.x, dy = cm.y - y.y, dz = cm.z - y.z;
       const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       const bool accept = nchild == -1 || ri.x < theta2 * d2;
-      const float inv = rsqrtf(d2 + eps2);
+      const float inv = rsqrt_fast(d2 + eps2);
       const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
       px = fmaf(wgt, dx, px);
       py = fmaf(wgt, dy, py);
@@ -369,7 +379,7 @@ __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const fl
         for (int b = 0; b < nb; ++b) {
           const float4 q = bodies[b0 + b];
           const float ex = q.x - y.x, ey = q.y - y.y, ez = q.z - y.z;
-          const float iq = rsqrtf(fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, eps2))));
+          const float iq = rsqrt_fast(fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, eps2))));
           const float wq = q.w * (iq * iq * iq);
           px = fmaf(wq, ex, px);
           py = fmaf(wq, ey, py);

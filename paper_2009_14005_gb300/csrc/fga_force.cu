@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(BS) k_direct(const float4* __restrict__ X, int
       for (int q = 0; q < QPT; ++q) {
         const float dx = s.x - yx[q], dy = s.y - yy[q], dz = s.z - yz[q];
         const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-        const float inv = rsqrtf(r2);
+        const float inv = rsqrt_fast(r2);
         const float w = s.w * (inv * inv * inv);
         px[q] = fmaf(w, dx, px[q]);
         py[q] = fmaf(w, dy, py[q]);
@@ -86,19 +86,32 @@ __global__ void __launch_bounds__(BS) k_direct(const float4* __restrict__ X, int
   }
 }
 
+// Tile shape (threads per block, template points per thread) per template
+// size class: M < 8k, M < 64k, M >= 64k. Encoded bs * 16 + qpt; the
+// autotuner may replace the defaults.
+static std::atomic<int> g_direct_tile[3] = {{128 * 16 + 1}, {256 * 16 + 1}, {256 * 16 + 2}};
+
+int direct_size_class(int64_t M) { return M < 8 * 1024 ? 0 : (M < 64 * 1024 ? 1 : 2); }
+
+bool direct_tile_supported(int bs, int qpt) {
+  return (bs == 128 || bs == 256) && (qpt == 1 || qpt == 2 || qpt == 4);
+}
+
+void set_direct_tile(int size_class, int bs, int qpt) {
+  if (size_class >= 0 && size_class < 3 && direct_tile_supported(bs, qpt))
+    g_direct_tile[size_class].store(bs * 16 + qpt);
+}
+
+void get_direct_tile(int size_class, int* bs, int* qpt) {
+  const int v = g_direct_tile[size_class].load();
+  *bs = v / 16;
+  *qpt = v % 16;
+}
+
 DirectPlan plan_direct(int64_t N, int64_t M) {
   DirectPlan p;
   const int64_t sms = sm_count();
-  if (M >= 64 * 1024) {
-    p.bs = 256;
-    p.qpt = 2;
-  } else if (M >= 8 * 1024) {
-    p.bs = 256;
-    p.qpt = 1;
-  } else {
-    p.bs = 128;
-    p.qpt = 1;
-  }
+  get_direct_tile(direct_size_class(M), &p.bs, &p.qpt);
   const int64_t qblocks = (M + (int64_t)p.bs * p.qpt - 1) / ((int64_t)p.bs * p.qpt);
   const int64_t target = 4 * sms;  // blocks to fill every SM a few times
   int64_t S = std::max<int64_t>(1, (target + qblocks - 1) / qblocks);
@@ -117,12 +130,22 @@ int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const
   const float eps2 = eps * eps;
   const int64_t qblocks = (M + (int64_t)plan.bs * plan.qpt - 1) / ((int64_t)plan.bs * plan.qpt);
   dim3 grid((unsigned)qblocks, (unsigned)plan.S);
-  if (plan.bs == 256 && plan.qpt == 2)
-    k_direct<256, 2><<<grid, 256, 0, s>>>(X, N, plan.chunk, Y0, M, ds, eps2, fb.hi, fb.lo);
-  else if (plan.bs == 256)
-    k_direct<256, 1><<<grid, 256, 0, s>>>(X, N, plan.chunk, Y0, M, ds, eps2, fb.hi, fb.lo);
-  else
-    k_direct<128, 1><<<grid, 128, 0, s>>>(X, N, plan.chunk, Y0, M, ds, eps2, fb.hi, fb.lo);
+#define FGA_DIRECT_CASE(B, Q)                                                               \
+  else if (plan.bs == B && plan.qpt == Q)                                                   \
+    k_direct<B, Q><<<grid, B, 0, s>>>(X, N, plan.chunk, Y0, M, ds, eps2, fb.hi, fb.lo);
+  if (false) {
+  }
+  FGA_DIRECT_CASE(128, 1)
+  FGA_DIRECT_CASE(128, 2)
+  FGA_DIRECT_CASE(128, 4)
+  FGA_DIRECT_CASE(256, 1)
+  FGA_DIRECT_CASE(256, 2)
+  FGA_DIRECT_CASE(256, 4)
+#undef FGA_DIRECT_CASE
+  else {
+    set_error("launch_direct: unsupported tile shape");
+    return FGA_EINTERNAL;
+  }
   FGA_LAUNCH_CHECK("direct");
   fb.S = plan.S;
   return FGA_OK;

@@ -166,6 +166,11 @@ struct DirectPlan {
   int64_t chunk = 0;
 };
 DirectPlan plan_direct(int64_t N, int64_t M);
+// The direct kernel's tile table (see plan_direct); size classes 0..2.
+int direct_size_class(int64_t M);
+bool direct_tile_supported(int bs, int qpt);
+void set_direct_tile(int size_class, int bs, int qpt);
+void get_direct_tile(int size_class, int* bs, int* qpt);
 
 int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const DevState* ds,
                   float eps, const DirectPlan& plan, ForceBuffers& fb, cudaStream_t s);

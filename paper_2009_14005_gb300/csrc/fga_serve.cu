@@ -21,6 +21,7 @@
 // ordered after every launch that still lists it.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
@@ -40,6 +41,7 @@ struct Request {
   int64_t ticket = 0;
   fga_pair q{};
   int64_t charge = 0;
+  double work = 0;  // estimated force terms per iteration
   double submit_ms = 0;
 };
 
@@ -80,6 +82,7 @@ struct fga_server {
   std::deque<fga_served> completed;
   int preparing = 0, resident = 0;
   int64_t charged = 0, next_ticket = 1;
+  double work = 0, max_work = 0;
   int64_t n_submitted = 0, n_completed = 0, n_failed = 0, n_taken = 0;
   int64_t ticks = 0, pair_iters = 0;
   double busy_ms = 0;
@@ -153,12 +156,15 @@ void admit_loop(fga_server* S) {
         if (S->stop) return true;
         if (S->pending.empty()) return false;
         const int held = S->preparing + (int)S->ready.size() + S->resident;
-        return held < S->cfg.max_pairs && S->charged + S->pending.front().charge <= S->budget;
+        const Request& h = S->pending.front();
+        const bool work_ok = S->max_work <= 0 || held == 0 || S->work + h.work <= S->max_work;
+        return held < S->cfg.max_pairs && S->charged + h.charge <= S->budget && work_ok;
       });
       if (S->stop) return;
       sl->req = S->pending.front();
       S->pending.pop_front();
       S->charged += sl->req.charge;
+      S->work += sl->req.work;
       ++S->preparing;
       sl->admit_ms = S->now_ms();
     }
@@ -173,6 +179,7 @@ void admit_loop(fga_server* S) {
     --S->preparing;
     if (rc) {
       S->charged -= sl->req.charge;
+      S->work -= sl->req.work;
       S->fail_locked(sl->req, rc, msg.c_str(), sl->admit_ms);
       S->cv_admit.notify_all();
     } else {
@@ -479,6 +486,7 @@ class Runner {
       ++S_->n_completed;
       if (outs[j].result.status == FGA_EINTERNAL) ++S_->n_failed;
       S_->charged -= fin[j]->req.charge;
+      S_->work -= fin[j]->req.work;
       --S_->resident;
     }
     S_->cv_done.notify_all();
@@ -493,6 +501,7 @@ class Runner {
     for (auto& sl : active_) {
       S_->fail_locked(sl->req, code, msg, sl->admit_ms);
       S_->charged -= sl->req.charge;
+      S_->work -= sl->req.work;
       --S_->resident;
     }
     active_.clear();
@@ -532,6 +541,7 @@ extern "C" int fga_server_create(const fga_params* p, const fga_server_config* c
   if (cfg) S->cfg = *cfg;
   if (S->cfg.max_pairs <= 0) S->cfg.max_pairs = 4096;
   if (S->cfg.iters_per_tick <= 0) S->cfg.iters_per_tick = 4;
+  S->max_work = S->cfg.max_work == 0 ? 4e9 : S->cfg.max_work;
   if (S->cfg.device >= 0) {
     FGA_CUDA_TRY(cudaSetDevice(S->cfg.device));
     S->device = S->cfg.device;
@@ -568,7 +578,10 @@ extern "C" int fga_server_submit(fga_server* S, const fga_pair* req, int64_t* ti
   }
   Request r;
   r.q = *req;
-  r.charge = pair_bytes_bound(req->N, req->M, resolve_method(&S->p, req->N), &S->p);
+  const int method = resolve_method(&S->p, req->N);
+  r.charge = pair_bytes_bound(req->N, req->M, method, &S->p);
+  r.work = method == FGA_BH ? 64.0 * (double)req->M * std::log2((double)req->N + 1.0)
+                            : (double)req->N * (double)req->M;
   std::lock_guard<std::mutex> lk(S->mu);
   if (r.charge > S->budget) {
     set_error("fga_server_submit: the pair needs up to " + std::to_string(r.charge) +
@@ -628,6 +641,7 @@ extern "C" int fga_server_stats_get(fga_server* S, fga_server_stats* out) {
   out->preparing = S->preparing + (int)S->ready.size();
   out->resident = S->resident;
   out->bytes_charged = S->charged;
+  out->work_admitted = S->work;
   out->mem_budget = S->budget;
   out->ticks = S->ticks;
   out->pair_iterations = S->pair_iters;

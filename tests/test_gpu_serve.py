@@ -154,3 +154,23 @@ def test_early_exit_matches_alone(fga):
         b = alone[tickets[r["ticket"]]]
         assert r["converged"] and r["iterations"] == b["iterations"] < 300
         assert np.array_equal(r["R"], b["R"])
+
+
+def test_work_cap_admits_one_at_a_time(fga):
+    pairs = mixed_pairs()[:5]
+    p = params(fga, method=fga.FGA_DIRECT, max_iter=12)
+    alone = [fga.fga_register_batch([pr], p)[0][0] for pr in pairs]
+    # a cap below every pair's estimate: a pair is admitted only when none is held
+    with fga.Server(p, iters_per_tick=2, max_work=1.0) as srv:
+        tickets = {srv.submit(X, Y): k for k, (X, Y) in enumerate(pairs)}
+        held, got = 0, []
+        while len(got) < len(pairs):
+            st = srv.stats()
+            held = max(held, st["resident"] + st["preparing"])
+            got.extend(srv.poll(64, wait_ms=1))
+    assert held == 1
+    order = [tickets[r["ticket"]] for r in got]
+    assert order == sorted(order)  # FIFO admission, one at a time
+    for r in got:
+        b = alone[tickets[r["ticket"]]]
+        assert np.array_equal(r["R"], b["R"]) and np.array_equal(r["t"], b["t"])
