@@ -238,7 +238,8 @@ def special_config(a, w):
                 "N_M": "log-uniform in [%d, %d], independently" % (w["lo"], w["n"]),
                 "overlap": "uniform in [0.3, 1.0] (cropped piecewise-planar scenes)",
                 "iterations": w["iters"],
-                "method": "per pair: all-pairs if N <= 32768 else barnes-hut (theta %.1f)" % w["theta"],
+                "method": "per pair: all-pairs if N <= the autotuned crossover, else barnes-hut "
+                          "(theta %.1f)" % w["theta"],
                 "masses": "uniform", "eps": w["eps"], "eta": w["eta"], "dt": 0.1, "G": w["G"],
                 "timing": "host clock: first arrival to last result; latency = submit to result on host",
                 "l2": "not flushed: the trace's inputs (hundreds of MB) exceed L2",
@@ -246,7 +247,8 @@ def special_config(a, w):
     if w["gen"] == "batch":
         return {"workload": "batch-%d-pairs-500-50k-%dit" % (w["n"], w["iters"]), "pairs": w["n"],
                 "N_M": "log-uniform in [500, 50000], independently", "iterations": w["iters"],
-                "method": "per pair: all-pairs if N <= 32768 else barnes-hut (theta %.1f)" % w["theta"],
+                "method": "per pair: all-pairs if N <= the autotuned crossover, else barnes-hut "
+                          "(theta %.1f)" % w["theta"],
                 "masses": "uniform", "eps": w["eps"], "eta": w["eta"], "dt": 0.1, "G": w["G"],
                 "pairs_per_rank": a.pairs,
                 "l2": "flushed between steps (256 MB device write outside the timed events)",
@@ -452,6 +454,7 @@ def run_ours_batch(a):
     p.profile = 0
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
+    tuned = fga.autotune(p, stream=stream)  # tiles and crossover for this GPU (untimed)
     for k in range(a.warmup):
         fga.fga_register_batch(dev[k % len(dev)], p, stream=stream)
     torch.cuda.synchronize()
@@ -546,7 +549,8 @@ def run_ours_batch(a):
                     "unit": "interactions/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_tmax / max(a.e2e_steps, 1)},
-            "gpu_launches": launches, "roofline": roof, "clocks": clk}
+            "gpu_launches": launches, "roofline": roof, "clocks": clk,
+            "autotuned": tune_summary(tuned)}
     if world == 1 and not a.no_cpu_baseline:
         i, t, cores = cpu_sample(batches[0], a, a.cpu_iters)
         line["cpu_baseline"] = {"value": i / t, "unit": "interactions/s", "cores": cores,
@@ -557,6 +561,12 @@ def run_ours_batch(a):
                                              len(batches[0][0][1]), t)}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def tune_summary(rep):
+    return {"direct_max_n": rep["direct_max_n"],
+            "direct_tiles": ["%dx%d" % (b, q) for b, q in zip(rep["direct_bs"], rep["direct_qpt"])],
+            "tune_ms": rep["elapsed_ms"]}
 
 
 def replay_served(fga, p, trace, inputs, warm):
@@ -618,6 +628,7 @@ def run_ours_serve(a):
     p = lib_params(fga, a)
     p.profile = 0
     stream = torch.cuda.current_stream()
+    tuned = fga.autotune(p, stream=stream)  # tiles and crossover for this GPU (untimed)
 
     clocks = ClockSampler(local)
     barrier(world)
@@ -689,7 +700,8 @@ def run_ours_serve(a):
                     "ms_per_step": e2e_tmax / max(a.steps, 1),
                     "p50_ms": float(np.percentile([r["done_ms"] - r["submit_ms"] for r in res_h], 50)),
                     "p99_ms": float(np.percentile([r["done_ms"] - r["submit_ms"] for r in res_h], 99))},
-            "gpu_launches": launches, "roofline": roof, "clocks": clk}
+            "gpu_launches": launches, "roofline": roof, "clocks": clk,
+            "autotuned": tune_summary(tuned)}
     if world == 1 and not a.no_cpu_baseline:
         X, Y = trace[0][1], trace[0][2]
         i, t, cores = cpu_sample([(X, Y, None, None)], a, a.cpu_iters)

@@ -291,6 +291,11 @@ struct fga_state {
   double* traj = nullptr;
   int max_traj = 0;
   int queued = 0;
+  unsigned* bh_cost = nullptr;   // BH: step count of every task in the last launch
+  unsigned* bh_order = nullptr;  // BH: heavy-first task order derived from bh_cost
+  unsigned bh_ntasks = 0;
+  int bh_launches = 0;
+  bool bh_have_order = false;
   std::vector<cudaEvent_t> events;  // with p.profile: start/stop per force launch
   int timed = 0;                    // recorded start/stop pairs
 };
@@ -499,6 +504,11 @@ static int state_create_checked(const float* Xn, const float* mX, int64_t N, con
       dev_alloc_n(&st->counter, 1, s))
     return fail(FGA_ENOMEM);
   if (bh && dev_alloc_n(&st->perm, M, s)) return fail(FGA_ENOMEM);
+  if (bh) {
+    st->bh_ntasks = (unsigned)((M + 31) / 32) * (unsigned)st->tree->n_front;
+    if (dev_alloc_n(&st->bh_cost, st->bh_ntasks, s) || dev_alloc_n(&st->bh_order, st->bh_ntasks, s))
+      return fail(FGA_ENOMEM);
+  }
   if ((rc = pack_template(Yn, mY, p->dt, M, bh, st->Y0, st->perm, s))) return fail(rc);
   if (dev_alloc_n(&st->fb.hi, (size_t)st->fb.S * M, s) || dev_alloc_n(&st->fb.lo, (size_t)st->fb.S * M, s))
     return fail(FGA_ENOMEM);
@@ -532,10 +542,19 @@ static int step_impl(fga_state* st, int n_iter, cudaStream_t s) {
   for (int k = 0; k < n_iter; ++k) {
     int rc;
     if (p.profile) FGA_CUDA_TRY(cudaEventRecord(st->events[2 * st->timed], s));
-    if (p.method == FGA_BH)
-      rc = launch_bh(st->tree, st->Y0, st->M, st->ds, p.eps, p.theta, st->fb, s);
-    else
+    if (p.method == FGA_BH) {
+      rc = launch_bh(st->tree, st->Y0, st->M, st->ds, p.eps, p.theta, st->fb, s,
+                     st->bh_have_order ? st->bh_order : nullptr, st->bh_cost);
+      // heavy-first order for the following launches, refreshed on a schedule
+      // (the task costs drift slowly as the template moves)
+      ++st->bh_launches;
+      if (rc == FGA_OK && bh_reorder_due(st->bh_launches)) {
+        rc = launch_bh_order(st->bh_cost, st->bh_ntasks, st->bh_order, s);
+        st->bh_have_order = true;
+      }
+    } else {
       rc = launch_direct(st->X4, st->N, st->Y0, st->M, st->ds, p.eps, st->plan, st->fb, s);
+    }
     if (rc) return rc;
     if (p.profile) {
       FGA_CUDA_TRY(cudaEventRecord(st->events[2 * st->timed + 1], s));
@@ -674,6 +693,8 @@ void fga_state_destroy(fga_state* st) {
   dev_free(st->partials, s);
   dev_free(st->counter, s);
   dev_free(st->traj, s);
+  dev_free(st->bh_cost, s);
+  dev_free(st->bh_order, s);
   if (st->own_tree) fga_tree_destroy(st->own_tree);
   for (cudaEvent_t e : st->events) cudaEventDestroy(e);
   if (prev != st->device) cudaSetDevice(prev);

@@ -38,21 +38,28 @@ __device__ __forceinline__ int owner_of(const unsigned* __restrict__ start, int 
   return lo;
 }
 
-__global__ void __launch_bounds__(BATCH_WARPS * 32, 8) k_batch_force(const PairDev* __restrict__ pairs,
+#ifndef FGA_BATCH_MINBLOCKS
+#define FGA_BATCH_MINBLOCKS 8  // resident blocks per SM the register budget is sized for
+#endif
+__global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch_force(const PairDev* __restrict__ pairs,
                                                                      int npairs,
                                                                      const unsigned* __restrict__ task_start,
                                                                      unsigned ntasks, unsigned* ctr,
-                                                                     float eps2, float theta2) {
+                                                                     float eps2, float theta2,
+                                                                     const unsigned* __restrict__ order,
+                                                                     unsigned* __restrict__ cost) {
   __shared__ unsigned s_stack[BATCH_WARPS][BH_DEPTH][32];
   __shared__ float4 s_tile[BATCH_WARPS][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned* const stk = &s_stack[w][0][lane];
   bool overflow = false;
   for (;;) {
-    unsigned task = 0;
-    if (lane == 0) task = atomicAdd(&ctr[0], 1u);
-    task = __shfl_sync(FULL, task, 0);
-    if (task >= ntasks) break;
+    unsigned slot = 0;
+    if (lane == 0) slot = atomicAdd(&ctr[0], 1u);
+    slot = __shfl_sync(FULL, slot, 0);
+    if (slot >= ntasks) break;
+    unsigned task = order ? order[slot] : slot;
+    if (task >= ntasks) task = slot;  // never index past the task range
     const int k = owner_of(task_start, npairs, task);
     const PairDev& P = pairs[k];
     DevState* ds = P.ds;
@@ -68,8 +75,10 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, 8) k_batch_force(const PairD
     unsigned count = 0;
     const unsigned f = local - grp * (unsigned)P.K;
     if (P.method == FGA_BH) {
+      unsigned steps = 0;
       bh_task(P.rec, P.bodies, P.front, f, y, valid, eps2, theta2, stk, overflow, hx, hy, hz, lx, ly,
-              lz, count);
+              lz, count, steps);
+      if (cost && lane == 0) cost[task] = steps + 1u;
       if (__any_sync(FULL, overflow)) {
         if (lane == 0) atomicOr(&ds->status, 1);
         overflow = false;
@@ -77,6 +86,8 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, 8) k_batch_force(const PairD
     } else {
       const int64_t j0 = (int64_t)f * BATCH_CHUNK;
       const int64_t j1 = min(P.N, j0 + BATCH_CHUNK);
+      // a 32-source tile costs about as much as 8 Barnes-Hut walk steps
+      if (cost && lane == 0) cost[task] = 8u * (unsigned)((j1 - j0 + 31) / 32) + 1u;
       for (int64_t b = j0; b < j1; b += 32) {
         const int64_t j = b + lane;
         s_tile[w][lane] = j < j1 ? P.X4[j] : make_float4(0.f, 0.f, 0.f, 0.f);  // m = 0 pads
@@ -179,13 +190,26 @@ int batch_force_grid(unsigned ntasks) {
                         ((int64_t)ntasks + BATCH_WARPS - 1) / BATCH_WARPS);
 }
 
+__global__ void __launch_bounds__(1024) k_batch_order(const unsigned* __restrict__ cost, unsigned n,
+                                                      unsigned* __restrict__ order) {
+  order_by_cost(cost, n, order);
+}
+
+int launch_batch_order(const unsigned* cost, unsigned ntasks, unsigned* order, cudaStream_t s) {
+  if (ntasks == 0) return FGA_OK;
+  k_batch_order<<<1, 1024, 0, s>>>(cost, ntasks, order);
+  FGA_LAUNCH_CHECK("batch order");
+  return FGA_OK;
+}
+
 int launch_batch_iteration(const PairDev* d_pairs, int npairs, const unsigned* d_task_start,
                            unsigned ntasks, const unsigned* d_block_start, unsigned nblocks,
-                           unsigned* d_ctr, float eps2, float theta2, int fgrid, cudaStream_t s) {
+                           unsigned* d_ctr, float eps2, float theta2, int fgrid, cudaStream_t s,
+                           const unsigned* order, unsigned* cost) {
   if (npairs <= 0) return FGA_OK;
   if (ntasks > 0) {
     k_batch_force<<<fgrid, BATCH_WARPS * 32, 0, s>>>(d_pairs, npairs, d_task_start, ntasks, d_ctr, eps2,
-                                                     theta2);
+                                                     theta2, order, cost);
     FGA_LAUNCH_CHECK("batch force");
   }
   if (nblocks > 0) {
@@ -221,8 +245,8 @@ int64_t pair_bytes_bound(int64_t N, int64_t M, int method, const fga_params* p) 
     // tree: bodies, index, keys, node arrays (<= 2N nodes), records, sort scratch
     const int64_t nodes = 2 * N + 64;
     int64_t tree = f4 * N + 4 * N + 8 * N + nodes * (f4 + 16 + 2 * f4) + 2 * 16 * N +
-                   (int64_t)FRONT_TARGET * (int64_t)sizeof(FrontCell) + 32 * pad;
-    keep += tree + 4 * M + 2 * f4 * (int64_t)FRONT_TARGET * M;
+                   (int64_t)batch_front_target(N) * (int64_t)sizeof(FrontCell) + 32 * pad;
+    keep += tree + 4 * M + 2 * f4 * (int64_t)batch_front_target(N) * M;
   } else {
     const int64_t K = (N + BATCH_CHUNK - 1) / BATCH_CHUNK;
     keep += f4 * N + 2 * f4 * K * M;
@@ -243,7 +267,7 @@ int build_pair(const fga_pair& q, const Prepared& pr, const fga_params* p, Scrat
   if (sc.alloc(&Y0, q.M)) return FGA_ENOMEM;
   if (P.method == FGA_BH) {
     fga_tree* t = nullptr;
-    if ((rc = tree_build(pr.Xn, pr.mXn, q.N, p->max_depth, &t, s))) return rc;
+    if ((rc = tree_build(pr.Xn, pr.mXn, q.N, p->max_depth, &t, s, batch_front_target(q.N)))) return rc;
     *tree = t;
     int* perm = nullptr;
     if (sc.alloc(&perm, q.M)) return FGA_ENOMEM;
@@ -375,9 +399,10 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
     return FGA_EINVAL;
   }
   PairDev* d_pairs = nullptr;
-  unsigned *d_tstart = nullptr, *d_bstart = nullptr, *d_ctr = nullptr;
+  unsigned *d_tstart = nullptr, *d_bstart = nullptr, *d_ctr = nullptr, *d_cost = nullptr, *d_order = nullptr;
   if (sc.alloc(&d_pairs, (size_t)count) || sc.alloc(&d_tstart, (size_t)count + 1) ||
-      sc.alloc(&d_bstart, (size_t)count + 1) || sc.alloc(&d_ctr, 2))
+      sc.alloc(&d_bstart, (size_t)count + 1) || sc.alloc(&d_ctr, 2) ||
+      sc.alloc(&d_cost, (size_t)task_start[count] + 1) || sc.alloc(&d_order, (size_t)task_start[count] + 1))
     return FGA_ENOMEM;
   FGA_CUDA_TRY(cudaMemcpyAsync(d_pairs, order.data(), sizeof(PairDev) * count, cudaMemcpyHostToDevice, s));
   FGA_CUDA_TRY(cudaMemcpyAsync(d_tstart, task_start.data(), sizeof(unsigned) * (count + 1),
@@ -390,6 +415,23 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
   const unsigned ntasks = task_start[count], nblocks = block_start[count];
   const int fgrid = batch_force_grid(ntasks);
   const float eps2 = p->eps * p->eps, theta2 = p->theta * p->theta;
+  // iteration `it`: the force launch (heavy-first task order from the second
+  // iteration on, refreshed on the bh_reorder_due schedule), then the epilogue
+  bool have_order = false;  // d_order is written (by an earlier launch on the same stream)
+  auto force = [&](int it, cudaStream_t st) -> int {
+    int r = launch_batch_iteration(d_pairs, count, d_tstart, ntasks, d_bstart, 0, d_ctr, eps2, theta2,
+                                   fgrid, st, have_order ? d_order : nullptr, d_cost);
+    if (r == FGA_OK && bh_reorder_due(it + 1, FGA_BATCH_REORDER_EVERY)) {
+      r = launch_batch_order(d_cost, ntasks, d_order, st);
+      have_order = true;
+      count_launch(1);
+    }
+    return r;
+  };
+  auto epilogue = [&](cudaStream_t st) -> int {
+    return launch_batch_iteration(d_pairs, count, d_tstart, 0, d_bstart, nblocks, d_ctr, eps2, theta2,
+                                  fgrid, st);
+  };
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   cudaGraph_t graph = nullptr;
@@ -428,13 +470,9 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
     for (auto& e : evs) FGA_CUDA_TRY(cudaEventCreate(&e));
     for (int it = 0; it < p->max_iter; ++it) {
       FGA_CUDA_TRY(cudaEventRecord(evs[2 * it], cs));
-      if ((rc = launch_batch_iteration(d_pairs, count, d_tstart, ntasks, d_bstart, 0, d_ctr, eps2,
-                                       theta2, fgrid, cs)))
-        return rc;
+      if ((rc = force(it, cs))) return rc;
       FGA_CUDA_TRY(cudaEventRecord(evs[2 * it + 1], cs));
-      if ((rc = launch_batch_iteration(d_pairs, count, d_tstart, 0, d_bstart, nblocks, d_ctr, eps2,
-                                       theta2, fgrid, cs)))
-        return rc;
+      if ((rc = epilogue(cs))) return rc;
       count_launch(2);
     }
     FGA_CUDA_TRY(cudaStreamSynchronize(cs));
@@ -448,8 +486,8 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
     FGA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int lrc = FGA_OK;
     for (int it = 0; it < p->max_iter && lrc == FGA_OK; ++it) {
-      lrc = launch_batch_iteration(d_pairs, count, d_tstart, ntasks, d_bstart, nblocks, d_ctr, eps2,
-                                   theta2, fgrid, cs);
+      lrc = force(it, cs);
+      if (lrc == FGA_OK) lrc = epilogue(cs);
       count_launch(2);
     }
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);

@@ -308,15 +308,61 @@ static __device__ void rigid_step(const double* red, int64_t M, DevState* ds, co
 // monopole is added only when f owns the ancestor's first frontier cell),
 // then the depth-first walk of f's subtree with pending sibling ranges in
 // shared memory (stk: this lane's column, stride 32, depth bh_depth).
-// Adds into the compensated accumulators (hx, lx), ... and the term count.
+// Adds into the compensated accumulators (hx, lx), ... and the term count;
+// `steps` gains the number of warp-wide walk steps (the task's cost).
 // A lane with valid == false takes part in the warp-wide loop but adds nothing.
+// Heavy-first order of warp tasks for the next force launch, from the step
+// counts `cost` the previous launch recorded: tasks sorted by descending
+// floor(log2(cost)) (a counting sort over 32 buckets; order within a bucket
+// is arbitrary). The walk's cost of a (group, frontier cell) task hardly
+// changes between iterations, and the few tasks that hold a group's near
+// field take far longer than the rest; started first, they no longer decide
+// when the launch ends. Each task writes only its own partial-sum slot, so
+// the order never changes a result. Run by one block (any size, multiple of
+// 32).
+__device__ __forceinline__ void order_by_cost(const unsigned* __restrict__ cost, unsigned n,
+                                              unsigned* __restrict__ order) {
+  __shared__ unsigned hist[32];
+  __shared__ unsigned base[32];
+  const unsigned lane = threadIdx.x & 31u;
+  if (threadIdx.x < 32) hist[threadIdx.x] = 0u;
+  __syncthreads();
+  for (unsigned t0 = 0; t0 < n; t0 += blockDim.x) {
+    const unsigned t = t0 + threadIdx.x;
+    const bool v = t < n;
+    const unsigned b = v ? (unsigned)__clz(cost[t] | 1u) : 32u;  // heavier: smaller bucket
+    const unsigned peers = __match_any_sync(FULL, b);
+    if (v && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&hist[b], (unsigned)__popc(peers));
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned acc = 0;
+    for (int b = 0; b < 32; ++b) {
+      base[b] = acc;
+      acc += hist[b];
+    }
+  }
+  __syncthreads();
+  for (unsigned t0 = 0; t0 < n; t0 += blockDim.x) {
+    const unsigned t = t0 + threadIdx.x;
+    const bool v = t < n;
+    const unsigned b = v ? (unsigned)__clz(cost[t] | 1u) : 32u;
+    const unsigned peers = __match_any_sync(FULL, b);
+    const int leader = __ffs(peers) - 1;
+    unsigned start = 0;
+    if (v && (int)lane == leader) start = atomicAdd(&base[b], (unsigned)__popc(peers));
+    start = __shfl_sync(FULL, start, leader);
+    if (v) order[start + (unsigned)__popc(peers & ((1u << lane) - 1u))] = t;
+  }
+}
+
 constexpr int BH_DEPTH = 24;  // > 21 tree levels: one pending range per level
 
 __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const float4* __restrict__ bodies,
                                         const FrontCell* __restrict__ front, unsigned f, float3 y,
                                         bool valid, float eps2, float theta2, unsigned* stk,
                                         bool& overflow, float& hx, float& hy, float& hz, float& lx,
-                                        float& ly, float& lz, unsigned& count) {
+                                        float& ly, float& lz, unsigned& count, unsigned& steps) {
   float px = 0.f, py = 0.f, pz = 0.f;
   bool live = valid;
   {
@@ -346,6 +392,7 @@ __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const fl
   int sp = 0;               // saved ranges in shared memory
   int since_flush = 0;
   while (__any_sync(FULL, cnt > 0)) {
+    ++steps;
     if (cnt > 0) {
       const int v = cur;
       ++cur;

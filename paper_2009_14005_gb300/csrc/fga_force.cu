@@ -173,15 +173,23 @@ int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const
 // monopole is added by the task owning the ancestor's first frontier cell),
 // then walks the frontier cell's subtree. Tasks are handed out dynamically
 // from a counter in DevState; the last warp to finish resets it.
-static constexpr int BH_WARPS = 4;
+#ifndef FGA_BH_WARPS
+#define FGA_BH_WARPS 4
+#endif
+static constexpr int BH_WARPS = FGA_BH_WARPS;
 
-__global__ void __launch_bounds__(BH_WARPS * 32, 8) k_bh(const float4* __restrict__ rec,
+#ifndef FGA_BH_MINBLOCKS
+#define FGA_BH_MINBLOCKS 8  // resident blocks per SM the register budget is sized for
+#endif
+__global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const float4* __restrict__ rec,
                                                          const float4* __restrict__ bodies,
                                                          const float4* __restrict__ Y0, int64_t M,
                                                          const FrontCell* __restrict__ front, int K,
                                                          DevState* __restrict__ ds, float eps2,
                                                          float theta2, float4* __restrict__ hi_out,
-                                                         float4* __restrict__ lo_out) {
+                                                         float4* __restrict__ lo_out,
+                                                         const unsigned* __restrict__ order,
+                                                         unsigned* __restrict__ cost) {
   if (ds->done) return;
   __shared__ unsigned s_stack[BH_WARPS][BH_DEPTH][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -191,18 +199,22 @@ __global__ void __launch_bounds__(BH_WARPS * 32, 8) k_bh(const float4* __restric
   unsigned long long total = 0;
   bool overflow = false;
   for (;;) {
-    unsigned task = 0;
-    if (lane == 0) task = atomicAdd(&ds->bh_next, 1u);
-    task = __shfl_sync(FULL, task, 0);
-    if (task >= ntasks) break;
+    unsigned slot = 0;
+    if (lane == 0) slot = atomicAdd(&ds->bh_next, 1u);
+    slot = __shfl_sync(FULL, slot, 0);
+    if (slot >= ntasks) break;
+    unsigned task = order ? order[slot] : slot;
+    if (task >= ntasks) task = slot;  // never index past the task range
     const unsigned g = task / (unsigned)K, f = task % (unsigned)K;
     const int64_t i = (int64_t)g * 32 + lane;
     const bool valid = i < M;
     const float3 y = place(xf, Y0[valid ? i : 0]);
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
     unsigned count = 0;
+    unsigned steps = 0;
     bh_task(rec, bodies, front, f, y, valid, eps2, theta2, stk, overflow, hx, hy, hz, lx, ly, lz,
-            count);
+            count, steps);
+    if (cost && lane == 0) cost[task] = steps + 1u;
     if (valid) {
       hi_out[(int64_t)f * M + i] = make_float4(hx, hy, hz, 0.f);
       lo_out[(int64_t)f * M + i] = make_float4(lx, ly, lz, 0.f);
@@ -242,12 +254,23 @@ static int bh_grid(int64_t M, int K) {
 }
 
 int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, float eps,
-              float theta, ForceBuffers& fb, cudaStream_t s) {
+              float theta, ForceBuffers& fb, cudaStream_t s, const unsigned* order, unsigned* cost) {
   k_bh<<<bh_grid(M, t->n_front), BH_WARPS * 32, 0, s>>>(t->node_rec, t->bodies, Y0, M, t->front,
                                                         t->n_front, ds, eps * eps, theta * theta,
-                                                        fb.hi, fb.lo);
+                                                        fb.hi, fb.lo, order, cost);
   FGA_LAUNCH_CHECK("bh");
   fb.S = t->n_front;
+  return FGA_OK;
+}
+
+__global__ void __launch_bounds__(1024) k_bh_order(const unsigned* __restrict__ cost, unsigned n,
+                                                   unsigned* __restrict__ order) {
+  order_by_cost(cost, n, order);
+}
+
+int launch_bh_order(const unsigned* cost, unsigned ntasks, unsigned* order, cudaStream_t s) {
+  k_bh_order<<<1, 1024, 0, s>>>(cost, ntasks, order);
+  FGA_LAUNCH_CHECK("bh order");
   return FGA_OK;
 }
 

@@ -96,7 +96,22 @@ struct FrontCell {
   int path[FRONT_MAX_PATH];
   int pad;
 };
-constexpr int FRONT_TARGET = 32;  // frontier size the build aims for
+#ifndef FGA_FRONT_TARGET
+#define FGA_FRONT_TARGET 64
+#endif
+constexpr int FRONT_TARGET = FGA_FRONT_TARGET;  // frontier size the build aims for (and its cap)
+// Frontier size for trees of the batch executor and the server, whose launches
+// already hold many pairs' tasks: about one frontier cell per
+// FGA_BATCH_FRONT_BODIES reference points, at least 8 and at most
+// FRONT_TARGET (small pairs: few large tasks; large pairs: enough tasks that
+// none of them decides when the launch ends).
+#ifndef FGA_BATCH_FRONT_BODIES
+#define FGA_BATCH_FRONT_BODIES 4096
+#endif
+inline int batch_front_target(int64_t N) {
+  const int64_t k = (N + FGA_BATCH_FRONT_BODIES - 1) / FGA_BATCH_FRONT_BODIES;
+  return (int)(k < 8 ? 8 : (k > FRONT_TARGET ? FRONT_TARGET : k));
+}
 }  // namespace fga
 
 struct fga_tree {
@@ -151,7 +166,7 @@ int centroid4(const float4* p, int64_t n, double* d_out3, cudaStream_t s);
 
 // ------------------------------------------------------------------ tree (fga_tree.cu)
 int tree_build(const float* X, const float* mX, int64_t N, int max_depth, fga_tree** out,
-               cudaStream_t s);
+               cudaStream_t s, int front_target = FRONT_TARGET);
 
 // ------------------------------------------------------------------ forces (fga_force.cu)
 struct ForceBuffers {
@@ -174,8 +189,25 @@ void get_direct_tile(int size_class, int* bs, int* qpt);
 
 int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const DevState* ds,
                   float eps, const DirectPlan& plan, ForceBuffers& fb, cudaStream_t s);
+// order: heavy-first task order from launch_bh_order, or null (task index
+// order); cost: where each task's step count is recorded, or null.
 int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, float eps,
-              float theta, ForceBuffers& fb, cudaStream_t s);
+              float theta, ForceBuffers& fb, cudaStream_t s, const unsigned* order = nullptr,
+              unsigned* cost = nullptr);
+// Heavy-first order of ntasks tasks from their recorded costs (one block).
+// Refreshed after the first two force launches and then every
+// FGA_BH_REORDER_EVERY launches (0: never, tasks run in index order).
+#ifndef FGA_BH_REORDER_EVERY
+#define FGA_BH_REORDER_EVERY 8
+#endif
+inline bool bh_reorder_due(int launches_done, int every = FGA_BH_REORDER_EVERY) {
+  return every > 0 && (launches_done <= 2 || launches_done % every == 0);
+}
+// The same schedule for the batch executor and the server.
+#ifndef FGA_BATCH_REORDER_EVERY
+#define FGA_BATCH_REORDER_EVERY 8
+#endif
+int launch_bh_order(const unsigned* cost, unsigned ntasks, unsigned* order, cudaStream_t s);
 
 struct EpiParams {
   float G, dt, eta;

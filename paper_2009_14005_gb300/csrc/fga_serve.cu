@@ -247,6 +247,11 @@ struct Listing {
   int n = 0;
   unsigned ntasks = 0, nblocks = 0;
   int fgrid = 1;
+  unsigned* cost = nullptr;   // per-task cost of the last force launch
+  unsigned* order = nullptr;  // heavy-first order derived from it
+  size_t task_cap = 0;
+  int launches = 0;           // force launches since the listing changed
+  bool have_order = false;
 };
 
 int listing_reserve(Listing& L, size_t n, cudaStream_t s) {
@@ -371,6 +376,8 @@ class Runner {
     dev_free(L_.bstart, s_);
     dev_free(L_.flags, s_);
     dev_free(L_.ctr, s_);
+    dev_free(L_.cost, s_);
+    dev_free(L_.order, s_);
     cudaStreamSynchronize(s_);
   }
 
@@ -407,14 +414,34 @@ class Runner {
       L_.ntasks = ts[n];
       L_.nblocks = bs[n];
       L_.fgrid = batch_force_grid(L_.ntasks);
+      if (L_.ntasks > L_.task_cap) {
+        dev_free(L_.cost, s_);
+        dev_free(L_.order, s_);
+        L_.cost = L_.order = nullptr;
+        L_.task_cap = 0;
+        const size_t cap = std::max<size_t>(4096, 2 * (size_t)L_.ntasks);
+        if (dev_alloc_n(&L_.cost, cap, s_) || dev_alloc_n(&L_.order, cap, s_)) return FGA_ENOMEM;
+        L_.task_cap = cap;
+      }
+      // task indices changed: the next launch runs in index order and records costs
+      L_.launches = 0;
+      L_.have_order = false;
       dirty_ = false;
     } else if ((rc = stage_reserve(T, (size_t)L_.n))) {
       return rc;
     }
     const float eps2 = S_->p.eps * S_->p.eps, theta2 = S_->p.theta * S_->p.theta;
     for (int it = 0; it < S_->cfg.iters_per_tick; ++it) {
-      if ((rc = launch_batch_iteration(L_.pairs, L_.n, L_.tstart, L_.ntasks, L_.bstart, L_.nblocks, L_.ctr,
-                                       eps2, theta2, L_.fgrid, s_)))
+      if ((rc = launch_batch_iteration(L_.pairs, L_.n, L_.tstart, L_.ntasks, L_.bstart, 0, L_.ctr, eps2,
+                                       theta2, L_.fgrid, s_, L_.have_order ? L_.order : nullptr, L_.cost)))
+        return rc;
+      if (bh_reorder_due(++L_.launches, FGA_BATCH_REORDER_EVERY)) {
+        if ((rc = launch_batch_order(L_.cost, L_.ntasks, L_.order, s_))) return rc;
+        L_.have_order = true;
+        count_launch(1);
+      }
+      if ((rc = launch_batch_iteration(L_.pairs, L_.n, L_.tstart, 0, L_.bstart, L_.nblocks, L_.ctr, eps2,
+                                       theta2, L_.fgrid, s_)))
         return rc;
       count_launch(2);
     }

@@ -188,9 +188,9 @@ __global__ void k_mass_level(int L, const LevelInfo* __restrict__ lv, const floa
 
 // Frontier for splitting BH work (see FrontCell): starting from the root,
 // repeatedly replace the frontier cell holding the most bodies by its
-// children, until about FRONT_TARGET cells (never more than 32) or only
+// children, until about `target` cells (never more) or only
 // leaves remain. Uses the first levels of the breadth-first node arrays.
-static int build_frontier(fga_tree* T, cudaStream_t s) {
+static int build_frontier(fga_tree* T, int target, cudaStream_t s) {
   const int64_t P = std::min<int64_t>(T->n_nodes, 1 << 16);
   std::vector<int4> info(P);
   std::vector<int2> nb(P);
@@ -202,8 +202,8 @@ static int build_frontier(fga_tree* T, cudaStream_t s) {
     std::vector<int> path;
   };
   std::vector<Item> front{{0, {}}};
-  const int kMax = 32;
-  while ((int)front.size() < FRONT_TARGET) {
+  const int kMax = std::max(1, target);
+  while ((int)front.size() < kMax) {
     int best = -1, best_n = 1;
     for (int k = 0; k < (int)front.size(); ++k) {
       const int v = front[k].node;
@@ -256,7 +256,8 @@ __global__ void k_interleave(const float4* __restrict__ cm, const int4* __restri
   }
 }
 
-int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out, cudaStream_t s) {
+int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out, cudaStream_t s,
+               int front_target) {
   if (N > ((int64_t)1 << 26)) {
     set_error("tree_build: at most 2^26 points per tree");
     return FGA_EINVAL;
@@ -361,7 +362,7 @@ int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out
   }
   T->n_nodes = h_lv.start[D + 1];
   T->n_unique = (int)h_nu;
-  if ((rc = build_frontier(T, s))) {
+  if ((rc = build_frontier(T, front_target, s))) {
     fga_tree_destroy(T);
     return rc;
   }
