@@ -154,18 +154,26 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def source_hash(path):
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+DEVICE_HEADER = "paper_2009_14005_gb300/csrc/fga_device.cuh"
+
+
+def source_hash(paths):
+    """Hash of the kernel's source: its own file and the shared device header."""
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel_file: str, summary: str):
     """Per-launch DRAM bytes from a committed ncu summary, if it was taken on the
-    current source of the kernel (line 'traffic_bytes_per_launch: <B> source_sha: <h>')."""
+    current source of the kernel (line 'traffic_bytes_per_launch: <B> source_sha: <h>',
+    h = source_hash of the kernel's file and the shared device header)."""
     p = os.path.join(ROOT, "profiles", summary)
     if not os.path.exists(p):
         return None
-    cur = source_hash(os.path.join(ROOT, kernel_file))
+    cur = source_hash([os.path.join(ROOT, kernel_file), os.path.join(ROOT, DEVICE_HEADER)])
     for ln in open(p):
         if ln.startswith("traffic_bytes_per_launch:"):
             parts = ln.split()

@@ -386,23 +386,24 @@ __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const fl
       live = live && !accept;
     }
   }
-  // per-lane walk of the frontier cell's subtree
-  int cur = front[f].node;  // next cell of the current sibling range
-  int cnt = live ? 1 : 0;   // cells left in the current range
-  int sp = 0;               // saved ranges in shared memory
-  int since_flush = 0;
-  while (__any_sync(FULL, cnt > 0)) {
+  // per-lane walk of the frontier cell's subtree. The current sibling range is
+  // one word, e = next cell << 4 | cells left (at most 8), so advancing is
+  // e += 15; saved ranges use the same form.
+  unsigned e = live ? (((unsigned)front[f].node << 4) | 1u) : 0u;
+  int sp = 0;  // saved ranges in shared memory
+  while (__any_sync(FULL, (e & 15u) != 0u)) {
     ++steps;
-    if (cnt > 0) {
-      const int v = cur;
-      ++cur;
-      --cnt;
+    if ((e & 15u) != 0u) {
+      const int v = (int)(e >> 4);
+      e += 15u;
       const float4 cm = rec[2 * v];
       const float4 ri = rec[2 * v + 1];
       const int nchild = __float_as_int(ri.z);
       const float dx = cm.x - y.x, dy = cm.y - y.y, dz = cm.z - y.z;
       const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      const bool accept = nchild == -1 || ri.x < theta2 * d2;
+      // single-particle leaves carry l^2 = -1 in the traversal record, so the
+      // test accepts them (one exact term) without a separate leaf check
+      const bool accept = ri.x < theta2 * d2;
       const float inv = rsqrt_fast(d2 + eps2);
       const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
       px = fmaf(wgt, dx, px);
@@ -412,14 +413,13 @@ __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const fl
       // descend into an internal cell that fails the test: save the rest of
       // the current range, continue with the children (branch-free)
       const bool descend = !accept && nchild > 0;
-      const bool save = descend && cnt > 0;
+      const bool save = descend && (e & 15u) != 0u;
       if (save) {
-        if (sp < BH_DEPTH) stk[32 * sp] = ((unsigned)cur << 4) | (unsigned)cnt;
+        if (sp < BH_DEPTH) stk[32 * sp] = e;
         else overflow = true;
       }
       sp += save;
-      cur = descend ? __float_as_int(ri.y) : cur;
-      cnt = descend ? nchild : cnt;
+      e = descend ? (((unsigned)__float_as_int(ri.y) << 4) | (unsigned)nchild) : e;
       if (!accept && nchild < -1) {
         // leaf holding several particles: add each exactly (rare)
         const int b0 = __float_as_int(ri.y), nb = -nchild;
@@ -435,18 +435,15 @@ __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const fl
         count += (unsigned)nb;
       }
       // range exhausted: resume the innermost saved range
-      const bool pop = cnt == 0 && sp > 0;
+      const bool pop = (e & 15u) == 0u && sp > 0;
       sp -= pop;
-      const unsigned e = (pop && sp < BH_DEPTH) ? stk[32 * sp] : 0u;
-      cur = pop ? (int)(e >> 4) : cur;
-      cnt = pop ? (int)(e & 15u) : cnt;
+      e = (pop && sp < BH_DEPTH) ? stk[32 * sp] : e;
     }
-    if (++since_flush == 32) {
+    if ((steps & 31u) == 0u) {
       comp_add(hx, lx, px);
       comp_add(hy, ly, py);
       comp_add(hz, lz, pz);
       px = py = pz = 0.f;
-      since_flush = 0;
     }
   }
   comp_add(hx, lx, px);

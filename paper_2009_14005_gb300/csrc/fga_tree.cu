@@ -251,8 +251,10 @@ __global__ void k_interleave(const float4* __restrict__ cm, const int4* __restri
        i += (int64_t)gridDim.x * blockDim.x) {
     const int4 in = info[i];
     rec[2 * i] = cm[i];
-    rec[2 * i + 1] = make_float4(__int_as_float(in.x), __int_as_float(in.y), __int_as_float(in.z),
-                                 __int_as_float(in.w));
+    // a single-particle leaf is always added as its one exact term (its
+    // particle), accepted or not; l^2 = -1 makes the opening test accept it
+    const float l2 = in.z == -1 ? -1.0f : __int_as_float(in.x);
+    rec[2 * i + 1] = make_float4(l2, __int_as_float(in.y), __int_as_float(in.z), __int_as_float(in.w));
   }
 }
 

@@ -1,0 +1,97 @@
+"""Parity at the other full sizes the benchmark runs, on outputs the oracle
+can compute one by one.
+
+* Large inhomogeneous clouds: 1M x 1M piecewise-planar scene. Barnes-Hut
+  forces (Eq. 15) at theta 0.3 / 0.5 / 0.7 and the all-pairs force (Eq. 6),
+  both over the full 1M-point reference, on a sample of template points.
+* Batch: the benchmark's 256-pair batch (N, M log-uniform in [500, 50k])
+  registered in one call in the benchmark's launch configuration; pairs the
+  oracle finishes in seconds are checked against the oracle's registration.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module")
+def fga():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2009_14005_gb300 as m
+    return m
+
+
+def _cuda(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda")
+
+
+@pytest.fixture(scope="module")
+def big(orc):
+    X, Y, _, _ = synth.planar_scene_pair(1000, n=1_000_000)  # the planar workloads' first pair
+    Xn, Yn, _ = orc.normalize(X, Y)
+    Xn = Xn.astype(np.float32).astype(np.float64)
+    Yn = Yn.astype(np.float32).astype(np.float64)
+    mX = np.full(len(Xn), 1.0 / len(Xn))
+    idx = np.random.default_rng(7).choice(len(Yn), 1024, replace=False)
+    a_d, ab = orc.direct_acc(Xn, mX, Yn[idx], 66.7, 0.2, want_abs=True)
+    return Xn, Yn, mX, idx, a_d, ab
+
+
+@pytest.mark.parametrize("theta", [0.3, 0.5, 0.7])
+def test_1m_bh_forces_on_sample(fga, orc, big, theta):
+    Xn, Yn, mX, idx, a_d, _ = big
+    p = fga.params(theta=theta, G=66.7, eps=0.2)
+    t = fga.fga_tree_build(_cuda(Xn), _cuda(mX), p)
+    a, cnt = fga.fga_forces(t, None, None, _cuda(Yn), None, p, want_count=True)
+    a = a.cpu().numpy().astype(np.float64)[idx]
+    a_bo, c_o = orc.Tree(Xn, mX).bh_acc(Yn[idx], 66.7, 0.2, theta)
+    err_gpu = np.linalg.norm(a - a_d) / np.linalg.norm(a_d)
+    err_orc = np.linalg.norm(a_bo - a_d) / np.linalg.norm(a_d)
+    assert err_gpu <= err_orc + 1e-5, (err_gpu, err_orc)
+    close = np.linalg.norm(a - a_bo, axis=1) <= 1e-4 * np.linalg.norm(a_bo, axis=1) + 1e-6
+    assert close.mean() > 0.99
+    assert abs(cnt / len(Yn) - c_o.mean()) < 0.1 * c_o.mean()
+
+
+def test_1m_direct_forces_on_sample(fga, orc, big):
+    Xn, Yn, mX, idx, a_d, ab = big
+    a = fga.fga_forces(None, _cuda(Xn), _cuda(mX), _cuda(Yn), None,
+                       fga.params(G=66.7, eps=0.2)).cpu().numpy().astype(np.float64)[idx]
+    err = np.linalg.norm(a - a_d, axis=1)
+    assert np.all(err <= 1e-5 * ab), (err / ab).max()
+
+
+def test_full_batch_pairs_match_oracle(fga, orc):
+    pairs = synth.batch_pairs(1000, count=256)  # the batch workload's first batch
+    p = fga.params(method=fga.FGA_AUTO, theta=0.5, max_iter=100, G=66.7, eps=0.2, eta=0.2)
+    old = fga.fga_direct_max_n(4096)
+    try:
+        res, st = fga.fga_register_batch([(_cuda(X), _cuda(Y)) for X, Y, _, _ in pairs], p)
+    finally:
+        fga.fga_direct_max_n(old)
+    assert st["status"] in (fga.FGA_OK, fga.FGA_EDEGENERATE)
+    sizes = np.array([(len(X), len(Y)) for X, Y, _, _ in pairs])
+    direct = [k for k in range(len(pairs)) if sizes[k, 0] <= 4096]
+    bh = [k for k in range(len(pairs)) if sizes[k, 0] > 4096]
+    assert all(res[k]["method"] == fga.FGA_DIRECT for k in direct)
+    assert all(res[k]["method"] == fga.FGA_BH for k in bh)
+    # the cheapest pairs of each kind for the oracle
+    pick = sorted(direct, key=lambda k: sizes[k].prod())[:3] + sorted(bh, key=lambda k: sizes[k, 1])[:2]
+    import oracle
+    for k in pick:
+        X, Y, _, _ = pairs[k]
+        po = orc.Params(method=orc.FGA_DIRECT if k in direct else orc.FGA_BH, theta=0.5, max_iter=100,
+                        G=66.7, eps=0.2, eta=0.2)
+        o = orc.register_full(X, Y, po)
+        diag = float(np.linalg.norm(X.max(0) - X.min(0)))
+        dphi = oracle.rotation_error_deg(res[k]["R"], o["R"])
+        dt = float(np.linalg.norm(res[k]["t"] - o["t"])) / diag
+        assert dphi <= 0.01 and dt <= 1e-4, (k, sizes[k], dphi, dt)
+        assert res[k]["iterations"] == 100
