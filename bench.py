@@ -206,6 +206,11 @@ WORKLOADS = {
                   G=66.7, eps=0.2, eta=0.2),
     # served requests: Poisson arrivals at 200/s, N and M log-uniform in
     # [1k, 500k], overlap 30-100 %; one step = one request of the trace
+    # a parameter grid as one batch: a 1k-point anisotropic box and its copy
+    # under a 30 deg rotation, registered under 25 G x 20 eps x 20 eta = 10^4
+    # parameter cells, all-pairs forces; n = number of cells
+    "grid": dict(gen="grid", n=10_000, iters=100, method="direct", theta=0.5, niv=False,
+                 G=66.7, eps=0.05, eta=0.1),
     "serve": dict(gen="serve", n=500_000, iters=100, method="auto", theta=0.5, niv=False,
                   G=66.7, eps=0.2, eta=0.2, rate=200.0, lo=1000),
 }
@@ -222,7 +227,7 @@ def workload(a):
 
 def workload_config(a):
     w = workload(a)
-    if w["gen"] in ("batch", "serve"):
+    if w["gen"] in ("batch", "serve", "grid"):
         return special_config(a, w)
     name = "%s-%dk-%s%s-%dit" % (
         {"lidar": "lidar-sweeps", "sphere": "unit-sphere", "planar": "planar-scene",
@@ -236,6 +241,17 @@ def workload_config(a):
             "eps": w["eps"], "eta": w["eta"], "dt": 0.1, "G": w["G"], "pairs_per_rank": a.pairs,
             "l2": "flushed between steps (256 MB device write outside the timed events)",
             "inputs": "resident in HBM at the start of each timed step"}
+
+
+def grid_cells(n):
+    """(G, eps, eta) of the grid workload: log-spaced G in [1, 300] and eps in
+    [0.01, 0.5], linear eta in [0.02, 0.5]; the first n cells of the 25 x 20 x 20
+    grid (G slowest)."""
+    Gs = np.geomspace(1.0, 300.0, 25)
+    es = np.geomspace(0.01, 0.5, 20)
+    hs = np.linspace(0.02, 0.5, 20)
+    cells = [(g, e, h) for g in Gs for e in es for h in hs]
+    return cells[:n]
 
 
 def special_config(a, w):
@@ -252,6 +268,16 @@ def special_config(a, w):
                 "timing": "host clock: first arrival to last result; latency = submit to result on host",
                 "l2": "not flushed: the trace's inputs (hundreds of MB) exceed L2",
                 "inputs": "device-resident at submit (value); pinned host (e2e)"}
+    if w["gen"] == "grid":
+        return {"workload": "grid-%d-cells-box-1k-%dit" % (w["n"], w["iters"]), "cells": w["n"],
+                "pair": "1000 points uniform in a 2 x 1.2 x 0.6 box and the same points under a "
+                        "30 deg rotation and t = (0.1, -0.05, 0.08) (seed 0)",
+                "G": "25 values log-spaced in [1, 300]", "eps": "20 values log-spaced in [0.01, 0.5]",
+                "eta": "20 values in [0.02, 0.5]", "iterations": w["iters"], "method": "all-pairs",
+                "masses": "uniform", "dt": 0.1,
+                "l2": "flushed between steps (256 MB device write outside the timed events)",
+                "inputs": "resident in HBM at the start of each timed step; one preparation "
+                          "shared by all cells"}
     if w["gen"] == "batch":
         return {"workload": "batch-%d-pairs-500-50k-%dit" % (w["n"], w["iters"]), "pairs": w["n"],
                 "N_M": "log-uniform in [500, 50000], independently", "iterations": w["iters"],
@@ -268,6 +294,8 @@ def make_pairs(seeds, a):
     w = workload(a)
     if w["gen"] == "batch":
         return [synth.batch_pairs(s, count=w["n"]) for s in seeds]
+    if w["gen"] == "grid":
+        return [[synth.box_pair(0, n=1000, deg=30.0)] for s in seeds]
     if w["gen"] == "serve":
         tr = synth.serve_trace(seeds[0], max(a.steps, 1), rate=w["rate"], lo=w["lo"], hi=w["n"])
         return [[(X, Y, R, t) for _, X, Y, R, t in tr]]
@@ -292,7 +320,7 @@ def cpu_sample(pair, a, iters):
     import oracle
     oracle.build()
     w = workload(a)
-    if w["gen"] in ("batch", "serve"):
+    if w["gen"] in ("batch", "serve", "grid"):
         pair = pair[0]
         w = dict(w, method="direct" if len(pair[0]) <= 32768 else "bh")
     X, Y, _, _ = pair
@@ -571,6 +599,134 @@ def run_ours_batch(a):
     return 0
 
 
+def run_ours_grid(a):
+    """One step = one fga_register_batch over all cells of the parameter grid."""
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    __graft_entry__.build_library()
+    import paper_2009_14005_gb300 as fga
+
+    w = workload(a)
+    X, Y, R_gt, t_gt = synth.box_pair(rank, n=1000, deg=30.0)  # every rank its own pair (weak scaling)
+    Xd, Yd = torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda")
+    Xh, Yh = torch.from_numpy(X).pin_memory(), torch.from_numpy(Y).pin_memory()
+    cells = [fga.params(method=fga.FGA_DIRECT, G=float(g), eps=float(e), eta=float(h), max_iter=w["iters"])
+             for g, e, h in grid_cells(w["n"])]
+    base = fga.params(method=fga.FGA_DIRECT, max_iter=w["iters"])
+    batch = [(Xd, Yd, None, None, c) for c in cells]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    tuned = fga.autotune(base, stream=stream)
+    for _ in range(a.warmup):
+        fga.fga_register_batch(batch, base, stream=stream)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = fga.fga_launch_count()
+    step_ms, inter = [], 0
+    for k in range(a.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res, st = fga.fga_register_batch(batch, base, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        inter += st["interactions"]
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = fga.fga_launch_count() - launches0
+    clk = clocks.stop()
+    t_local = sum(step_ms)
+    t_max, inter_all = reduce_max_sum(t_local, float(inter), world)
+    value = inter_all / (t_max / 1e3)
+
+    # the map the grid is for: rotation error of every cell against the ground truth
+    import math
+    err = np.array([math.degrees(math.acos(max(-1.0, min(1.0, (np.trace(r["R"].T @ R_gt) - 1) / 2))))
+                    for r in res])
+    best = int(np.argmin(err))
+
+    # the force kernel alone: one profiled call on the first 1000 cells
+    pp = fga.params(method=fga.FGA_DIRECT, max_iter=w["iters"], profile=1)
+    _, pst = fga.fga_register_batch(batch[:1000], pp, stream=stream)
+    # the one-pair path on a sample of cells
+    sample = cells[:: max(1, len(cells) // 200)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in sample:
+        fga.fga_register(Xd, Yd, c, stream=stream)
+    torch.cuda.synchronize()
+    seq_s = time.perf_counter() - t0
+    # e2e: host inputs through the same call
+    e2e_t, h2d = 0.0, 0
+    hbatch = [(Xh, Yh, None, None, c) for c in cells]
+    for _ in range(a.e2e_steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res_h, st_h = fga.fga_register_batch(hbatch, base, stream=stream)
+        e2e_t += time.perf_counter() - t0
+        h2d = st_h["h2d_bytes"]
+    e2e_tmax, e2e_iall = reduce_max_sum(1e3 * e2e_t, float(inter / max(a.steps, 1) * a.e2e_steps), world)
+
+    if rank != 0:
+        return 0
+    peaks, peak_src = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_rate = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / FP32_INSTR_PER_INTERACTION
+    launch_inter = pst["interactions"] / max(pst["force_launches"], 1)
+    launch_s = pst["force_ms"] / 1e3 / max(pst["force_launches"], 1)
+    achieved = launch_inter / launch_s if launch_s > 0 else 0.0
+    roof = {"bound": "alu", "kernel": "k_batch_force", "achieved": achieved / 1e9,
+            "peak": peak_rate / 1e9, "unit": "Ginteractions/s", "frac": achieved / peak_rate,
+            "traffic": recorded_traffic("paper_2009_14005_gb300/csrc/fga_batch.cu",
+                                        "k_batch_force_%s.md" % a.workload),
+            "peak_source": "%d SMs x %d FP32 lanes x %.0f MHz (sm_max_mhz, %s) / %d FP32 "
+                           "instructions per interaction" % (sms, FP32_LANES_PER_SM, sm_mhz, peak_src,
+                                                             FP32_INSTR_PER_INTERACTION),
+            "launches": pst["force_launches"], "interactions_per_launch": launch_inter,
+            "mean_launch_ms": 1e3 * launch_s,
+            "measured_on": "fga_register_batch of the first 1000 cells, events around each force launch"}
+    n = len(cells)
+    line = {"metric": "pair-interactions/s", "value": value, "unit": "interactions/s",
+            "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": workload_config(a),
+            "registrations_per_s": n * a.steps * world / (t_max / 1e3),
+            "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
+            "grid_map": {"cells_within_1deg": float((err < 1.0).mean()),
+                         "cells_within_0.1deg": float((err < 0.1).mean()),
+                         "best": {"G": cells[best].G, "eps": cells[best].eps, "eta": cells[best].eta,
+                                  "rot_err_deg": float(err[best])},
+},
+            "one_pair_path": {"registrations_per_s": len(sample) / seq_s,
+                              "note": "%d cells of the grid, one fga_register call each" % len(sample)},
+            "e2e": {"value": e2e_iall / (e2e_tmax / 1e3) if e2e_tmax > 0 else None,
+                    "unit": "interactions/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": (8 * 12 + 64) * n,
+                    "ms_per_step": e2e_tmax / max(a.e2e_steps, 1)},
+            "gpu_launches": launches, "roofline": roof, "clocks": clk, "autotuned": tune_summary(tuned)}
+    if world == 1 and not a.no_cpu_baseline:
+        i, t, cores = cpu_sample([(X, Y, None, None)], a, a.cpu_iters)
+        line["cpu_baseline"] = {"value": i / t, "unit": "interactions/s", "cores": cores,
+                                "kind": "oracle",
+                                "sample": "FP64 C oracle (OpenMP), %d of %d iterations of one cell "
+                                          "(1000 x 1000, %.1f s)" % (a.cpu_iters, w["iters"], t)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def tune_summary(rep):
     return {"direct_max_n": rep["direct_max_n"],
             "direct_tiles": ["%dx%d" % (b, q) for b, q in zip(rep["direct_bs"], rep["direct_qpt"])],
@@ -730,6 +886,8 @@ def main(argv=None):
         return run_ours_batch(a)
     if workload(a)["gen"] == "serve":
         return run_ours_serve(a)
+    if workload(a)["gen"] == "grid":
+        return run_ours_grid(a)
     return run_ours(a)
 
 

@@ -265,6 +265,12 @@ typedef struct fga_pair {
   int64_t M;
   const float* mX; /* NULL: p->mass_mode, sum 1 */
   const float* mY; /* NULL: dt each              */
+  const fga_params* params; /* NULL: the call's (or server's) parameters;
+                               else this pair's own (G, eps, eta, dt, theta,
+                               max_iter, conv_tol, method, normalisation,
+                               masses, velocity mode, max_depth), e.g. one
+                               cell of a parameter grid (read during the
+                               call / at submission; profile is ignored)   */
 } fga_pair;
 
 typedef struct fga_pair_result {
@@ -283,7 +289,9 @@ typedef struct fga_pair_result {
  * in its own block), and the p->max_iter iterations are captured in one CUDA
  * graph. With p->method == FGA_AUTO each pair takes the all-pairs sum when
  * N <= fga_direct_max_n(0) and Barnes-Hut otherwise. A pair whose stop test
- * fires (conv_tol > 0) skips the remaining work. Results per pair go to
+ * fires (conv_tol > 0) skips the remaining work. A pair with its own
+ * parameters (fga_pair.params) is registered with those: the loop runs the
+ * largest max_iter of all pairs and each pair stops at its own. Results per pair go to
  * results[count] (host). stats (optional): total interactions, elapsed_ms =
  * whole call, force_ms = the iteration graph. Synchronises `stream`.
  * Errors: FGA_EINVAL (any pair invalid; message names it), FGA_ENOMEM,
@@ -394,7 +402,9 @@ typedef struct fga_server_stats {
  * Errors: FGA_EINVAL (bad parameters), FGA_ECUDA, FGA_ENOMEM. */
 int fga_server_create(const fga_params* p, const fga_server_config* cfg, fga_server** out);
 
-/* Queues one request and returns its ticket (> 0) in *ticket. X, Y, mX, mY
+/* Queues one request and returns its ticket (> 0) in *ticket. req->params,
+ * if set, replaces the server's parameters for this request (copied at
+ * submission; max_iter >= 1). X, Y, mX, mY
  * may be host or device pointers; they are read during preparation (on the
  * server's own stream, so device data must be complete when submitted) and
  * must stay valid until the request's result has been polled. Never waits

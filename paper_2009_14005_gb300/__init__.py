@@ -89,7 +89,8 @@ class fga_stats(ctypes.Structure):
 
 class fga_pair(ctypes.Structure):
     _fields_ = [("X", ctypes.c_void_p), ("N", ctypes.c_int64), ("Y", ctypes.c_void_p),
-                ("M", ctypes.c_int64), ("mX", ctypes.c_void_p), ("mY", ctypes.c_void_p)]
+                ("M", ctypes.c_int64), ("mX", ctypes.c_void_p), ("mY", ctypes.c_void_p),
+                ("params", ctypes.c_void_p)]
 
 
 class fga_pair_result(ctypes.Structure):
@@ -494,9 +495,11 @@ def fga_direct_max_n(new_value: int = 0) -> int:
 def fga_register_batch(pairs, p: fga_params | None = None, stream=None):
     """Register many (X, Y) pairs together (one graph-captured loop for all).
 
-    ``pairs``: list of (X, Y) or (X, Y, mX, mY); arrays may be CUDA tensors or
-    host arrays. Returns (list of dicts with R, t, method, iterations,
-    converged, status, interactions; stats dict)."""
+    ``pairs``: list of (X, Y), (X, Y, mX, mY) or (X, Y, mX, mY, params) where
+    params (an ``fga_params``, or None) replaces ``p`` for that pair, e.g. one
+    cell of a parameter grid; arrays may be CUDA tensors or host arrays.
+    Returns (list of dicts with R, t, method, iterations, converged, status,
+    interactions; stats dict)."""
     torch = _torch()
     p = p or params()
     keep = []
@@ -517,10 +520,14 @@ def fga_register_batch(pairs, p: fga_params | None = None, stream=None):
         X, Y = pr[0], pr[1]
         mX = pr[2] if len(pr) > 2 else None
         mY = pr[3] if len(pr) > 3 else None
+        pk = pr[4] if len(pr) > 4 else None
         Xt, Yt, mXt, mYt = arr(X, 3), arr(Y, 3), arr(mX, None), arr(mY, None)
+        if pk is not None:
+            keep.append(pk)
         cp[k] = fga_pair(Xt.data_ptr(), Xt.shape[0], Yt.data_ptr(), Yt.shape[0],
                          mXt.data_ptr() if mXt is not None else None,
-                         mYt.data_ptr() if mYt is not None else None)
+                         mYt.data_ptr() if mYt is not None else None,
+                         ctypes.addressof(pk) if pk is not None else None)
     res = (fga_pair_result * n)()
     st = fga_stats()
     code = lib.fga_register_batch(cp, n, ctypes.byref(p), res, ctypes.byref(st), _stream(stream))
@@ -579,7 +586,7 @@ class Server:
         _err(lib.fga_server_create(ctypes.byref(p or params()), ctypes.byref(cfg), ctypes.byref(self._h)))
         self._keep = {}
 
-    def submit(self, X, Y, mX=None, mY=None) -> int:
+    def submit(self, X, Y, mX=None, mY=None, params: fga_params | None = None) -> int:
         torch = _torch()
         held = []
 
@@ -599,7 +606,8 @@ class Server:
             torch.cuda.current_stream(Xt.device if Xt.is_cuda else Yt.device).synchronize()
         q = fga_pair(Xt.data_ptr(), Xt.shape[0], Yt.data_ptr(), Yt.shape[0],
                      mXt.data_ptr() if mXt is not None else None,
-                     mYt.data_ptr() if mYt is not None else None)
+                     mYt.data_ptr() if mYt is not None else None,
+                     ctypes.addressof(params) if params is not None else None)
         ticket = ctypes.c_int64()
         _err(lib.fga_server_submit(self._h, ctypes.byref(q), ctypes.byref(ticket)))
         self._keep[int(ticket.value)] = held

@@ -18,6 +18,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <vector>
 
 #include "fga_batch.cuh"
@@ -45,7 +46,6 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch
                                                                      int npairs,
                                                                      const unsigned* __restrict__ task_start,
                                                                      unsigned ntasks, unsigned* ctr,
-                                                                     float eps2, float theta2,
                                                                      const unsigned* __restrict__ order,
                                                                      unsigned* __restrict__ cost) {
   __shared__ unsigned s_stack[BATCH_WARPS][BH_DEPTH][32];
@@ -65,6 +65,7 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch
     DevState* ds = P.ds;
     if (ds->done) continue;
     const int64_t M = P.M;
+    const float eps2 = P.eps2, theta2 = P.theta2;
     const unsigned local = task - task_start[k];
     const unsigned grp = local / (unsigned)P.K;
     const int64_t i = (int64_t)grp * 32 + lane;
@@ -204,12 +205,12 @@ int launch_batch_order(const unsigned* cost, unsigned ntasks, unsigned* order, c
 
 int launch_batch_iteration(const PairDev* d_pairs, int npairs, const unsigned* d_task_start,
                            unsigned ntasks, const unsigned* d_block_start, unsigned nblocks,
-                           unsigned* d_ctr, float eps2, float theta2, int fgrid, cudaStream_t s,
+                           unsigned* d_ctr, int fgrid, cudaStream_t s,
                            const unsigned* order, unsigned* cost) {
   if (npairs <= 0) return FGA_OK;
   if (ntasks > 0) {
-    k_batch_force<<<fgrid, BATCH_WARPS * 32, 0, s>>>(d_pairs, npairs, d_task_start, ntasks, d_ctr, eps2,
-                                                     theta2, order, cost);
+    k_batch_force<<<fgrid, BATCH_WARPS * 32, 0, s>>>(d_pairs, npairs, d_task_start, ntasks, d_ctr, order,
+                                                     cost);
     FGA_LAUNCH_CHECK("batch force");
   }
   if (nblocks > 0) {
@@ -255,8 +256,8 @@ int64_t pair_bytes_bound(int64_t N, int64_t M, int method, const fga_params* p) 
   return prep + keep;
 }
 
-int build_pair(const fga_pair& q, const Prepared& pr, const fga_params* p, Scratch& sc,
-               fga_tree** tree, DevState* ds, PairDev& P, cudaStream_t s) {
+int build_inputs(const fga_pair& q, const Prepared& pr, const fga_params* p, Scratch& sc,
+                 fga_tree** tree, PairDev& P, double** mu0, cudaStream_t s) {
   int rc = 0;
   *tree = nullptr;
   std::memset(&P, 0, sizeof(P));
@@ -264,7 +265,7 @@ int build_pair(const fga_pair& q, const Prepared& pr, const fga_params* p, Scrat
   P.N = q.N;
   P.M = q.M;
   float4* Y0 = nullptr;
-  if (sc.alloc(&Y0, q.M)) return FGA_ENOMEM;
+  if (sc.alloc(&Y0, q.M) || sc.alloc(mu0, 3)) return FGA_ENOMEM;
   if (P.method == FGA_BH) {
     fga_tree* t = nullptr;
     if ((rc = tree_build(pr.Xn, pr.mXn, q.N, p->max_depth, &t, s, batch_front_target(q.N)))) return rc;
@@ -285,21 +286,37 @@ int build_pair(const fga_pair& q, const Prepared& pr, const fga_params* p, Scrat
     P.K = (int)((q.N + BATCH_CHUNK - 1) / BATCH_CHUNK);
   }
   P.Y0 = Y0;
+  return centroid4(Y0, q.M, *mu0, s);
+}
+
+int build_state(const fga_params* p, const double* mu0, Scratch& sc, DevState* ds, PairDev& P,
+                cudaStream_t s) {
+  int rc = 0;
+  const int64_t M = P.M;
   P.ds = ds;
-  P.nblk = epilogue_blocks(q.M);
-  double* mu0 = nullptr;
-  if (sc.alloc(&P.hi, (size_t)P.K * q.M) || sc.alloc(&P.lo, (size_t)P.K * q.M) ||
-      sc.alloc(&P.V, q.M) || sc.alloc(&P.partials, (size_t)P.nblk * NRED) || sc.alloc(&P.counter, 1) ||
-      sc.alloc(&mu0, 3))
+  P.nblk = epilogue_blocks(M);
+  if (sc.alloc(&P.hi, (size_t)P.K * M) || sc.alloc(&P.lo, (size_t)P.K * M) || sc.alloc(&P.V, M) ||
+      sc.alloc(&P.partials, (size_t)P.nblk * NRED) || sc.alloc(&P.counter, 1))
     return FGA_ENOMEM;
-  FGA_CUDA_TRY(cudaMemsetAsync(P.V, 0, sizeof(float4) * q.M, s));
+  FGA_CUDA_TRY(cudaMemsetAsync(P.V, 0, sizeof(float4) * M, s));
   FGA_CUDA_TRY(cudaMemsetAsync(P.counter, 0, sizeof(unsigned), s));
-  if ((rc = centroid4(Y0, q.M, mu0, s))) return rc;
   if ((rc = launch_state_init(ds, mu0, s))) return rc;
+  // no iterations at all: the pair starts finished (max_iter = 0 in EpiParams
+  // would mean "no limit")
+  if (p->max_iter <= 0) FGA_CUDA_TRY(cudaMemsetAsync(&ds->done, 1, sizeof(int), s));
   P.ep = EpiParams{p->G, p->dt, p->eta, p->velocity_mode, (double)p->conv_tol, 0,
-                   1.0 / (double)q.M, 1.0 / (double)p->dt, p->max_iter};
-  P.inter_add = P.method == FGA_BH ? 0ull : (unsigned long long)(q.N * q.M);
+                   1.0 / (double)M, 1.0 / (double)p->dt, p->max_iter};
+  P.inter_add = P.method == FGA_BH ? 0ull : (unsigned long long)(P.N * M);
+  P.eps2 = p->eps * p->eps;
+  P.theta2 = p->theta * p->theta;
   return FGA_OK;
+}
+
+int build_pair(const fga_pair& q, const Prepared& pr, const fga_params* p, Scratch& sc,
+               fga_tree** tree, DevState* ds, PairDev& P, cudaStream_t s) {
+  double* mu0 = nullptr;
+  const int rc = build_inputs(q, pr, p, sc, tree, P, &mu0, s);
+  return rc ? rc : build_state(p, mu0, sc, ds, P, s);
 }
 
 void fill_pair_result(const DevState& h, const double* info, int method, const fga_params* p,
@@ -351,12 +368,21 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
   }
   int rc = check_register_params(p);
   if (rc) return rc;
+  // each pair's parameters: its own, or the call's
+  std::vector<const fga_params*> pp(count);
+  int iters = 0;
   for (int k = 0; k < count; ++k) {
     const fga_pair& q = pairs[k];
     if (!q.X || !q.Y || q.N <= 0 || q.M <= 0 || q.N > ((int64_t)1 << 26) || q.M > ((int64_t)1 << 26)) {
       set_error("fga_register_batch: bad sizes or null points in pair " + std::to_string(k));
       return FGA_EINVAL;
     }
+    pp[k] = q.params ? q.params : p;
+    if (q.params && (rc = check_register_params(q.params))) {
+      set_error("fga_register_batch: parameters of pair " + std::to_string(k) + ": " + fga_last_error());
+      return rc;
+    }
+    iters = std::max(iters, pp[k]->max_iter);
   }
   Scratch sc(s);
   std::vector<fga_tree*> trees;
@@ -366,27 +392,59 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
       for (fga_tree* t : trees) fga_tree_destroy(t);
     }
   } cleanup{trees};
+  // Pairs with the same inputs and the same input-shaping parameters (e.g.
+  // the cells of a parameter grid over one pair) share one preparation: the
+  // normalised clouds, masses, tree or packed reference and packed template.
+  std::vector<int> src(count);
+  {
+    std::map<std::vector<uint64_t>, int> first;
+    for (int k = 0; k < count; ++k) {
+      const fga_pair& q = pairs[k];
+      const fga_params* pk = pp[k];
+      const int method = resolve_method(pk, q.N);
+      auto bits = [](float f) {
+        uint32_t u;
+        std::memcpy(&u, &f, 4);
+        return (uint64_t)u;
+      };
+      const std::vector<uint64_t> key = {
+          (uint64_t)(uintptr_t)q.X, (uint64_t)q.N, (uint64_t)(uintptr_t)q.Y, (uint64_t)q.M,
+          (uint64_t)(uintptr_t)q.mX, (uint64_t)(uintptr_t)q.mY, (uint64_t)pk->normalize,
+          pk->normalize ? bits(pk->a) : 0, pk->normalize ? bits(pk->b) : 0, (uint64_t)pk->mass_mode,
+          pk->mass_mode == FGA_MASS_NIV ? (uint64_t)pk->lattice : 0, bits(pk->dt), (uint64_t)method,
+          method == FGA_BH ? (uint64_t)pk->max_depth : 0};
+      src[k] = first.emplace(key, k).first->second;
+    }
+  }
   int64_t h2d = 0;
   std::vector<Prepared> prep(count);
   std::vector<PairDev> host(count);
+  std::vector<double*> mu0(count, nullptr);
   DevState* dsarr = nullptr;
   if (sc.alloc(&dsarr, (size_t)count)) return FGA_ENOMEM;
   for (int k = 0; k < count; ++k) {
     const fga_pair& q = pairs[k];
-    if ((rc = prepare_inputs(sc, q.X, q.N, q.Y, q.M, q.mX, q.mY, p, prep[k], h2d, s))) return rc;
+    if (src[k] != k) continue;
+    if ((rc = prepare_inputs(sc, q.X, q.N, q.Y, q.M, q.mX, q.mY, pp[k], prep[k], h2d, s))) return rc;
   }
   // all checks of all pairs with one synchronisation
   std::vector<int> flags((size_t)8 * count);
   for (int k = 0; k < count; ++k)
-    FGA_CUDA_TRY(cudaMemcpyAsync(&flags[8 * k], prep[k].flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    if (src[k] == k)
+      FGA_CUDA_TRY(cudaMemcpyAsync(&flags[8 * k], prep[k].flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaStreamSynchronize(s));
   for (int k = 0; k < count; ++k)
-    if ((rc = check_pair_flags(&flags[8 * k], "fga_register_batch", k))) return rc;
+    if (src[k] == k && (rc = check_pair_flags(&flags[8 * k], "fga_register_batch", k))) return rc;
   for (int k = 0; k < count; ++k) {
+    if (src[k] != k) continue;
     fga_tree* t = nullptr;
-    rc = build_pair(pairs[k], prep[k], p, sc, &t, dsarr + k, host[k], s);
+    rc = build_inputs(pairs[k], prep[k], pp[k], sc, &t, host[k], &mu0[k], s);
     if (t) trees.push_back(t);
     if (rc) return rc;
+  }
+  for (int k = 0; k < count; ++k) {
+    host[k] = host[src[k]];
+    if ((rc = build_state(pp[k], mu0[src[k]], sc, dsarr + k, host[k], s))) return rc;
   }
   // Barnes-Hut pairs (usually the heaviest tasks) are handed out first
   std::vector<PairDev> order;
@@ -414,13 +472,11 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
   // the iteration loop as one CUDA graph on a private stream ordered after s
   const unsigned ntasks = task_start[count], nblocks = block_start[count];
   const int fgrid = batch_force_grid(ntasks);
-  const float eps2 = p->eps * p->eps, theta2 = p->theta * p->theta;
   // iteration `it`: the force launch (heavy-first task order from the second
   // iteration on, refreshed on the bh_reorder_due schedule), then the epilogue
   bool have_order = false;  // d_order is written (by an earlier launch on the same stream)
   auto force = [&](int it, cudaStream_t st) -> int {
-    int r = launch_batch_iteration(d_pairs, count, d_tstart, ntasks, d_bstart, 0, d_ctr, eps2, theta2,
-                                   fgrid, st, have_order ? d_order : nullptr, d_cost);
+    int r = launch_batch_iteration(d_pairs, count, d_tstart, ntasks, d_bstart, 0, d_ctr, fgrid, st, have_order ? d_order : nullptr, d_cost);
     if (r == FGA_OK && bh_reorder_due(it + 1, FGA_BATCH_REORDER_EVERY)) {
       r = launch_batch_order(d_cost, ntasks, d_order, st);
       have_order = true;
@@ -429,8 +485,7 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
     return r;
   };
   auto epilogue = [&](cudaStream_t st) -> int {
-    return launch_batch_iteration(d_pairs, count, d_tstart, 0, d_bstart, nblocks, d_ctr, eps2, theta2,
-                                  fgrid, st);
+    return launch_batch_iteration(d_pairs, count, d_tstart, 0, d_bstart, nblocks, d_ctr, fgrid, st);
   };
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -457,9 +512,9 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
   FGA_CUDA_TRY(cudaStreamWaitEvent(cs, ev_in, 0));
   double prof_ms = 0.0;
   int prof_launches = 0;
-  if (p->max_iter > 0 && p->profile) {
+  if (iters > 0 && p->profile) {
     // profiling: plain launches with a pair of events around every force launch
-    std::vector<cudaEvent_t> evs((size_t)2 * p->max_iter, nullptr);
+    std::vector<cudaEvent_t> evs((size_t)2 * iters, nullptr);
     struct EvCleanup {
       std::vector<cudaEvent_t>& v;
       ~EvCleanup() {
@@ -468,7 +523,7 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
       }
     } evclean{evs};
     for (auto& e : evs) FGA_CUDA_TRY(cudaEventCreate(&e));
-    for (int it = 0; it < p->max_iter; ++it) {
+    for (int it = 0; it < iters; ++it) {
       FGA_CUDA_TRY(cudaEventRecord(evs[2 * it], cs));
       if ((rc = force(it, cs))) return rc;
       FGA_CUDA_TRY(cudaEventRecord(evs[2 * it + 1], cs));
@@ -476,16 +531,16 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
       count_launch(2);
     }
     FGA_CUDA_TRY(cudaStreamSynchronize(cs));
-    for (int it = 0; it < p->max_iter; ++it) {
+    for (int it = 0; it < iters; ++it) {
       float ms = 0.f;
       FGA_CUDA_TRY(cudaEventElapsedTime(&ms, evs[2 * it], evs[2 * it + 1]));
       prof_ms += ms;
     }
-    prof_launches = p->max_iter;
-  } else if (p->max_iter > 0) {
+    prof_launches = iters;
+  } else if (iters > 0) {
     FGA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     int lrc = FGA_OK;
-    for (int it = 0; it < p->max_iter && lrc == FGA_OK; ++it) {
+    for (int it = 0; it < iters && lrc == FGA_OK; ++it) {
       lrc = force(it, cs);
       if (lrc == FGA_OK) lrc = epilogue(cs);
       count_launch(2);
@@ -505,20 +560,21 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
   std::vector<double> infos((size_t)8 * count);
   FGA_CUDA_TRY(cudaMemcpyAsync(hs.data(), dsarr, sizeof(DevState) * count, cudaMemcpyDeviceToHost, s));
   for (int k = 0; k < count; ++k)
-    FGA_CUDA_TRY(cudaMemcpyAsync(&infos[8 * k], prep[k].info, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (src[k] == k)
+      FGA_CUDA_TRY(cudaMemcpyAsync(&infos[8 * k], prep[k].info, 8 * sizeof(double), cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaStreamSynchronize(s));
   const auto t_end = std::chrono::steady_clock::now();
   int code = FGA_OK;
   int64_t total = 0;
   for (int k = 0; k < count; ++k) {
-    fill_pair_result(hs[k], &infos[8 * k], host[k].method, p, results[k]);
+    fill_pair_result(hs[k], &infos[8 * src[k]], host[k].method, pp[k], results[k]);
     if (results[k].status == FGA_EINTERNAL) code = FGA_EINTERNAL;
     else if (results[k].status == FGA_EDEGENERATE && code == FGA_OK) code = FGA_EDEGENERATE;
     total += results[k].interactions;
   }
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
-    stats->iterations = p->max_iter;
+    stats->iterations = iters;
     stats->interactions = total;
     stats->status = code;
     stats->h2d_bytes = h2d;

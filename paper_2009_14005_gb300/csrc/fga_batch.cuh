@@ -31,6 +31,7 @@ struct PairDev {
   int nblk;                   // epilogue blocks of this pair
   EpiParams ep;
   unsigned long long inter_add;  // direct: N*M terms per iteration
+  float eps2, theta2;            // this pair's softening and opening parameters, squared
 };
 
 // Builds the resident data of one prepared pair (tree or packed reference,
@@ -39,6 +40,14 @@ struct PairDev {
 // The tree, if any, is returned in *tree (owned by the caller).
 int build_pair(const fga_pair& q, const Prepared& pr, const fga_params* p, Scratch& keep,
                fga_tree** tree, DevState* ds, PairDev& P, cudaStream_t s);
+// The two halves of build_pair. build_inputs: the read-only inputs of the
+// pair (method, tree or packed reference, packed template, its centroid in
+// *mu0), which pairs with the same inputs may share. build_state: this pair's
+// own state, velocities, partial sums and parameters, on inputs already in P.
+int build_inputs(const fga_pair& q, const Prepared& pr, const fga_params* p, Scratch& keep,
+                 fga_tree** tree, PairDev& P, double** mu0, cudaStream_t s);
+int build_state(const fga_params* p, const double* mu0, Scratch& keep, DevState* ds, PairDev& P,
+                cudaStream_t s);
 
 // Work layout of a batch of pairs (in the order of `pairs`): pair k owns warp
 // tasks task_start[k] .. task_start[k+1]-1 (task = group * K + f: 32-point
@@ -73,7 +82,7 @@ int batch_force_grid(unsigned ntasks);
 // each task's cost is recorded, or null (see order_by_cost).
 int launch_batch_iteration(const PairDev* d_pairs, int npairs, const unsigned* d_task_start,
                            unsigned ntasks, const unsigned* d_block_start, unsigned nblocks,
-                           unsigned* d_ctr, float eps2, float theta2, int fgrid, cudaStream_t s,
+                           unsigned* d_ctr, int fgrid, cudaStream_t s,
                            const unsigned* order = nullptr, unsigned* cost = nullptr);
 
 // Heavy-first order of ntasks batch tasks from their recorded costs.

@@ -40,6 +40,7 @@ using Clock = std::chrono::steady_clock;
 struct Request {
   int64_t ticket = 0;
   fga_pair q{};
+  fga_params prm{};  // this request's parameters (its own or the server's)
   int64_t charge = 0;
   double work = 0;  // estimated force terms per iteration
   double submit_ms = 0;
@@ -120,14 +121,14 @@ int prepare_slot(fga_server* S, Slot& sl) {
   Prepared pr;
   Scratch tmp(s);  // staged inputs and normalised copies, freed after setup
   sl.keep.reset(new Scratch(s));
-  int rc = prepare_inputs(tmp, q.X, q.N, q.Y, q.M, q.mX, q.mY, &S->p, pr, h2d, s);
+  int rc = prepare_inputs(tmp, q.X, q.N, q.Y, q.M, q.mX, q.mY, &sl.req.prm, pr, h2d, s);
   if (rc) return rc;
   int flags[8];
   FGA_CUDA_TRY(cudaMemcpyAsync(flags, pr.flags, sizeof(flags), cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaStreamSynchronize(s));
   if ((rc = check_pair_flags(flags, "fga_server", sl.req.ticket))) return rc;
   if (sl.keep->alloc(&sl.ds, 1)) return FGA_ENOMEM;
-  if ((rc = build_pair(q, pr, &S->p, *sl.keep, &sl.tree, sl.ds, sl.P, s))) return rc;
+  if ((rc = build_pair(q, pr, &sl.req.prm, *sl.keep, &sl.tree, sl.ds, sl.P, s))) return rc;
   FGA_CUDA_TRY(cudaMemcpyAsync(sl.info, pr.info, sizeof(sl.info), cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaStreamSynchronize(s));
   return FGA_OK;
@@ -430,18 +431,17 @@ class Runner {
     } else if ((rc = stage_reserve(T, (size_t)L_.n))) {
       return rc;
     }
-    const float eps2 = S_->p.eps * S_->p.eps, theta2 = S_->p.theta * S_->p.theta;
     for (int it = 0; it < S_->cfg.iters_per_tick; ++it) {
-      if ((rc = launch_batch_iteration(L_.pairs, L_.n, L_.tstart, L_.ntasks, L_.bstart, 0, L_.ctr, eps2,
-                                       theta2, L_.fgrid, s_, L_.have_order ? L_.order : nullptr, L_.cost)))
+      if ((rc = launch_batch_iteration(L_.pairs, L_.n, L_.tstart, L_.ntasks, L_.bstart, 0, L_.ctr, L_.fgrid,
+                                       s_, L_.have_order ? L_.order : nullptr, L_.cost)))
         return rc;
       if (bh_reorder_due(++L_.launches, FGA_BATCH_REORDER_EVERY)) {
         if ((rc = launch_batch_order(L_.cost, L_.ntasks, L_.order, s_))) return rc;
         L_.have_order = true;
         count_launch(1);
       }
-      if ((rc = launch_batch_iteration(L_.pairs, L_.n, L_.tstart, 0, L_.bstart, L_.nblocks, L_.ctr, eps2,
-                                       theta2, L_.fgrid, s_)))
+      if ((rc = launch_batch_iteration(L_.pairs, L_.n, L_.tstart, 0, L_.bstart, L_.nblocks, L_.ctr, L_.fgrid,
+                                       s_)))
         return rc;
       count_launch(2);
     }
@@ -494,7 +494,7 @@ class Runner {
       fga_served& o = outs[j];
       std::memset(&o, 0, sizeof(o));
       o.ticket = sl.req.ticket;
-      fill_pair_result(h_states_[j], sl.info, sl.P.method, &S_->p, o.result);
+      fill_pair_result(h_states_[j], sl.info, sl.P.method, &sl.req.prm, o.result);
       o.submit_ms = sl.req.submit_ms;
       o.admit_ms = sl.admit_ms;
       o.start_ms = sl.start_ms;
@@ -605,8 +605,19 @@ extern "C" int fga_server_submit(fga_server* S, const fga_pair* req, int64_t* ti
   }
   Request r;
   r.q = *req;
-  const int method = resolve_method(&S->p, req->N);
-  r.charge = pair_bytes_bound(req->N, req->M, method, &S->p);
+  r.prm = req->params ? *req->params : S->p;
+  r.prm.profile = 0;
+  r.q.params = nullptr;
+  if (req->params) {
+    int rc = check_register_params(&r.prm);
+    if (rc) return rc;
+    if (r.prm.max_iter < 1) {
+      set_error("fga_server_submit: max_iter must be >= 1");
+      return FGA_EINVAL;
+    }
+  }
+  const int method = resolve_method(&r.prm, req->N);
+  r.charge = pair_bytes_bound(req->N, req->M, method, &r.prm);
   r.work = method == FGA_BH ? 64.0 * (double)req->M * std::log2((double)req->N + 1.0)
                             : (double)req->N * (double)req->M;
   std::lock_guard<std::mutex> lk(S->mu);

@@ -156,7 +156,6 @@ extern "C" int fga_autotune(const fga_params* p_in, int flags, void* stream, fga
   if (rc) return rc;
   std::memset(out, 0, sizeof(*out));
   cudaStream_t s = (cudaStream_t)stream;
-  const float eps2 = p.eps * p.eps, theta2 = p.theta * p.theta;
   const int reps = 3;
 
   // ---------------------------------------------------------------- direct tiles
@@ -262,7 +261,7 @@ extern "C" int fga_autotune(const fga_params* p_in, int flags, void* stream, fga
         const int fgrid = batch_force_grid(ts[1]);
         double ms = 0;
         rc = time_min(s, reps, [&] {
-          return launch_batch_iteration(d_pairs, 1, d_ts, ts[1], d_bs, 0, d_ctr, eps2, theta2, fgrid, s);
+          return launch_batch_iteration(d_pairs, 1, d_ts, ts[1], d_bs, 0, d_ctr, fgrid, s);
         }, &ms);
         if (rc) return rc;
         count_launch(reps + 1);
