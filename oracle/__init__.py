@@ -99,6 +99,7 @@ def lib():
         _lib.orc_denormalize.argtypes = [D, D, D, ctypes.c_double, D]
         _lib.orc_masses_niv.argtypes = [D, L, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, D]
+        _lib.orc_masses_rbf.argtypes = [D, L, LP, ctypes.c_int, ctypes.c_double, ctypes.c_double, D]
         _lib.orc_direct_acc.argtypes = [D, D, L, D, L, ctypes.c_double, ctypes.c_double, D, D]
         _lib.orc_tree_build.argtypes = [D, D, L, ctypes.c_int]
         _lib.orc_tree_build.restype = ctypes.c_void_p
@@ -173,6 +174,29 @@ def masses_niv(P, lattice: int = 16, a: float = -5.0, b: float = 5.0, total: flo
     if rc != 0:
         raise ValueError("bad NIV arguments")
     return out
+
+
+def masses_rbf(P, landmarks, sigma: float = 10.0 / 16.0, floor: float = 1e-3):
+    """Eq. 17: the RBF interpolant B over the landmark indices (readings in the
+    C source); B = 1 everywhere without landmarks."""
+    P = _d(P)
+    idx = np.ascontiguousarray(np.asarray(landmarks, dtype=np.int64))
+    out = np.empty(len(P))
+    rc = lib().orc_masses_rbf(_p(P), len(P), idx.ctypes.data_as(ctypes.POINTER(ctypes.c_long)), len(idx),
+                              sigma, floor, _p(out))
+    if rc != 0:
+        raise ValueError("bad RBF arguments (%d)" % rc)
+    return out
+
+
+def masses_spm(P, landmarks, sigma: float = 10.0 / 16.0, floor: float = 1e-3, lattice: int = 16,
+               a: float = -5.0, b: float = 5.0, total: float = 1.0, niv: bool = True):
+    """Eq. 19: smooth-particle masses S = N o B (NIV weights times the RBF
+    interpolant; B alone with niv=False), scaled to sum to `total`."""
+    B = masses_rbf(P, landmarks, sigma, floor)
+    N = masses_niv(P, lattice, a, b, 1.0) if niv else np.ones(len(B))
+    S = N * B
+    return total * S / S.sum()
 
 
 def masses_uniform(n: int, total: float = 1.0) -> np.ndarray:

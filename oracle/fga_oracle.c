@@ -13,6 +13,9 @@
  *   orc_normalize / orc_denormalize  Appendix, Eqs. A.1-A.3 (and the derivation
  *                                    of dnorm(t) that follows them)
  *   orc_masses_niv                   Sec. IV-F.2, Eq. 18 (NIV measure)
+ *   orc_masses_rbf                   Sec. IV-F.1, Eq. 17 (RBF mass interpolant);
+ *                                    with the NIV weights, Eq. 19 (SPM) is
+ *                                    their point-wise product
  *   orc_direct_acc                   Sec. IV-C, Eq. 6 (all-pairs force)
  *   orc_tree_build                   Sec. IV-E, Algorithm 1 (BH tree)
  *   orc_bh_acc                       Sec. IV-E, Eq. 15 and BHForce in Algorithm 2
@@ -161,6 +164,85 @@ int orc_masses_niv(const double* P, long n, int lattice, double a, double b, dou
     for (long i = 0; i < n; ++i) m_out[i] = total * m_out[i] / wsum;
     free(count);
     free(cell);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. IV-F.1, Eq. 17: RBF mass interpolant from landmarks                  */
+/* ------------------------------------------------------------------------ */
+
+/* B(P_i) = sum_c lambda_c Phi(|P_i - P_c|), Phi(s) = exp(-s^2 / sigma^2), over
+ * the m landmarks c = idx[0..m-1] (Eq. 17; B = 1 everywhere when m = 0).
+ * Reading: Eq. 17 writes the coefficients lambda_{i c}; they are those of the
+ * standard RBF interpolant, one per landmark, fixed by collocation at the
+ * landmarks: sum_c' Phi(|P_c - P_c'|) lambda_c' = w_c with w_c = 1, the
+ * "strong weight" the paper gives landmarks. sigma is the kernel width (the
+ * paper gives none). B is then clamped below at `floor` (> 0) so that every
+ * mass stays positive far from the landmarks.
+ * The m x m system (symmetric positive definite for distinct landmarks) is
+ * solved by Cholesky factorisation in index order. Returns 0, -1 for bad
+ * arguments, -2 when the collocation matrix is not positive definite
+ * (repeated landmarks). */
+int orc_masses_rbf(const double* P, long n, const long* idx, int m, double sigma, double floor_v,
+                   double* B_out) {
+    if (n <= 0 || m < 0 || !(sigma > 0) || !(floor_v > 0)) return -1;
+    for (int c = 0; c < m; ++c)
+        if (idx[c] < 0 || idx[c] >= n) return -1;
+    if (m == 0) {
+        for (long i = 0; i < n; ++i) B_out[i] = 1.0;
+        return 0;
+    }
+    double* A = (double*)malloc((size_t)m * m * sizeof(double));
+    double* lam = (double*)malloc((size_t)m * sizeof(double));
+    if (!A || !lam) { free(A); free(lam); return -2; }
+    const double is2 = 1.0 / (sigma * sigma);
+    for (int r = 0; r < m; ++r)
+        for (int c = 0; c < m; ++c) {
+            double d2 = 0;
+            for (int k = 0; k < 3; ++k) {
+                double d = P[3 * idx[r] + k] - P[3 * idx[c] + k];
+                d2 += d * d;
+            }
+            A[r * m + c] = exp(-d2 * is2);
+        }
+    /* Cholesky A = L L^T (L overwrites the lower triangle) */
+    for (int j = 0; j < m; ++j) {
+        double s = A[j * m + j];
+        for (int k = 0; k < j; ++k) s -= A[j * m + k] * A[j * m + k];
+        if (!(s > 0)) { free(A); free(lam); return -2; }
+        const double ljj = sqrt(s);
+        A[j * m + j] = ljj;
+        for (int i = j + 1; i < m; ++i) {
+            double t = A[i * m + j];
+            for (int k = 0; k < j; ++k) t -= A[i * m + k] * A[j * m + k];
+            A[i * m + j] = t / ljj;
+        }
+    }
+    /* L z = w (w = 1), then L^T lambda = z */
+    for (int i = 0; i < m; ++i) {
+        double t = 1.0;
+        for (int k = 0; k < i; ++k) t -= A[i * m + k] * lam[k];
+        lam[i] = t / A[i * m + i];
+    }
+    for (int i = m - 1; i >= 0; --i) {
+        double t = lam[i];
+        for (int k = i + 1; k < m; ++k) t -= A[k * m + i] * lam[k];
+        lam[i] = t / A[i * m + i];
+    }
+    for (long i = 0; i < n; ++i) {
+        double b = 0;
+        for (int c = 0; c < m; ++c) {
+            double d2 = 0;
+            for (int k = 0; k < 3; ++k) {
+                double d = P[3 * i + k] - P[3 * idx[c] + k];
+                d2 += d * d;
+            }
+            b += lam[c] * exp(-d2 * is2);
+        }
+        B_out[i] = b > floor_v ? b : floor_v;
+    }
+    free(A);
+    free(lam);
     return 0;
 }
 
