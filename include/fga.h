@@ -49,6 +49,8 @@ extern "C" {
 
 #define FGA_MASS_UNIFORM 0 /* equal masses                              */
 #define FGA_MASS_NIV 1     /* normalised intrinsic volume, Eq. 18       */
+#define FGA_MASS_RBF 2     /* landmark RBF interpolant, Eq. 17 (fga_masses_landmarks only) */
+#define FGA_MASS_SPM 3     /* smooth-particle masses, Eq. 19 (fga_masses_landmarks only)   */
 
 typedef struct fga_params {
   float G;           /* gravitational constant (paper default 66.7)             */
@@ -136,6 +138,27 @@ void fga_denormalize(const double R[9], const double t_norm[3], const double inf
  * Errors: FGA_EINVAL for n <= 0, bad mode/lattice, b <= a, total <= 0. */
 int fga_masses(const float* pts, int64_t n, int mode, int lattice, float a, float b,
                double total, float* masses_out, void* stream);
+
+/* Landmark-driven masses, Sec. IV-F.1 and IV-F.3.
+ * mode = FGA_MASS_RBF: the RBF interpolant of Eq. 17,
+ *   B(p) = sum_c lambda_c exp(-|p - p_c|^2 / sigma^2),
+ * over the m landmarks p_c = pts[landmarks[c]], with lambda fixed by
+ * collocation so that B = 1 at every landmark (the landmarks' strong weight;
+ * an m x m FP64 Cholesky solve on the device), clamped below at `floor`
+ * (> 0) so that every mass stays positive; B = 1 everywhere when m = 0.
+ * mode = FGA_MASS_SPM: the smooth-particle masses of Eq. 19, S = N o B, the
+ * point-wise product with the NIV weights of fga_masses (lattice, a, b).
+ * The result is scaled to sum to `total`.
+ * pts: device (n x 3), in the frame the masses are meant for (the
+ * normalised frame for sigma in its units); landmarks: HOST array of m point
+ * indices, m <= FGA_MAX_LANDMARKS; masses_out: device (n). Synchronises
+ * `stream` once when m > 0.
+ * Errors: FGA_EINVAL (bad sizes, modes, indices, sigma or floor <= 0,
+ * repeated or coincident landmarks), FGA_ENOMEM, FGA_ECUDA. */
+#define FGA_MAX_LANDMARKS 512
+int fga_masses_landmarks(const float* pts, int64_t n, const int64_t* landmarks, int m, float sigma,
+                         float floor, int mode, int lattice, float a, float b, double total,
+                         float* masses_out, void* stream);
 
 /* ----------------------------------------------------------------- Sec. IV-E */
 typedef struct fga_tree fga_tree;

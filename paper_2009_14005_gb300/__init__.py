@@ -43,6 +43,9 @@ FGA_VEL_UNCONSTRAINED = 0
 FGA_VEL_RIGID = 1
 FGA_MASS_UNIFORM = 0
 FGA_MASS_NIV = 1
+FGA_MASS_RBF = 2
+FGA_MASS_SPM = 3
+FGA_MAX_LANDMARKS = 512
 
 SYMBOLS = [
     "fga_params_default", "fga_last_error", "fga_launch_count", "fga_normalize",
@@ -52,6 +55,7 @@ SYMBOLS = [
     "fga_forces_direct_static", "fga_register_batch", "fga_direct_max_n",
     "fga_server_create", "fga_server_submit", "fga_server_poll", "fga_server_stats_get",
     "fga_server_destroy", "fga_autotune", "fga_set_direct_tile", "fga_get_direct_tile",
+    "fga_masses_landmarks",
 ]
 FGA_STATIC_SCRATCH_FLOAT4 = 524288
 
@@ -190,6 +194,8 @@ def _load():
         "fga_server_stats_get": (ctypes.c_int, [P, ctypes.POINTER(fga_server_stats)]),
         "fga_server_destroy": (ctypes.c_int, [P]),
         "fga_autotune": (ctypes.c_int, [PP, ctypes.c_int, VP, ctypes.POINTER(fga_tune_report)]),
+        "fga_masses_landmarks": (ctypes.c_int, [P, I64, P, ctypes.c_int, F, F, ctypes.c_int, ctypes.c_int,
+                                                F, F, D, P, VP]),
         "fga_set_direct_tile": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
         "fga_get_direct_tile": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                                ctypes.POINTER(ctypes.c_int)]),
@@ -296,6 +302,20 @@ def fga_masses(pts, mode: int = FGA_MASS_UNIFORM, lattice: int = 16, a: float = 
     out = torch.empty(pts.shape[0], dtype=torch.float32, device=pts.device)
     _err(lib.fga_masses(_ptr(pts), pts.shape[0], mode, lattice, a, b, total, _ptr(out),
                         _stream(stream)))
+    return out
+
+
+def fga_masses_landmarks(pts, landmarks, mode: int = FGA_MASS_SPM, sigma: float = 0.625,
+                         floor: float = 1e-3, lattice: int = 16, a: float = -5.0, b: float = 5.0,
+                         total: float = 1.0, stream=None):
+    """Eq. 17 (mode FGA_MASS_RBF) or Eq. 19 (FGA_MASS_SPM) masses from landmark
+    point indices; see fga_masses_landmarks in fga.h."""
+    torch = _torch()
+    pts = _dev(pts, 3, "pts")
+    idx = np.ascontiguousarray(np.asarray(landmarks, dtype=np.int64).reshape(-1))
+    out = torch.empty(pts.shape[0], dtype=torch.float32, device=pts.device)
+    _err(lib.fga_masses_landmarks(_ptr(pts), pts.shape[0], idx.ctypes.data if len(idx) else None, len(idx),
+                                  sigma, floor, mode, lattice, a, b, total, _ptr(out), _stream(stream)))
     return out
 
 
