@@ -59,7 +59,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("eps", ctypes.c_double), ("eta", ctypes.c_double),
                 ("dt", ctypes.c_double), ("theta", ctypes.c_double), ("max_iter", ctypes.c_int),
                 ("conv_tol", ctypes.c_double), ("method", ctypes.c_int),
-                ("velocity_mode", ctypes.c_int), ("max_depth", ctypes.c_int)]
+                ("velocity_mode", ctypes.c_int), ("max_depth", ctypes.c_int), ("dim", ctypes.c_int)]
 
 
 @dataclass
@@ -79,10 +79,11 @@ class Params:
     b: float = 5.0
     lattice: int = 16
     niv_masses: bool = False
+    dim: int = 3  # 2: clouds given as (n, 2), registered in the plane
 
     def _c(self) -> _Params:
         return _Params(self.G, self.eps, self.eta, self.dt, self.theta, self.max_iter,
-                       self.conv_tol, self.method, self.velocity_mode, self.max_depth)
+                       self.conv_tol, self.method, self.velocity_mode, self.max_depth, self.dim)
 
 
 _lib = None
@@ -99,6 +100,9 @@ def lib():
         _lib.orc_denormalize.argtypes = [D, D, D, ctypes.c_double, D]
         _lib.orc_masses_niv.argtypes = [D, L, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, D]
+        _lib.orc_masses_niv_d.argtypes = [D, L, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                          ctypes.c_double, ctypes.c_double, D]
+        _lib.orc_kabsch_d.argtypes = [D, D, L, ctypes.c_int, D, D]
         _lib.orc_masses_rbf.argtypes = [D, L, LP, ctypes.c_int, ctypes.c_double, ctypes.c_double, D]
         _lib.orc_direct_acc.argtypes = [D, D, L, D, L, ctypes.c_double, ctypes.c_double, D, D]
         _lib.orc_tree_build.argtypes = [D, D, L, ctypes.c_int]
@@ -166,11 +170,12 @@ def denormalize(R, t, info, a: float = -5.0) -> np.ndarray:
 
 # --------------------------------------------------------------------------- masses
 
-def masses_niv(P, lattice: int = 16, a: float = -5.0, b: float = 5.0, total: float = 1.0):
-    """Eq. 18 with the readings documented in the C source."""
+def masses_niv(P, lattice: int = 16, a: float = -5.0, b: float = 5.0, total: float = 1.0, dim: int = 3):
+    """Eq. 18 with the readings documented in the C source (dim 2: the x, y
+    lattice with discs)."""
     P = _d(P)
     out = np.empty(len(P))
-    rc = lib().orc_masses_niv(_p(P), len(P), lattice, a, b, total, _p(out))
+    rc = lib().orc_masses_niv_d(_p(P), len(P), dim, lattice, a, b, total, _p(out))
     if rc != 0:
         raise ValueError("bad NIV arguments")
     return out
@@ -270,12 +275,13 @@ def ode_step(v, acc, mY, dt: float, eta: float):
     return vo, do
 
 
-def kabsch(Y, D):
-    """Eqs. 14 and 16: returns (R, t, status) with status 1 for a degenerate fit."""
+def kabsch(Y, D, dim: int = 3):
+    """Eqs. 14 and 16: returns (R, t, status) with status 1 for a degenerate fit
+    (dim 2: the 2 x 2 fit of the x, y components, embedded as diag(R', 1))."""
     Y, D = _d(Y), _d(D)
     R = np.zeros(9)
     t = np.zeros(3)
-    st = lib().orc_kabsch(_p(Y), _p(D), len(Y), _p(R), _p(t))
+    st = lib().orc_kabsch_d(_p(Y), _p(D), len(Y), dim, _p(R), _p(t))
     return R.reshape(3, 3), t, int(st)
 
 
@@ -311,7 +317,7 @@ def register(Xn, mX, Yn, mY, params: Params, V0=None, want_traj: bool = False,
 def default_masses(Xn, Yn, params: Params):
     """Masses per the module docstring: X sums to 1 (uniform or NIV), Y mean dt."""
     if params.niv_masses:
-        mX = masses_niv(Xn, params.lattice, params.a, params.b, 1.0)
+        mX = masses_niv(Xn, params.lattice, params.a, params.b, 1.0, dim=params.dim)
     else:
         mX = masses_uniform(len(Xn), 1.0)
     mY = masses_uniform(len(Yn), params.dt * len(Yn))
@@ -326,6 +332,11 @@ def register_full(X, Y, params: Params, round_to_f32: bool = True, want_traj: bo
     stores them; the loop itself stays FP64.
     Returns dict(R, t (original frame), R_n, t_n (normalised frame), info, ...).
     """
+    if params.dim == 2:
+        # the plane z = 0 of the 3-D formulas: a zero coordinate never sets
+        # the normalisation's extremes, and the tree does not split z
+        X = embed2(X)
+        Y = embed2(Y)
     Xn, Yn, info = normalize(X, Y, params.a, params.b)
     if round_to_f32:
         Xn = Xn.astype(np.float32).astype(np.float64)
@@ -338,7 +349,15 @@ def register_full(X, Y, params: Params, round_to_f32: bool = True, want_traj: bo
     out["R_n"], out["t_n"] = out["R"], out["t"]
     out["t"] = denormalize(out["R_n"], out["t_n"], info, params.a)
     out["info"] = info
+    if params.dim == 2:
+        out["R2"], out["t2"] = out["R"][:2, :2], out["t"][:2]
     return out
+
+
+def embed2(P):
+    """(n, 2) -> (n, 3) with z = 0."""
+    P = _d(P)
+    return np.ascontiguousarray(np.column_stack([P[:, 0], P[:, 1], np.zeros(len(P))]))
 
 
 def rotation_error_deg(R1, R2) -> float:

@@ -43,6 +43,9 @@ typedef struct {
     int velocity_mode;   /* 0 = unconstrained velocities kept (Eq. 9),
                             1 = velocities replaced by the rigid motion   */
     int max_depth;       /* depth limit of the BH tree (paper: 20) */
+    int dim;             /* D = 3, or D = 2 for clouds in the plane z = 0:
+                            the tree is then the quadtree (no z split), and the
+                            rigid fit of Eq. 14 is the 2 x 2 one */
 } orc_params;
 
 void orc_set_threads(int n) {
@@ -134,17 +137,17 @@ void orc_denormalize(const double R[9], const double t[3], const double info[8],
  * f = 1 - (1 - V(ball) / V(cell))^n. A point's weight is 1 / f of its cell
  * (Eq. 18; the normalising integral is a common factor that cancels), and the
  * weights are scaled to sum to `total`. */
-int orc_masses_niv(const double* P, long n, int lattice, double a, double b, double total,
-                   double* m_out) {
-    if (n <= 0 || lattice <= 0 || !(b > a)) return -1;
-    long ncell = (long)lattice * lattice * lattice;
+int orc_masses_niv_d(const double* P, long n, int dim, int lattice, double a, double b, double total,
+                     double* m_out) {
+    if (n <= 0 || lattice <= 0 || !(b > a) || (dim != 2 && dim != 3)) return -1;
+    long ncell = dim == 3 ? (long)lattice * lattice * lattice : (long)lattice * lattice;
     long* count = (long*)calloc((size_t)ncell, sizeof(long));
     long* cell = (long*)malloc((size_t)n * sizeof(long));
     if (!count || !cell) { free(count); free(cell); return -2; }
     double h = (b - a) / (double)lattice;
     for (long i = 0; i < n; ++i) {
-        long c[3];
-        for (int k = 0; k < 3; ++k) {
+        long c[3] = {0, 0, 0};
+        for (int k = 0; k < dim; ++k) {
             double q = floor((P[3 * i + k] - a) / h);
             if (q > lattice - 1) q = lattice - 1;
             if (q < 0) q = 0;
@@ -153,8 +156,11 @@ int orc_masses_niv(const double* P, long n, int lattice, double a, double b, dou
         cell[i] = (c[2] * lattice + c[1]) * lattice + c[0];
         count[cell[i]] += 1;
     }
-    double rad = (b - a) / (2.0 * 3.0 * (double)lattice);
-    double ratio = (4.0 / 3.0 * M_PI * rad * rad * rad) / (h * h * h);
+    /* Eq. 18 with d = D: balls of radius (b-a)/(2 D rho); in 2D discs of area
+       pi r^2 in cells of area h^2 */
+    double rad = (b - a) / (2.0 * (double)dim * (double)lattice);
+    double ratio = dim == 3 ? (4.0 / 3.0 * M_PI * rad * rad * rad) / (h * h * h)
+                            : (M_PI * rad * rad) / (h * h);
     double wsum = 0;
     for (long i = 0; i < n; ++i) {
         double f = 1.0 - pow(1.0 - ratio, (double)count[cell[i]]);
@@ -165,6 +171,11 @@ int orc_masses_niv(const double* P, long n, int lattice, double a, double b, dou
     free(count);
     free(cell);
     return 0;
+}
+
+int orc_masses_niv(const double* P, long n, int lattice, double a, double b, double total,
+                   double* m_out) {
+    return orc_masses_niv_d(P, n, 3, lattice, a, b, total, m_out);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -647,7 +658,58 @@ static double det3(const double A[9]) {
  * (Eq. 16). Reading: if the second singular value is below 1e-12 of the first
  * (collinear template), no rotation is determined: R = I, t = mu_YD - mu_Y,
  * and the return value is 1 instead of 0. */
+/* Eq. 14 for D = 2 (clouds in the plane z = 0): the 2 x 2 cross-covariance
+ * C = sum (y + d - mu_YD)(y - mu_Y)^T of the x, y components, its SVD
+ * C = U S V^T by one Jacobi rotation (the textbook 2 x 2 case), and
+ * R' = U diag(1, sgn det(U V^T)) V^T, embedded as diag(R', 1). The fit is
+ * unique unless c11 + c22 and c21 - c12 both vanish (every rotation is then
+ * equally good): R' = I, status 1. */
+static int kabsch2(const double C3[9], double R[9]) {
+    const double c11 = C3[0], c12 = C3[1], c21 = C3[3], c22 = C3[4];
+    for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    const double fro = sqrt(c11 * c11 + c12 * c12 + c21 * c21 + c22 * c22);
+    if (!(hypot(c11 + c22, c21 - c12) > 1e-12 * fro)) return 1;
+    /* V: the rotation that diagonalises C^T C (columns a = C e1, b = C e2) */
+    const double aa = c11 * c11 + c21 * c21, bb = c12 * c12 + c22 * c22, ab = c11 * c12 + c21 * c22;
+    const double phi = 0.5 * atan2(2.0 * ab, aa - bb);
+    const double cv = cos(phi), sv = sin(phi);
+    double V[4] = {cv, -sv, sv, cv};
+    /* C V = U S: columns u_k s_k */
+    double W[4];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) W[2 * r + c] = C3[3 * r] * V[c] + C3[3 * r + 1] * V[2 + c];
+    double s1 = hypot(W[0], W[2]), s2 = hypot(W[1], W[3]);
+    double U[4];
+    if (s1 < s2) { /* order the singular values */
+        double t0 = W[0], t2 = W[2];
+        W[0] = W[1]; W[2] = W[3]; W[1] = t0; W[3] = t2;
+        double sw = s1; s1 = s2; s2 = sw;
+        double v0 = V[0], v2 = V[2];
+        V[0] = V[1]; V[2] = V[3]; V[1] = v0; V[3] = v2;
+    }
+    U[0] = W[0] / s1;
+    U[2] = W[2] / s1;
+    if (s2 > 0) {
+        U[1] = W[1] / s2;
+        U[3] = W[3] / s2;
+    } else { /* rank 1: complete U to an orthonormal basis */
+        U[1] = -U[2];
+        U[3] = U[0];
+    }
+    const double detU = U[0] * U[3] - U[1] * U[2], detV = V[0] * V[3] - V[1] * V[2];
+    const double sg = detU * detV < 0 ? -1.0 : 1.0;
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) R[3 * r + c] = U[2 * r] * V[2 * c] + sg * U[2 * r + 1] * V[2 * c + 1];
+    return 0;
+}
+
+int orc_kabsch_d(const double* Y, const double* D, long M, int dim, double R[9], double t[3]);
+
 int orc_kabsch(const double* Y, const double* D, long M, double R[9], double t[3]) {
+    return orc_kabsch_d(Y, D, M, 3, R, t);
+}
+
+int orc_kabsch_d(const double* Y, const double* D, long M, int dim, double R[9], double t[3]) {
     double my[3] = {0, 0, 0}, myd[3] = {0, 0, 0};
     for (long i = 0; i < M; ++i)
         for (int k = 0; k < 3; ++k) {
@@ -661,9 +723,15 @@ int orc_kabsch(const double* Y, const double* D, long M, double R[9], double t[3
             for (int c = 0; c < 3; ++c)
                 C[3 * r + c] += (Y[3 * i + r] + D[3 * i + r] - myd[r]) * (Y[3 * i + c] - my[c]);
     double U[9], s[3], V[9];
-    svd3(C, U, s, V);
     int status = 0;
-    if (!(s[1] > 1e-12 * s[0])) {
+    if (dim == 2) {
+        status = kabsch2(C, R);
+    } else {
+        svd3(C, U, s, V);
+    }
+    if (dim == 2) {
+        /* R set by kabsch2 */
+    } else if (!(s[1] > 1e-12 * s[0])) {
         for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
         status = 1;
     } else {
@@ -736,7 +804,7 @@ int orc_register(const double* Xn, const double* mX, long N, const double* Yn, c
         }
         orc_ode_step(V, A, mY, M, p->dt, p->eta, V, Dd);
         double Rp[9], tp[3];
-        degenerate += orc_kabsch(Y, Dd, M, Rp, tp);
+        degenerate += orc_kabsch_d(Y, Dd, M, p->dim == 2 ? 2 : 3, Rp, tp);
         double Rn[9], tn[3];
         for (int r = 0; r < 3; ++r) {
             for (int c = 0; c < 3; ++c)
