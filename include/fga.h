@@ -69,6 +69,12 @@ typedef struct fga_params {
   int lattice;       /* NIV lattice resolution varrho (16)                      */
   int profile;       /* 1: time every force-kernel launch with CUDA events on the
                         launch stream (reported in fga_stats.force_ms)           */
+  int dim;           /* D: 3 (default), or 2 for planar clouds. With 2, the
+                        clouds given to fga_register / fga_register_batch /
+                        fga_server_submit are N x 2 and M x 2 (row-major); they
+                        are registered in the plane (quadtree, 2-D NIV discs,
+                        the 2 x 2 rigid fit of Eq. 14), and R_out / t_out keep
+                        the 3-D layout: R = diag(R2, 1), t = (t2, ~0)         */
 } fga_params;
 
 /* Fills `p` with the paper's defaults (Sec. V, parameter settings):

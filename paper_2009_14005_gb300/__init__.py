@@ -67,7 +67,7 @@ class fga_params(ctypes.Structure):
                 ("normalize", ctypes.c_int), ("a", ctypes.c_float), ("b", ctypes.c_float),
                 ("velocity_mode", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("mass_mode", ctypes.c_int), ("lattice", ctypes.c_int),
-                ("profile", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("dim", ctypes.c_int)]
 
 
 class fga_stats(ctypes.Structure):
@@ -493,7 +493,8 @@ def fga_register(X, Y, p: fga_params | None = None, mX=None, mY=None, stream=Non
         t = torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.float32)))
         return t
 
-    Xa, Ya = host_or_dev(X, 3), host_or_dev(Y, 3)
+    cols = 2 if p.dim == 2 else 3
+    Xa, Ya = host_or_dev(X, cols), host_or_dev(Y, cols)
     mXa, mYa = host_or_dev(mX, None), host_or_dev(mY, None)
     R = np.zeros(9)
     t = np.zeros(3)
@@ -541,7 +542,8 @@ def fga_register_batch(pairs, p: fga_params | None = None, stream=None):
         mX = pr[2] if len(pr) > 2 else None
         mY = pr[3] if len(pr) > 3 else None
         pk = pr[4] if len(pr) > 4 else None
-        Xt, Yt, mXt, mYt = arr(X, 3), arr(Y, 3), arr(mX, None), arr(mY, None)
+        cols = 2 if (pk if pk is not None else p).dim == 2 else 3
+        Xt, Yt, mXt, mYt = arr(X, cols), arr(Y, cols), arr(mX, None), arr(mY, None)
         if pk is not None:
             keep.append(pk)
         cp[k] = fga_pair(Xt.data_ptr(), Xt.shape[0], Yt.data_ptr(), Yt.shape[0],
@@ -601,9 +603,10 @@ class Server:
     def __init__(self, p: fga_params | None = None, mem_budget: int = 0, max_pairs: int = 0,
                  iters_per_tick: int = 0, device: int = -1, max_work: float = 0.0):
         self._h = ctypes.c_void_p()
+        self._p = p or params()
         cfg = fga_server_config(int(mem_budget), int(max_pairs), int(iters_per_tick), int(device),
                                 float(max_work))
-        _err(lib.fga_server_create(ctypes.byref(p or params()), ctypes.byref(cfg), ctypes.byref(self._h)))
+        _err(lib.fga_server_create(ctypes.byref(self._p), ctypes.byref(cfg), ctypes.byref(self._h)))
         self._keep = {}
 
     def submit(self, X, Y, mX=None, mY=None, params: fga_params | None = None) -> int:
@@ -620,7 +623,8 @@ class Server:
             held.append(t)
             return t
 
-        Xt, Yt, mXt, mYt = arr(X, 3), arr(Y, 3), arr(mX, None), arr(mY, None)
+        cols = 2 if (params if params is not None else self._p).dim == 2 else 3
+        Xt, Yt, mXt, mYt = arr(X, cols), arr(Y, cols), arr(mX, None), arr(mY, None)
         if any(t.is_cuda for t in held):
             # the server reads device inputs on its own stream: they must be complete
             torch.cuda.current_stream(Xt.device if Xt.is_cuda else Yt.device).synchronize()

@@ -117,6 +117,10 @@ int check_params(const fga_params* p, bool need_tree) {
     set_error("max_depth must be in 1..20");
     return FGA_EINVAL;
   }
+  if (p->dim != 2 && p->dim != 3) {
+    set_error("dim must be 2 or 3");
+    return FGA_EINVAL;
+  }
   if (p->max_iter < 0) {
     set_error("max_iter must be >= 0");
     return FGA_EINVAL;
@@ -233,9 +237,18 @@ int prepare_inputs(Scratch& sc, const float* X, int64_t N, const float* Y, int64
     return FGA_OK;
   };
   const float *dX = nullptr, *dY = nullptr, *dmX = nullptr, *dmY = nullptr;
-  if ((rc = stage(X, 3 * N, &dX)) || (rc = stage(Y, 3 * M, &dY)) || (rc = stage(mX, N, &dmX)) ||
+  const int64_t cols = p->dim == 2 ? 2 : 3;
+  if ((rc = stage(X, cols * N, &dX)) || (rc = stage(Y, cols * M, &dY)) || (rc = stage(mX, N, &dmX)) ||
       (rc = stage(mY, M, &dmY)))
     return rc;
+  if (cols == 2) {
+    // planar clouds: the plane z = 0 of the 3-D path
+    float *eX = nullptr, *eY = nullptr;
+    if (sc.alloc(&eX, 3 * N) || sc.alloc(&eY, 3 * M)) return FGA_ENOMEM;
+    if ((rc = embed_planar(dX, N, eX, s)) || (rc = embed_planar(dY, M, eY, s))) return rc;
+    dX = eX;
+    dY = eY;
+  }
   if (sc.alloc(&out.Xn, 3 * N) || sc.alloc(&out.Yn, 3 * M) || sc.alloc(&out.mXn, N) ||
       sc.alloc(&out.mYn, M) || sc.alloc(&out.info, 8) || sc.alloc(&out.flags, 8))
     return FGA_ENOMEM;
@@ -258,7 +271,7 @@ int prepare_inputs(Scratch& sc, const float* X, int64_t N, const float* Y, int64
   if (dmX)
     rc = rescale_masses(dmX, N, 1.0, out.mXn, s);
   else
-    rc = masses_device(out.Xn, N, p->mass_mode, p->lattice, p->a, p->b, 1.0, out.mXn, s);
+    rc = masses_device(out.Xn, N, p->mass_mode, p->lattice, p->a, p->b, 1.0, out.mXn, s, p->dim == 2 ? 2 : 3);
   if (rc) return rc;
   if (dmY)
     rc = rescale_masses(dmY, M, (double)p->dt * (double)M, out.mYn, s);
@@ -320,6 +333,7 @@ void fga_params_default(fga_params* p) {
   p->mass_mode = FGA_MASS_UNIFORM;
   p->lattice = 16;
   p->profile = 0;
+  p->dim = 3;
 }
 
 const char* fga_last_error(void) { return g_err.c_str(); }
@@ -530,6 +544,7 @@ static int step_impl(fga_state* st, int n_iter, cudaStream_t s) {
   const fga_params& p = st->p;
   EpiParams ep{p.G, p.dt, p.eta, p.velocity_mode, (double)p.conv_tol, st->max_traj,
                1.0 / (double)st->M, 1.0 / (double)p.dt};
+  ep.dim = p.dim;
   const unsigned long long inter = p.method == FGA_BH ? 0ull : (unsigned long long)(st->N * st->M);
   if (p.profile) {
     const size_t need = 2 * (size_t)(st->timed + n_iter);

@@ -305,7 +305,7 @@ int build_state(const fga_params* p, const double* mu0, Scratch& sc, DevState* d
   // would mean "no limit")
   if (p->max_iter <= 0) FGA_CUDA_TRY(cudaMemsetAsync(&ds->done, 1, sizeof(int), s));
   P.ep = EpiParams{p->G, p->dt, p->eta, p->velocity_mode, (double)p->conv_tol, 0,
-                   1.0 / (double)M, 1.0 / (double)p->dt, p->max_iter};
+                   1.0 / (double)M, 1.0 / (double)p->dt, p->max_iter, p->dim};
   P.inter_add = P.method == FGA_BH ? 0ull : (unsigned long long)(P.N * M);
   P.eps2 = p->eps * p->eps;
   P.theta2 = p->theta * p->theta;
@@ -412,7 +412,7 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
           (uint64_t)(uintptr_t)q.mX, (uint64_t)(uintptr_t)q.mY, (uint64_t)pk->normalize,
           pk->normalize ? bits(pk->a) : 0, pk->normalize ? bits(pk->b) : 0, (uint64_t)pk->mass_mode,
           pk->mass_mode == FGA_MASS_NIV ? (uint64_t)pk->lattice : 0, bits(pk->dt), (uint64_t)method,
-          method == FGA_BH ? (uint64_t)pk->max_depth : 0};
+          method == FGA_BH ? (uint64_t)pk->max_depth : 0, (uint64_t)pk->dim};
       src[k] = first.emplace(key, k).first->second;
     }
   }

@@ -213,6 +213,29 @@ static __device__ bool polar_rotation(const double C[9], double R[9]) {
   return true;
 }
 
+// Eq. 14 for D = 2 (clouds in a plane z = const): the rotation R' of the
+// plane maximising tr(R'^T C2) over the x, y block C2 of C, i.e. the angle
+// atan2(c21 - c12, c11 + c22), embedded as diag(R', 1). False (no unique
+// optimum: every rotation fits equally) when both arguments vanish.
+__device__ __forceinline__ bool planar_rotation(const double C[9], double R[9]) {
+  const double c11 = C[0], c12 = C[1], c21 = C[3], c22 = C[4];
+  const double p = c11 + c22, q = c21 - c12;
+  const double r = sqrt(p * p + q * q);
+  const double fro = sqrt(c11 * c11 + c12 * c12 + c21 * c21 + c22 * c22);
+  if (!(r > 1e-12 * fro)) return false;
+  const double c = p / r, s = q / r;
+  R[0] = c;
+  R[1] = -s;
+  R[2] = 0.0;
+  R[3] = s;
+  R[4] = c;
+  R[5] = 0.0;
+  R[6] = 0.0;
+  R[7] = 0.0;
+  R[8] = 1.0;
+  return true;
+}
+
 // One thread: reductions -> C -> (R', t') -> compose, convergence, next-iteration constants.
 static __device__ void rigid_step(const double* red, int64_t M, DevState* ds, const EpiParams& ep,
                            double* traj, unsigned long long inter_add) {
@@ -229,7 +252,7 @@ static __device__ void rigid_step(const double* red, int64_t M, DevState* ds, co
     for (int c = 0; c < 3; ++c)
       C[3 * r + c] = S[3 * r + c] + red[12 + 3 * r + c] - Md * (ybar[r] + mud[r]) * ybar[c];
   double Rp[9];
-  const bool ok = polar_rotation(C, Rp) || rigid_rotation(C, Rp);
+  const bool ok = ep.dim == 2 ? planar_rotation(C, Rp) : (polar_rotation(C, Rp) || rigid_rotation(C, Rp));
   if (!ok) {
     for (int k = 0; k < 9; ++k) Rp[k] = (k % 4 == 0) ? 1.0 : 0.0;
     ds->degenerate += 1;

@@ -146,7 +146,9 @@ int check_masses(const float* m, int64_t n, int* d_flag, cudaStream_t s);
 int normalize_device(const float* X, int64_t N, const float* Y, int64_t M, float a, float b,
                      float* Xn, float* Yn, double* d_info, int* d_ok, cudaStream_t s);
 int masses_device(const float* pts, int64_t n, int mode, int lattice, float a, float b,
-                  double total, float* out, cudaStream_t s);
+                  double total, float* out, cudaStream_t s, int dim = 3);
+// (x, y) pairs -> (x, y, 0).
+int embed_planar(const float* in2, int64_t n, float* out3, cudaStream_t s);
 // Rescale masses (device) so they sum to `total`.
 int rescale_masses(const float* in, int64_t n, double total, float* out, cudaStream_t s);
 // Tight bounding box of float xyz triples or float4 bodies (device lo/hi, 3 floats each).
@@ -216,6 +218,7 @@ struct EpiParams {
   int max_traj;
   double inv_M, inv_dt;  // 1/M and 1/dt, FP64, computed on the host
   int max_iter;          // > 0: the pair stops by itself after this many iterations
+  int dim;               // 2: planar clouds, the 2 x 2 rigid fit; otherwise 3-D
 };
 int launch_epilogue(const float4* Y0, int64_t M, const ForceBuffers& fb, float4* V,
                     DevState* ds, double* d_partials, unsigned* d_counter, double* d_traj,

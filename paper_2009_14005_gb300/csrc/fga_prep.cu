@@ -205,10 +205,12 @@ int normalize_device(const float* X, int64_t N, const float* Y, int64_t M, float
 
 // ------------------------------------------------------------------ Sec. IV-F masses
 
-__device__ __forceinline__ int niv_cell(const float* p, int64_t i, double a, double h, int L) {
-  int c[3];
+// Lattice cell of point i; with dim = 2 only x and y are binned (z cell 0).
+__device__ __forceinline__ int niv_cell(const float* p, int64_t i, double a, double h, int L, int dim) {
+  int c[3] = {0, 0, 0};
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
+    if (k >= dim) break;
     double q = floor(((double)p[3 * i + k] - a) / h);
     q = q > (double)(L - 1) ? (double)(L - 1) : q;
     q = q < 0.0 ? 0.0 : q;
@@ -217,11 +219,11 @@ __device__ __forceinline__ int niv_cell(const float* p, int64_t i, double a, dou
   return (c[2] * L + c[1]) * L + c[0];
 }
 
-__global__ void k_niv_count(const float* __restrict__ p, int64_t n, double a, double h, int L,
+__global__ void k_niv_count(const float* __restrict__ p, int64_t n, double a, double h, int L, int dim,
                             unsigned* __restrict__ counts) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    atomicAdd(&counts[niv_cell(p, i, a, h, L)], 1u);
+    atomicAdd(&counts[niv_cell(p, i, a, h, L, dim)], 1u);
 }
 
 // Per cell: w = 1 / (1 - (1 - ratio)^count) (0 for empty cells); per-block sums of count * w.
@@ -248,13 +250,23 @@ __global__ void k_sum_parts(const double* __restrict__ part, int g, double* out)
   if (threadIdx.x == 0) *out = v[0];
 }
 
-__global__ void k_niv_assign(const float* __restrict__ p, int64_t n, double a, double h, int L,
+__global__ void k_niv_assign(const float* __restrict__ p, int64_t n, double a, double h, int L, int dim,
                              const double* __restrict__ w, const double* __restrict__ wsum,
                              double total, float* __restrict__ out) {
   const double inv = total / *wsum;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = (float)(w[niv_cell(p, i, a, h, L)] * inv);
+    out[i] = (float)(w[niv_cell(p, i, a, h, L, dim)] * inv);
+}
+
+// (x, y) pairs -> (x, y, 0): a planar cloud in the plane z = 0.
+__global__ void k_embed2(const float* __restrict__ in, int64_t n, float* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    out[3 * i] = in[2 * i];
+    out[3 * i + 1] = in[2 * i + 1];
+    out[3 * i + 2] = 0.f;
+  }
 }
 
 __global__ void k_fill(float* __restrict__ out, int64_t n, float v) {
@@ -263,18 +275,26 @@ __global__ void k_fill(float* __restrict__ out, int64_t n, float v) {
     out[i] = v;
 }
 
+int embed_planar(const float* in2, int64_t n, float* out3, cudaStream_t s) {
+  k_embed2<<<red_grid(n), RB, 0, s>>>(in2, n, out3);
+  FGA_LAUNCH_CHECK("embed2");
+  return FGA_OK;
+}
+
 int masses_device(const float* pts, int64_t n, int mode, int lattice, float a, float b,
-                  double total, float* out, cudaStream_t s) {
+                  double total, float* out, cudaStream_t s, int dim) {
   if (mode == FGA_MASS_UNIFORM) {
     k_fill<<<red_grid(n), RB, 0, s>>>(out, n, (float)(total / (double)n));
     FGA_LAUNCH_CHECK("fill");
     return FGA_OK;
   }
   const int L = lattice;
-  const int64_t ncell = (int64_t)L * L * L;
+  const int64_t ncell = dim == 2 ? (int64_t)L * L : (int64_t)L * L * L;
   const double h = ((double)b - (double)a) / (double)L;
-  const double rad = ((double)b - (double)a) / (2.0 * 3.0 * (double)L);
-  const double ratio = (4.0 / 3.0 * M_PI * rad * rad * rad) / (h * h * h);
+  // Eq. 18 with d = D: balls of radius (b-a)/(2 D rho); discs for D = 2
+  const double rad = ((double)b - (double)a) / (2.0 * (double)dim * (double)L);
+  const double ratio = dim == 2 ? (M_PI * rad * rad) / (h * h)
+                                : (4.0 / 3.0 * M_PI * rad * rad * rad) / (h * h * h);
   const int gc = red_grid(ncell);
   unsigned* counts = nullptr;
   double* w = nullptr;
@@ -285,13 +305,13 @@ int masses_device(const float* pts, int64_t n, int mode, int lattice, float a, f
   double* part = w + ncell;
   double* wsum = part + gc;
   FGA_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(unsigned) * ncell, s));
-  k_niv_count<<<red_grid(n), RB, 0, s>>>(pts, n, (double)a, h, L, counts);
+  k_niv_count<<<red_grid(n), RB, 0, s>>>(pts, n, (double)a, h, L, dim, counts);
   FGA_LAUNCH_CHECK("niv_count");
   k_niv_cellw<<<gc, RB, 0, s>>>(counts, ncell, ratio, w, part);
   FGA_LAUNCH_CHECK("niv_cellw");
   k_sum_parts<<<1, RB, 0, s>>>(part, gc, wsum);
   FGA_LAUNCH_CHECK("niv_wsum");
-  k_niv_assign<<<red_grid(n), RB, 0, s>>>(pts, n, (double)a, h, L, w, wsum, total, out);
+  k_niv_assign<<<red_grid(n), RB, 0, s>>>(pts, n, (double)a, h, L, dim, w, wsum, total, out);
   FGA_LAUNCH_CHECK("niv_assign");
   dev_free(counts, s);
   dev_free(w, s);

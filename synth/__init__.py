@@ -353,3 +353,32 @@ def serve_trace(seed: int, count: int, rate: float = 200.0, lo: int = 1000, hi: 
                                         float(overlaps[k]))
         out.append((float(times[k]), X, Y, R, t))
     return out
+
+
+def plane_pair(seed: int, n: int = 5000, m: int | None = None, max_deg: float = 30.0,
+               t_max: float = 0.2, sigma: float = 0.005):
+    """A planar (D = 2) pair: 6-12 random wall segments (a 2-D scan of a room),
+    per-segment density log-uniform over 10x, noise ``sigma``. X and Y are
+    sampled independently from the same segments; Y is moved by
+    ``(R_gt, t_gt)^-1`` with a rotation <= max_deg. Returns ``(X, Y, R_gt,
+    t_gt)`` with X, Y of shape (n, 2), (m, 2) and R_gt 2 x 2."""
+    m = n if m is None else m
+    rng = np.random.default_rng(seed)
+    k = int(rng.integers(6, 13))
+    a = rng.uniform(-1.5, 1.5, size=(k, 2))
+    b = a + rng.uniform(-1.2, 1.2, size=(k, 2))
+    dens = np.exp(rng.uniform(0.0, math.log(10.0), size=k)) * np.linalg.norm(b - a, axis=1)
+    ang = math.radians(rng.uniform(-max_deg, max_deg))
+    r_gt = np.array([[math.cos(ang), -math.sin(ang)], [math.sin(ang), math.cos(ang)]])
+    t_gt = rng.uniform(-1.0, 1.0, size=2)
+    t_gt *= rng.uniform(0.0, t_max) / max(np.linalg.norm(t_gt), 1e-12)
+
+    def sample(count):
+        seg = rng.choice(k, size=count, p=dens / dens.sum())
+        u = rng.uniform(0.0, 1.0, size=count)[:, None]
+        pts = a[seg] + u * (b[seg] - a[seg])
+        return pts + rng.normal(scale=sigma, size=pts.shape)
+
+    x = sample(n)
+    y = (sample(m) - t_gt) @ r_gt
+    return _f32(x), _f32(y), r_gt, t_gt
