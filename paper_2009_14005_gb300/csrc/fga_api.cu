@@ -520,8 +520,15 @@ static int state_create_checked(const float* Xn, const float* mX, int64_t N, con
   if (bh && dev_alloc_n(&st->perm, M, s)) return fail(FGA_ENOMEM);
   if (bh) {
     st->bh_ntasks = (unsigned)((M + 31) / 32) * (unsigned)st->tree->n_front;
-    if (dev_alloc_n(&st->bh_cost, st->bh_ntasks, s) || dev_alloc_n(&st->bh_order, st->bh_ntasks, s))
+    if (dev_alloc_n(&st->bh_cost, st->bh_ntasks, s) ||
+        dev_alloc_n(&st->bh_order, (size_t)st->bh_ntasks + TASK_ORDER_SCRATCH, s))
       return fail(FGA_ENOMEM);
+    if (st->tree->n_front <= 64) {
+      // which partial-sum slots each 32-point group wrote (cleared by the epilogue)
+      const int64_t groups = (M + 31) / 32;
+      if (dev_alloc_n(&st->fb.mask, groups, s)) return fail(FGA_ENOMEM);
+      FGA_CUDA_TRY(cudaMemsetAsync(st->fb.mask, 0, sizeof(unsigned long long) * groups, s));
+    }
   }
   if ((rc = pack_template(Yn, mY, p->dt, M, bh, st->Y0, st->perm, s))) return fail(rc);
   if (dev_alloc_n(&st->fb.hi, (size_t)st->fb.S * M, s) || dev_alloc_n(&st->fb.lo, (size_t)st->fb.S * M, s))
@@ -564,7 +571,7 @@ static int step_impl(fga_state* st, int n_iter, cudaStream_t s) {
       // (the task costs drift slowly as the template moves)
       ++st->bh_launches;
       if (rc == FGA_OK && bh_reorder_due(st->bh_launches)) {
-        rc = launch_bh_order(st->bh_cost, st->bh_ntasks, st->bh_order, s);
+        rc = launch_task_order(st->bh_cost, st->bh_ntasks, st->bh_order, s);
         st->bh_have_order = true;
       }
     } else {
@@ -710,6 +717,7 @@ void fga_state_destroy(fga_state* st) {
   dev_free(st->traj, s);
   dev_free(st->bh_cost, s);
   dev_free(st->bh_order, s);
+  dev_free(st->fb.mask, s);
   if (st->own_tree) fga_tree_destroy(st->own_tree);
   for (cudaEvent_t e : st->events) cudaEventDestroy(e);
   if (prev != st->device) cudaSetDevice(prev);

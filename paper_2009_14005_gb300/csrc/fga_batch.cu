@@ -191,17 +191,6 @@ int batch_force_grid(unsigned ntasks) {
                         ((int64_t)ntasks + BATCH_WARPS - 1) / BATCH_WARPS);
 }
 
-__global__ void __launch_bounds__(1024) k_batch_order(const unsigned* __restrict__ cost, unsigned n,
-                                                      unsigned* __restrict__ order) {
-  order_by_cost(cost, n, order);
-}
-
-int launch_batch_order(const unsigned* cost, unsigned ntasks, unsigned* order, cudaStream_t s) {
-  if (ntasks == 0) return FGA_OK;
-  k_batch_order<<<1, 1024, 0, s>>>(cost, ntasks, order);
-  FGA_LAUNCH_CHECK("batch order");
-  return FGA_OK;
-}
 
 int launch_batch_iteration(const PairDev* d_pairs, int npairs, const unsigned* d_task_start,
                            unsigned ntasks, const unsigned* d_block_start, unsigned nblocks,
@@ -460,7 +449,8 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
   unsigned *d_tstart = nullptr, *d_bstart = nullptr, *d_ctr = nullptr, *d_cost = nullptr, *d_order = nullptr;
   if (sc.alloc(&d_pairs, (size_t)count) || sc.alloc(&d_tstart, (size_t)count + 1) ||
       sc.alloc(&d_bstart, (size_t)count + 1) || sc.alloc(&d_ctr, 2) ||
-      sc.alloc(&d_cost, (size_t)task_start[count] + 1) || sc.alloc(&d_order, (size_t)task_start[count] + 1))
+      sc.alloc(&d_cost, (size_t)task_start[count] + 1) ||
+      sc.alloc(&d_order, (size_t)task_start[count] + 1 + TASK_ORDER_SCRATCH))
     return FGA_ENOMEM;
   FGA_CUDA_TRY(cudaMemcpyAsync(d_pairs, order.data(), sizeof(PairDev) * count, cudaMemcpyHostToDevice, s));
   FGA_CUDA_TRY(cudaMemcpyAsync(d_tstart, task_start.data(), sizeof(unsigned) * (count + 1),
@@ -478,7 +468,7 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
   auto force = [&](int it, cudaStream_t st) -> int {
     int r = launch_batch_iteration(d_pairs, count, d_tstart, ntasks, d_bstart, 0, d_ctr, fgrid, st, have_order ? d_order : nullptr, d_cost);
     if (r == FGA_OK && bh_reorder_due(it + 1, FGA_BATCH_REORDER_EVERY)) {
-      r = launch_batch_order(d_cost, ntasks, d_order, st);
+      r = launch_task_order(d_cost, ntasks, d_order, st);
       have_order = true;
       count_launch(1);
     }

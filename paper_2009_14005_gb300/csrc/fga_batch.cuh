@@ -79,14 +79,12 @@ int batch_force_grid(unsigned ntasks);
 // unsigned counters, zero before the first launch (the force kernel leaves
 // them zero). Pairs whose state is `done` skip their work.
 // order/cost: the heavy-first task order (slot -> task) or null, and where
-// each task's cost is recorded, or null (see order_by_cost).
+// each task's cost is recorded, or null (see launch_task_order).
 int launch_batch_iteration(const PairDev* d_pairs, int npairs, const unsigned* d_task_start,
                            unsigned ntasks, const unsigned* d_block_start, unsigned nblocks,
                            unsigned* d_ctr, int fgrid, cudaStream_t s,
                            const unsigned* order = nullptr, unsigned* cost = nullptr);
 
-// Heavy-first order of ntasks batch tasks from their recorded costs.
-int launch_batch_order(const unsigned* cost, unsigned ntasks, unsigned* order, cudaStream_t s);
 
 // out[k] = pairs[k].ds->done for k < n.
 int launch_done_flags(const PairDev* d_pairs, int n, int* d_out, cudaStream_t s);

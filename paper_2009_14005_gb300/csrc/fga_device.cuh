@@ -334,51 +334,6 @@ static __device__ void rigid_step(const double* red, int64_t M, DevState* ds, co
 // Adds into the compensated accumulators (hx, lx), ... and the term count;
 // `steps` gains the number of warp-wide walk steps (the task's cost).
 // A lane with valid == false takes part in the warp-wide loop but adds nothing.
-// Heavy-first order of warp tasks for the next force launch, from the step
-// counts `cost` the previous launch recorded: tasks sorted by descending
-// floor(log2(cost)) (a counting sort over 32 buckets; order within a bucket
-// is arbitrary). The walk's cost of a (group, frontier cell) task hardly
-// changes between iterations, and the few tasks that hold a group's near
-// field take far longer than the rest; started first, they no longer decide
-// when the launch ends. Each task writes only its own partial-sum slot, so
-// the order never changes a result. Run by one block (any size, multiple of
-// 32).
-__device__ __forceinline__ void order_by_cost(const unsigned* __restrict__ cost, unsigned n,
-                                              unsigned* __restrict__ order) {
-  __shared__ unsigned hist[32];
-  __shared__ unsigned base[32];
-  const unsigned lane = threadIdx.x & 31u;
-  if (threadIdx.x < 32) hist[threadIdx.x] = 0u;
-  __syncthreads();
-  for (unsigned t0 = 0; t0 < n; t0 += blockDim.x) {
-    const unsigned t = t0 + threadIdx.x;
-    const bool v = t < n;
-    const unsigned b = v ? (unsigned)__clz(cost[t] | 1u) : 32u;  // heavier: smaller bucket
-    const unsigned peers = __match_any_sync(FULL, b);
-    if (v && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&hist[b], (unsigned)__popc(peers));
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    unsigned acc = 0;
-    for (int b = 0; b < 32; ++b) {
-      base[b] = acc;
-      acc += hist[b];
-    }
-  }
-  __syncthreads();
-  for (unsigned t0 = 0; t0 < n; t0 += blockDim.x) {
-    const unsigned t = t0 + threadIdx.x;
-    const bool v = t < n;
-    const unsigned b = v ? (unsigned)__clz(cost[t] | 1u) : 32u;
-    const unsigned peers = __match_any_sync(FULL, b);
-    const int leader = __ffs(peers) - 1;
-    unsigned start = 0;
-    if (v && (int)lane == leader) start = atomicAdd(&base[b], (unsigned)__popc(peers));
-    start = __shfl_sync(FULL, start, leader);
-    if (v) order[start + (unsigned)__popc(peers & ((1u << lane) - 1u))] = t;
-  }
-}
-
 constexpr int BH_DEPTH = 24;  // > 21 tree levels: one pending range per level
 
 __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const float4* __restrict__ bodies,
@@ -500,31 +455,68 @@ __device__ __forceinline__ EpiCtx load_epi(const DevState* __restrict__ ds) {
 // Eq. 9 with the dissipative force of Eq. 7, v' = v + dt (a - eta v / m_Y);
 // Eq. 10, d = dt v'. Adds the point's 27 reduction terms to r: centred
 // position yc, d, yc yc^T (6), d yc^T (9), force m_Y a, torque yc x m_Y a.
+// `live`: bit s set for the slots to add (all S slots when no mask is kept);
+// the others are exact zeros, and adding a zero never changes a compensated
+// sum, so the result is the same as adding all S slots in order.
 __device__ __forceinline__ void epi_point(int64_t i, const float4* __restrict__ Y0,
                                           const float4* __restrict__ hi, const float4* __restrict__ lo,
                                           int S, int64_t M, float4* __restrict__ V,
-                                          const EpiParams& ep, const EpiCtx& c, float (&r)[NRED]) {
+                                          const EpiParams& ep, const EpiCtx& c, float (&r)[NRED],
+                                          unsigned long long live = ~0ull) {
   const float4 y0 = Y0[i];
   const float3 y = place(c.xf, y0);
   const float cx = y.x - c.mu[0], cy = y.y - c.mu[1], cz = y.z - c.mu[2];
   float ahx = 0.f, ahy = 0.f, ahz = 0.f, alx = 0.f, aly = 0.f, alz = 0.f;
-  for (int s = 0; s < S; s += 4) {
-    // four independent loads in flight, then the same in-order compensated sum
-    float4 h[4], l[4];
+  if (S <= 64 && live != ~0ull) {
+    unsigned long long rest = live & (S == 64 ? ~0ull : ((1ull << S) - 1ull));
+    while (rest) {
+      // up to four slots in flight, then the same in-order compensated sum
+      int sl[4];
+      int nk = 0;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const bool ok = s + k < S;
-      h[k] = ok ? hi[(int64_t)(s + k) * M + i] : make_float4(0.f, 0.f, 0.f, 0.f);
-      l[k] = ok ? lo[(int64_t)(s + k) * M + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = 0; k < 4; ++k) {
+        sl[k] = rest ? __ffsll((long long)rest) - 1 : -1;
+        if (rest) {
+          rest &= rest - 1ull;
+          ++nk;
+        }
+      }
+      float4 h[4], l[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        h[k] = sl[k] >= 0 ? hi[(int64_t)sl[k] * M + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        l[k] = sl[k] >= 0 ? lo[(int64_t)sl[k] * M + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        comp_add(ahx, alx, h[k].x);
+        comp_add(ahy, aly, h[k].y);
+        comp_add(ahz, alz, h[k].z);
+        alx += l[k].x;
+        aly += l[k].y;
+        alz += l[k].z;
+      }
+      (void)nk;
     }
+  } else {
+    for (int s = 0; s < S; s += 4) {
+      // four independent loads in flight, then the same in-order compensated sum
+      float4 h[4], l[4];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      comp_add(ahx, alx, h[k].x);
-      comp_add(ahy, aly, h[k].y);
-      comp_add(ahz, alz, h[k].z);
-      alx += l[k].x;
-      aly += l[k].y;
-      alz += l[k].z;
+      for (int k = 0; k < 4; ++k) {
+        const bool ok = s + k < S;
+        h[k] = ok ? hi[(int64_t)(s + k) * M + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        l[k] = ok ? lo[(int64_t)(s + k) * M + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        comp_add(ahx, alx, h[k].x);
+        comp_add(ahy, aly, h[k].y);
+        comp_add(ahz, alz, h[k].z);
+        alx += l[k].x;
+        aly += l[k].y;
+        alz += l[k].z;
+      }
     }
   }
   const float ax = ep.G * (ahx + alx), ay = ep.G * (ahy + aly), az = ep.G * (ahz + alz);

@@ -189,7 +189,8 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
                                                          float theta2, float4* __restrict__ hi_out,
                                                          float4* __restrict__ lo_out,
                                                          const unsigned* __restrict__ order,
-                                                         unsigned* __restrict__ cost) {
+                                                         unsigned* __restrict__ cost,
+                                                         unsigned long long* __restrict__ mask) {
   if (ds->done) return;
   __shared__ unsigned s_stack[BH_WARPS][BH_DEPTH][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -215,10 +216,14 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
     bh_task(rec, bodies, front, f, y, valid, eps2, theta2, stk, overflow, hx, hy, hz, lx, ly, lz,
             count, steps);
     if (cost && lane == 0) cost[task] = steps + 1u;
-    if (valid) {
+    // a task that added no term anywhere in the warp leaves exact zeros: with a
+    // mask its slot is neither written here nor read by the epilogue
+    const bool any = !mask || __any_sync(FULL, valid && count > 0u);
+    if (any && valid) {
       hi_out[(int64_t)f * M + i] = make_float4(hx, hy, hz, 0.f);
       lo_out[(int64_t)f * M + i] = make_float4(lx, ly, lz, 0.f);
     }
+    if (mask && any && lane == 0) atomicOr(&mask[g], 1ull << f);
     total += valid ? count : 0u;
   }
   if (__any_sync(FULL, overflow) && lane == 0) atomicOr(&ds->status, 1);
@@ -257,20 +262,98 @@ int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, floa
               float theta, ForceBuffers& fb, cudaStream_t s, const unsigned* order, unsigned* cost) {
   k_bh<<<bh_grid(M, t->n_front), BH_WARPS * 32, 0, s>>>(t->node_rec, t->bodies, Y0, M, t->front,
                                                         t->n_front, ds, eps * eps, theta * theta,
-                                                        fb.hi, fb.lo, order, cost);
+                                                        fb.hi, fb.lo, order, cost,
+                                                        t->n_front <= 64 ? fb.mask : nullptr);
   FGA_LAUNCH_CHECK("bh");
   fb.S = t->n_front;
   return FGA_OK;
 }
 
-__global__ void __launch_bounds__(1024) k_bh_order(const unsigned* __restrict__ cost, unsigned n,
-                                                   unsigned* __restrict__ order) {
-  order_by_cost(cost, n, order);
+// ------------------------------------------------------------------ heavy-first task order
+// Counting sort of task indices by descending floor(log2(cost)) over 32
+// buckets (bucket = clz(cost), heavier first), in three launches: per-block
+// bucket counts, their exclusive scan (bucket-major, so bucket 0 of every
+// block precedes bucket 1 of any block), and the scatter. The order within a
+// bucket is arbitrary; a task's result never depends on when it runs.
+constexpr int ORD_BS = 256;
+
+__device__ __forceinline__ unsigned cost_bucket(const unsigned* __restrict__ cost, unsigned t, unsigned n) {
+  return t < n ? (unsigned)__clz(cost[t] | 1u) : 32u;
 }
 
-int launch_bh_order(const unsigned* cost, unsigned ntasks, unsigned* order, cudaStream_t s) {
-  k_bh_order<<<1, 1024, 0, s>>>(cost, ntasks, order);
-  FGA_LAUNCH_CHECK("bh order");
+__global__ void __launch_bounds__(ORD_BS) k_ord_hist(const unsigned* __restrict__ cost, unsigned n, unsigned per,
+                                                     unsigned* __restrict__ hist) {
+  __shared__ unsigned h[32];
+  if (threadIdx.x < 32) h[threadIdx.x] = 0u;
+  __syncthreads();
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned t0 = blockIdx.x * per, t1 = min(n, t0 + per);
+  for (unsigned base = t0; base < t1; base += ORD_BS) {
+    const unsigned t = base + threadIdx.x;
+    const unsigned b = t < t1 ? cost_bucket(cost, t, n) : 32u;
+    const unsigned peers = __match_any_sync(FULL, b);
+    if (b < 32u && lane == (unsigned)(__ffs(peers) - 1)) atomicAdd(&h[b], (unsigned)__popc(peers));
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) hist[threadIdx.x * gridDim.x + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of `count` (<= TASK_ORDER_SCRATCH) values in place, one block.
+__global__ void __launch_bounds__(1024) k_ord_scan(unsigned* __restrict__ v, unsigned count) {
+  __shared__ unsigned part[1024];
+  const unsigned per = (count + 1023u) / 1024u;
+  const unsigned s0 = threadIdx.x * per, s1 = min(count, s0 + per);
+  unsigned sum = 0;
+  for (unsigned k = s0; k < s1; ++k) sum += v[k];
+  part[threadIdx.x] = sum;
+  __syncthreads();
+  for (unsigned off = 1; off < 1024; off <<= 1) {
+    const unsigned add = threadIdx.x >= off ? part[threadIdx.x - off] : 0u;
+    __syncthreads();
+    part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  unsigned run = part[threadIdx.x] - sum;  // exclusive prefix of this thread's slice
+  for (unsigned k = s0; k < s1; ++k) {
+    const unsigned x = v[k];
+    v[k] = run;
+    run += x;
+  }
+}
+
+__global__ void __launch_bounds__(ORD_BS) k_ord_scatter(const unsigned* __restrict__ cost, unsigned n, unsigned per,
+                                                        const unsigned* __restrict__ offs,
+                                                        unsigned* __restrict__ order) {
+  __shared__ unsigned base_b[32];
+  if (threadIdx.x < 32) base_b[threadIdx.x] = offs[threadIdx.x * gridDim.x + blockIdx.x];
+  __syncthreads();
+  const unsigned lane = threadIdx.x & 31u;
+  const unsigned t0 = blockIdx.x * per, t1 = min(n, t0 + per);
+  for (unsigned base = t0; base < t1; base += ORD_BS) {
+    const unsigned t = base + threadIdx.x;
+    const unsigned b = t < t1 ? cost_bucket(cost, t, n) : 32u;
+    const unsigned peers = __match_any_sync(FULL, b);
+    const int leader = __ffs(peers) - 1;
+    unsigned start = 0;
+    if (b < 32u && (int)lane == leader) start = atomicAdd(&base_b[b], (unsigned)__popc(peers));
+    start = __shfl_sync(FULL, start, leader);
+    if (b < 32u) order[start + (unsigned)__popc(peers & ((1u << lane) - 1u))] = t;
+  }
+}
+
+int launch_task_order(const unsigned* cost, unsigned ntasks, unsigned* order, cudaStream_t s) {
+  if (ntasks == 0) return FGA_OK;
+  const unsigned maxb = TASK_ORDER_SCRATCH / 32u;
+  unsigned nb = (ntasks + 4095u) / 4096u;
+  nb = nb < 1u ? 1u : (nb > maxb ? maxb : nb);
+  const unsigned per = (ntasks + nb - 1u) / nb;
+  unsigned* hist = order + ntasks;  // TASK_ORDER_SCRATCH entries after the order
+  k_ord_hist<<<nb, ORD_BS, 0, s>>>(cost, ntasks, per, hist);
+  FGA_LAUNCH_CHECK("order hist");
+  k_ord_scan<<<1, 1024, 0, s>>>(hist, 32u * nb);
+  FGA_LAUNCH_CHECK("order scan");
+  k_ord_scatter<<<nb, ORD_BS, 0, s>>>(cost, ntasks, per, hist, order);
+  FGA_LAUNCH_CHECK("order scatter");
   return FGA_OK;
 }
 
@@ -293,7 +376,8 @@ __global__ void __launch_bounds__(EPI_BS) k_epilogue(const float4* __restrict__ 
                                                      double* __restrict__ partials,
                                                      unsigned* __restrict__ counter,
                                                      double* __restrict__ traj, EpiParams ep,
-                                                     unsigned long long inter_add) {
+                                                     unsigned long long inter_add,
+                                                     unsigned long long* __restrict__ mask) {
   if (ds->done) return;
   __shared__ bool s_last;
   __shared__ double s_red[NRED];
@@ -301,8 +385,17 @@ __global__ void __launch_bounds__(EPI_BS) k_epilogue(const float4* __restrict__ 
   float r[NRED];
 #pragma unroll
   for (int k = 0; k < NRED; ++k) r[k] = 0.f;
-  for (int64_t i = blockIdx.x * (int64_t)EPI_BS + threadIdx.x; i < M; i += (int64_t)gridDim.x * EPI_BS)
-    epi_point(i, Y0, hi, lo, S, M, V, ep, c, r);
+  // one warp per 32-point group (so that it can clear the group's mask word
+  // once every lane has read it)
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = blockIdx.x * (int64_t)EPI_BS + (threadIdx.x & ~31); base < M;
+       base += (int64_t)gridDim.x * EPI_BS) {
+    const int64_t i = base + lane;
+    const unsigned long long live = mask ? mask[base >> 5] : ~0ull;
+    if (i < M) epi_point(i, Y0, hi, lo, S, M, V, ep, c, r, live);
+    __syncwarp();
+    if (mask && lane == 0) mask[base >> 5] = 0ull;
+  }
   epi_block_partial(r, partials + (int64_t)blockIdx.x * NRED);
   __threadfence();
   __syncthreads();
@@ -324,7 +417,8 @@ int launch_epilogue(const float4* Y0, int64_t M, const ForceBuffers& fb, float4*
                     double* d_partials, unsigned* d_counter, double* d_traj, const EpiParams& ep,
                     cudaStream_t s, unsigned long long inter_add) {
   k_epilogue<<<epilogue_blocks(M), EPI_BS, 0, s>>>(Y0, M, fb.hi, fb.lo, fb.S, V, ds, d_partials,
-                                                   d_counter, d_traj, ep, inter_add);
+                                                   d_counter, d_traj, ep, inter_add,
+                                                   fb.S <= 64 ? fb.mask : nullptr);
   FGA_LAUNCH_CHECK("epilogue");
   return FGA_OK;
 }

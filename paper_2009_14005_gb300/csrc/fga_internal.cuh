@@ -175,6 +175,10 @@ struct ForceBuffers {
   float4* hi = nullptr;   // S x M compensated partial sums (value)
   float4* lo = nullptr;   // S x M (compensation)
   int S = 1;              // number of source splits
+  // Optional (Barnes-Hut, S <= 64): bit s of mask[g] is set when slot s of
+  // the 32-point group g was written in this launch; unset slots are exact
+  // zeros, neither written nor read. The epilogue clears the mask.
+  unsigned long long* mask = nullptr;
 };
 
 // Plan for the all-pairs kernel: block size, queries per thread, source split.
@@ -191,12 +195,15 @@ void get_direct_tile(int size_class, int* bs, int* qpt);
 
 int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const DevState* ds,
                   float eps, const DirectPlan& plan, ForceBuffers& fb, cudaStream_t s);
-// order: heavy-first task order from launch_bh_order, or null (task index
+// order: heavy-first task order from launch_task_order, or null (task index
 // order); cost: where each task's step count is recorded, or null.
 int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, float eps,
               float theta, ForceBuffers& fb, cudaStream_t s, const unsigned* order = nullptr,
               unsigned* cost = nullptr);
-// Heavy-first order of ntasks tasks from their recorded costs (one block).
+// Heavy-first order of ntasks tasks from their recorded costs. `order` must
+// hold ntasks + TASK_ORDER_SCRATCH entries (the tail is the sort's scratch).
+constexpr unsigned TASK_ORDER_SCRATCH = 8192;
+int launch_task_order(const unsigned* cost, unsigned ntasks, unsigned* order, cudaStream_t s);
 // Refreshed after the first two force launches and then every
 // FGA_BH_REORDER_EVERY launches (0: never, tasks run in index order).
 #ifndef FGA_BH_REORDER_EVERY
@@ -209,7 +216,6 @@ inline bool bh_reorder_due(int launches_done, int every = FGA_BH_REORDER_EVERY) 
 #ifndef FGA_BATCH_REORDER_EVERY
 #define FGA_BATCH_REORDER_EVERY 8
 #endif
-int launch_bh_order(const unsigned* cost, unsigned ntasks, unsigned* order, cudaStream_t s);
 
 struct EpiParams {
   float G, dt, eta;

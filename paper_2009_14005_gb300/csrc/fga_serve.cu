@@ -421,7 +421,8 @@ class Runner {
         L_.cost = L_.order = nullptr;
         L_.task_cap = 0;
         const size_t cap = std::max<size_t>(4096, 2 * (size_t)L_.ntasks);
-        if (dev_alloc_n(&L_.cost, cap, s_) || dev_alloc_n(&L_.order, cap, s_)) return FGA_ENOMEM;
+        if (dev_alloc_n(&L_.cost, cap, s_) || dev_alloc_n(&L_.order, cap + TASK_ORDER_SCRATCH, s_))
+          return FGA_ENOMEM;
         L_.task_cap = cap;
       }
       // task indices changed: the next launch runs in index order and records costs
@@ -436,7 +437,7 @@ class Runner {
                                        s_, L_.have_order ? L_.order : nullptr, L_.cost)))
         return rc;
       if (bh_reorder_due(++L_.launches, FGA_BATCH_REORDER_EVERY)) {
-        if ((rc = launch_batch_order(L_.cost, L_.ntasks, L_.order, s_))) return rc;
+        if ((rc = launch_task_order(L_.cost, L_.ntasks, L_.order, s_))) return rc;
         L_.have_order = true;
         count_launch(1);
       }
