@@ -68,15 +68,15 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch
     const float eps2 = P.eps2, theta2 = P.theta2;
     const unsigned local = task - task_start[k];
     const unsigned grp = local / (unsigned)P.K;
-    const int64_t i = (int64_t)grp * 32 + lane;
-    const bool valid = i < M;
-    const Xf xf = load_xf(ds);
-    const float3 y = place(xf, P.Y0[valid ? i : 0]);
-    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-    unsigned count = 0;
     const unsigned f = local - grp * (unsigned)P.K;
+    const Xf xf = load_xf(ds);
     if (P.method == FGA_BH) {
-      unsigned steps = 0;
+      // 32 template points, one per lane, against frontier cell f
+      const int64_t i = (int64_t)grp * 32 + lane;
+      const bool valid = i < M;
+      const float3 y = place(xf, P.Y0[valid ? i : 0]);
+      float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+      unsigned count = 0, steps = 0;
       bh_task(P.rec, P.bodies, P.front, f, y, valid, eps2, theta2, stk, overflow, hx, hy, hz, lx, ly,
               lz, count, steps);
       if (cost && lane == 0) cost[task] = steps + 1u;
@@ -84,40 +84,62 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch
         if (lane == 0) atomicOr(&ds->status, 1);
         overflow = false;
       }
+      if (valid) {
+        P.hi[(int64_t)f * M + i] = make_float4(hx, hy, hz, 0.f);
+        P.lo[(int64_t)f * M + i] = make_float4(lx, ly, lz, 0.f);
+      }
+      unsigned long long c = valid ? count : 0u;
+      for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(FULL, c, off);
+      if (lane == 0 && c) atomicAdd(&ds->interactions, c);
     } else {
+      // 64 template points, two per lane (one shared-memory load serves two
+      // terms), against reference chunk f, staged 32 sources at a time
+      const int64_t i0 = (int64_t)grp * 64 + lane, i1 = i0 + 32;
+      const bool v0 = i0 < M, v1 = i1 < M;
+      const float3 y0 = place(xf, P.Y0[v0 ? i0 : 0]);
+      const float3 y1 = place(xf, P.Y0[v1 ? i1 : 0]);
+      float h0x = 0.f, h0y = 0.f, h0z = 0.f, l0x = 0.f, l0y = 0.f, l0z = 0.f;
+      float h1x = 0.f, h1y = 0.f, h1z = 0.f, l1x = 0.f, l1y = 0.f, l1z = 0.f;
       const int64_t j0 = (int64_t)f * BATCH_CHUNK;
       const int64_t j1 = min(P.N, j0 + BATCH_CHUNK);
-      // a 32-source tile costs about as much as 8 Barnes-Hut walk steps
-      if (cost && lane == 0) cost[task] = 8u * (unsigned)((j1 - j0 + 31) / 32) + 1u;
+      // a 32-source tile for 64 points costs about as much as 16 Barnes-Hut walk steps
+      if (cost && lane == 0) cost[task] = 16u * (unsigned)((j1 - j0 + 31) / 32) + 1u;
       for (int64_t b = j0; b < j1; b += 32) {
         const int64_t j = b + lane;
         s_tile[w][lane] = j < j1 ? P.X4[j] : make_float4(0.f, 0.f, 0.f, 0.f);  // m = 0 pads
         __syncwarp();
-        float px = 0.f, py = 0.f, pz = 0.f;
+        float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
 #pragma unroll 8
-        for (int k = 0; k < 32; ++k) {
-          const float4 q = s_tile[w][k];
-          const float dx = q.x - y.x, dy = q.y - y.y, dz = q.z - y.z;
-          const float inv = rsqrt_fast(fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2))));
-          const float wgt = q.w * (inv * inv * inv);
-          px = fmaf(wgt, dx, px);
-          py = fmaf(wgt, dy, py);
-          pz = fmaf(wgt, dz, pz);
+        for (int q = 0; q < 32; ++q) {
+          const float4 src = s_tile[w][q];
+          const float ax = src.x - y0.x, ay = src.y - y0.y, az = src.z - y0.z;
+          const float bx = src.x - y1.x, by = src.y - y1.y, bz = src.z - y1.z;
+          const float ia = rsqrt_fast(fmaf(ax, ax, fmaf(ay, ay, fmaf(az, az, eps2))));
+          const float ib = rsqrt_fast(fmaf(bx, bx, fmaf(by, by, fmaf(bz, bz, eps2))));
+          const float wa = src.w * (ia * ia * ia), wb = src.w * (ib * ib * ib);
+          p0x = fmaf(wa, ax, p0x);
+          p0y = fmaf(wa, ay, p0y);
+          p0z = fmaf(wa, az, p0z);
+          p1x = fmaf(wb, bx, p1x);
+          p1y = fmaf(wb, by, p1y);
+          p1z = fmaf(wb, bz, p1z);
         }
-        comp_add(hx, lx, px);
-        comp_add(hy, ly, py);
-        comp_add(hz, lz, pz);
+        comp_add(h0x, l0x, p0x);
+        comp_add(h0y, l0y, p0y);
+        comp_add(h0z, l0z, p0z);
+        comp_add(h1x, l1x, p1x);
+        comp_add(h1y, l1y, p1y);
+        comp_add(h1z, l1z, p1z);
         __syncwarp();
       }
-    }
-    if (valid) {
-      P.hi[(int64_t)f * M + i] = make_float4(hx, hy, hz, 0.f);
-      P.lo[(int64_t)f * M + i] = make_float4(lx, ly, lz, 0.f);
-    }
-    if (P.method == FGA_BH) {
-      unsigned long long c = valid ? count : 0u;
-      for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(FULL, c, off);
-      if (lane == 0 && c) atomicAdd(&ds->interactions, c);
+      if (v0) {
+        P.hi[(int64_t)f * M + i0] = make_float4(h0x, h0y, h0z, 0.f);
+        P.lo[(int64_t)f * M + i0] = make_float4(l0x, l0y, l0z, 0.f);
+      }
+      if (v1) {
+        P.hi[(int64_t)f * M + i1] = make_float4(h1x, h1y, h1z, 0.f);
+        P.lo[(int64_t)f * M + i1] = make_float4(l1x, l1y, l1z, 0.f);
+      }
     }
   }
   if (lane == 0) {
@@ -278,6 +300,15 @@ int build_inputs(const fga_pair& q, const Prepared& pr, const fga_params* p, Scr
   return centroid4(Y0, q.M, *mu0, s);
 }
 
+// The pair's own constants (its parameters) in its descriptor.
+static void fill_pair_params(const fga_params* p, PairDev& P) {
+  P.ep = EpiParams{p->G, p->dt, p->eta, p->velocity_mode, (double)p->conv_tol, 0,
+                   1.0 / (double)P.M, 1.0 / (double)p->dt, p->max_iter, p->dim};
+  P.inter_add = P.method == FGA_BH ? 0ull : (unsigned long long)(P.N * P.M);
+  P.eps2 = p->eps * p->eps;
+  P.theta2 = p->theta * p->theta;
+}
+
 int build_state(const fga_params* p, const double* mu0, Scratch& sc, DevState* ds, PairDev& P,
                 cudaStream_t s) {
   int rc = 0;
@@ -293,12 +324,14 @@ int build_state(const fga_params* p, const double* mu0, Scratch& sc, DevState* d
   // no iterations at all: the pair starts finished (max_iter = 0 in EpiParams
   // would mean "no limit")
   if (p->max_iter <= 0) FGA_CUDA_TRY(cudaMemsetAsync(&ds->done, 1, sizeof(int), s));
-  P.ep = EpiParams{p->G, p->dt, p->eta, p->velocity_mode, (double)p->conv_tol, 0,
-                   1.0 / (double)M, 1.0 / (double)p->dt, p->max_iter, p->dim};
-  P.inter_add = P.method == FGA_BH ? 0ull : (unsigned long long)(P.N * M);
-  P.eps2 = p->eps * p->eps;
-  P.theta2 = p->theta * p->theta;
+  fill_pair_params(p, P);
   return FGA_OK;
+}
+
+__global__ void k_states_init(DevState* __restrict__ ds, const double* const* __restrict__ mu0,
+                              const int* __restrict__ done, int n) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) state_init(ds + k, mu0[k], done[k]);
 }
 
 int build_pair(const fga_pair& q, const Prepared& pr, const fga_params* p, Scratch& sc,
@@ -329,7 +362,8 @@ bool batch_layout(const std::vector<PairDev>& pairs, std::vector<unsigned>& task
   block_start.assign(pairs.size() + 1, 0u);
   int64_t nt = 0, nb = 0;
   for (size_t k = 0; k < pairs.size(); ++k) {
-    nt += (pairs[k].M + 31) / 32 * (int64_t)pairs[k].K;
+    const int64_t gs = pairs[k].method == FGA_BH ? 32 : 64;  // template points per task
+    nt += (pairs[k].M + gs - 1) / gs * (int64_t)pairs[k].K;
     nb += pairs[k].nblk;
     if (nt >= ((int64_t)1 << 31) || nb >= ((int64_t)1 << 31)) return false;
     task_start[k + 1] = (unsigned)nt;
@@ -431,9 +465,53 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
     if (t) trees.push_back(t);
     if (rc) return rc;
   }
-  for (int k = 0; k < count; ++k) {
-    host[k] = host[src[k]];
-    if ((rc = build_state(pp[k], mu0[src[k]], sc, dsarr + k, host[k], s))) return rc;
+  // every pair's own state, velocities, partial sums and block counter in
+  // five allocations and one initialisation launch
+  {
+    size_t nhl = 0, nv = 0, npart = 0;
+    for (int k = 0; k < count; ++k) {
+      host[k] = host[src[k]];
+      host[k].nblk = epilogue_blocks(host[k].M);
+      nhl += (size_t)host[k].K * host[k].M;
+      nv += (size_t)host[k].M;
+      npart += (size_t)host[k].nblk * NRED;
+    }
+    float4 *hi = nullptr, *lo = nullptr, *V = nullptr;
+    double* part = nullptr;
+    unsigned* ctr = nullptr;
+    if (sc.alloc(&hi, nhl) || sc.alloc(&lo, nhl) || sc.alloc(&V, nv) || sc.alloc(&part, npart) ||
+        sc.alloc(&ctr, (size_t)count))
+      return FGA_ENOMEM;
+    FGA_CUDA_TRY(cudaMemsetAsync(V, 0, sizeof(float4) * nv, s));
+    FGA_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(unsigned) * count, s));
+    std::vector<const double*> mu0k(count);
+    std::vector<int> donek(count);
+    size_t ohl = 0, ov = 0, op = 0;
+    for (int k = 0; k < count; ++k) {
+      PairDev& P = host[k];
+      P.ds = dsarr + k;
+      P.hi = hi + ohl;
+      P.lo = lo + ohl;
+      P.V = V + ov;
+      P.partials = part + op;
+      P.counter = ctr + k;
+      ohl += (size_t)P.K * P.M;
+      ov += (size_t)P.M;
+      op += (size_t)P.nblk * NRED;
+      fill_pair_params(pp[k], P);
+      mu0k[k] = mu0[src[k]];
+      // no iterations at all: the pair starts finished (max_iter = 0 in
+      // EpiParams would mean "no limit")
+      donek[k] = pp[k]->max_iter <= 0 ? 1 : 0;
+    }
+    const double** d_mu0 = nullptr;
+    int* d_done = nullptr;
+    if (sc.alloc(&d_mu0, (size_t)count) || sc.alloc(&d_done, (size_t)count)) return FGA_ENOMEM;
+    FGA_CUDA_TRY(cudaMemcpyAsync(d_mu0, mu0k.data(), sizeof(double*) * count, cudaMemcpyHostToDevice, s));
+    FGA_CUDA_TRY(cudaMemcpyAsync(d_done, donek.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
+    k_states_init<<<(count + 127) / 128, 128, 0, s>>>(dsarr, d_mu0, d_done, count);
+    FGA_LAUNCH_CHECK("states_init");
+    count_launch(1);
   }
   // Barnes-Hut pairs (usually the heaviest tasks) are handed out first
   std::vector<PairDev> order;

@@ -50,8 +50,9 @@ int build_state(const fga_params* p, const double* mu0, Scratch& keep, DevState*
                 cudaStream_t s);
 
 // Work layout of a batch of pairs (in the order of `pairs`): pair k owns warp
-// tasks task_start[k] .. task_start[k+1]-1 (task = group * K + f: 32-point
-// group, frontier cell or reference chunk f) and epilogue blocks
+// tasks task_start[k] .. task_start[k+1]-1 (task = group * K + f: a group of
+// 32 template points and frontier cell f for Barnes-Hut, of 64 points and
+// reference chunk f for the all-pairs sum) and epilogue blocks
 // block_start[k] .. block_start[k+1]-1. Both arrays get pairs.size() + 1
 // entries. Returns false if a count exceeds 2^31.
 bool batch_layout(const std::vector<PairDev>& pairs, std::vector<unsigned>& task_start,

@@ -10,6 +10,36 @@ namespace fga {
 
 static constexpr unsigned FULL = 0xffffffffu;
 
+// The state before the first iteration: T = [I | 0], centroid mu0 of the
+// initial template (or 0), nothing counted; finished at once if `done`.
+__device__ __forceinline__ void state_init(DevState* ds, const double* __restrict__ mu0, int done) {
+  DevState z;
+  for (int k = 0; k < 9; ++k) {
+    z.R[k] = (k % 4 == 0) ? 1.0 : 0.0;
+    z.Rf[k] = (float)z.R[k];
+    z.A[k] = 0.f;
+  }
+  for (int k = 0; k < 12; ++k) z.Tm1[k] = z.Tm2[k] = (k < 9 && k % 4 == 0) ? 1.0 : 0.0;
+  for (int k = 0; k < 3; ++k) {
+    z.t[k] = 0.0;
+    z.tf[k] = 0.f;
+    z.b[k] = 0.f;
+    z.mu0[k] = mu0 ? mu0[k] : 0.0;
+    z.muf[k] = (float)z.mu0[k];
+    z.netF[k] = z.torque[k] = 0.0;
+  }
+  z.last_conv = -1.0;
+  z.interactions = 0ull;
+  z.iter = 0;
+  z.done = done;
+  z.converged = 0;
+  z.status = 0;
+  z.degenerate = 0;
+  z.bh_next = 0u;
+  z.bh_exited = 0u;
+  *ds = z;
+}
+
 // 1/sqrt(x) from the SFU (PTX rsqrt.approx.ftz.f32). Every argument on the
 // force path is r^2 + eps^2 >= eps^2 > 0, a normal number, where flushing
 // subnormals changes nothing; the non-flushing form costs extra instructions

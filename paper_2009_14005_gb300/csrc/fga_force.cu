@@ -457,33 +457,7 @@ int launch_forces_out(const ForceBuffers& fb, int64_t M, const float4* Y0, int u
   return FGA_OK;
 }
 
-__global__ void k_state_init(DevState* ds, const double* __restrict__ mu0) {
-  DevState z;
-  for (int k = 0; k < 9; ++k) {
-    z.R[k] = (k % 4 == 0) ? 1.0 : 0.0;
-    z.Rf[k] = (float)z.R[k];
-    z.A[k] = 0.f;
-  }
-  for (int k = 0; k < 12; ++k) z.Tm1[k] = z.Tm2[k] = (k < 9 && k % 4 == 0) ? 1.0 : 0.0;
-  for (int k = 0; k < 3; ++k) {
-    z.t[k] = 0.0;
-    z.tf[k] = 0.f;
-    z.b[k] = 0.f;
-    z.mu0[k] = mu0 ? mu0[k] : 0.0;
-    z.muf[k] = (float)z.mu0[k];
-    z.netF[k] = z.torque[k] = 0.0;
-  }
-  z.last_conv = -1.0;
-  z.interactions = 0ull;
-  z.iter = 0;
-  z.done = 0;
-  z.converged = 0;
-  z.status = 0;
-  z.degenerate = 0;
-  z.bh_next = 0u;
-  z.bh_exited = 0u;
-  *ds = z;
-}
+__global__ void k_state_init(DevState* ds, const double* __restrict__ mu0) { state_init(ds, mu0, 0); }
 
 int launch_state_init(DevState* ds, const double* d_mu0, cudaStream_t s) {
   k_state_init<<<1, 1, 0, s>>>(ds, d_mu0);
