@@ -473,10 +473,6 @@ int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N,
     FGA_CUDA_TRY(cudaMemcpyAsync(&h, ds, sizeof(h), cudaMemcpyDeviceToHost, s));
     FGA_CUDA_TRY(cudaStreamSynchronize(s));
     *interactions_out = tree ? (int64_t)h.interactions : N * M;
-    if (h.status & 1) {
-      set_error("fga_forces: traversal stack overflow");
-      return FGA_EINTERNAL;
-    }
   }
   return FGA_OK;
 }
@@ -670,8 +666,7 @@ int fga_state_get(fga_state* st, double R[9], double t[3], fga_stats* stats, voi
   }
   int code = FGA_OK;
   if (h.status) {
-    set_error(h.status & 1 ? "device check failed: traversal stack overflow"
-                           : "device check failed: non-finite transform");
+    set_error("device check failed: non-finite transform");
     code = FGA_EINTERNAL;
   } else if (h.degenerate) {
     set_error("rank-deficient rigid fit in at least one iteration");

@@ -52,7 +52,6 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch
   __shared__ float4 s_tile[BATCH_WARPS][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   unsigned* const stk = &s_stack[w][0][lane];
-  bool overflow = false;
   for (;;) {
     unsigned slot = 0;
     if (lane == 0) slot = atomicAdd(&ctr[0], 1u);
@@ -77,13 +76,9 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch
       const float3 y = place(xf, P.Y0[valid ? i : 0]);
       float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
       unsigned count = 0, steps = 0;
-      bh_task(P.rec, P.bodies, P.front, f, y, valid, eps2, theta2, stk, overflow, hx, hy, hz, lx, ly,
+      bh_task(P.rec, P.bodies, P.front, f, y, valid, eps2, theta2, stk, hx, hy, hz, lx, ly,
               lz, count, steps);
       if (cost && lane == 0) cost[task] = steps + 1u;
-      if (__any_sync(FULL, overflow)) {
-        if (lane == 0) atomicOr(&ds->status, 1);
-        overflow = false;
-      }
       if (valid) {
         P.hi[(int64_t)f * M + i] = make_float4(hx, hy, hz, 0.f);
         P.lo[(int64_t)f * M + i] = make_float4(lx, ly, lz, 0.f);

@@ -364,12 +364,17 @@ static __device__ void rigid_step(const double* red, int64_t M, DevState* ds, co
 // Adds into the compensated accumulators (hx, lx), ... and the term count;
 // `steps` gains the number of warp-wide walk steps (the task's cost).
 // A lane with valid == false takes part in the warp-wide loop but adds nothing.
-constexpr int BH_DEPTH = 24;  // > 21 tree levels: one pending range per level
+// Saved ranges per lane. A walk saves at most one range per tree level it
+// descends below the frontier cell, and the tree has at most 21 levels (depth
+// 0..20: 20-bit keys per axis, max_depth <= 20), so at most 20 ranges are ever
+// saved; the min() in the walk only keeps every index provably in bounds.
+constexpr int BH_DEPTH = 24;
+static_assert(BH_DEPTH > 20, "the BH walk stack must hold one range per tree level");
 
 __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const float4* __restrict__ bodies,
                                         const FrontCell* __restrict__ front, unsigned f, float3 y,
                                         bool valid, float eps2, float theta2, unsigned* stk,
-                                        bool& overflow, float& hx, float& hy, float& hz, float& lx,
+                                        float& hx, float& hy, float& hz, float& lx,
                                         float& ly, float& lz, unsigned& count, unsigned& steps) {
   float px = 0.f, py = 0.f, pz = 0.f;
   bool live = valid;
@@ -422,10 +427,7 @@ __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const fl
       // the current range, continue with the children (branch-free)
       const bool descend = !accept && nchild > 0;
       const bool save = descend && (e & 15u) != 0u;
-      if (save) {
-        if (sp < BH_DEPTH) stk[32 * sp] = e;
-        else overflow = true;
-      }
+      if (save) stk[32 * min(sp, BH_DEPTH - 1)] = e;
       sp += save;
       e = descend ? (((unsigned)__float_as_int(ri.y) << 4) | (unsigned)nchild) : e;
       if (!accept && nchild < -1) {
@@ -445,7 +447,7 @@ __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const fl
       // range exhausted: resume the innermost saved range
       const bool pop = (e & 15u) == 0u && sp > 0;
       sp -= pop;
-      e = (pop && sp < BH_DEPTH) ? stk[32 * sp] : e;
+      e = pop ? stk[32 * min(sp, BH_DEPTH - 1)] : e;
     }
     if ((steps & 31u) == 0u) {
       comp_add(hx, lx, px);

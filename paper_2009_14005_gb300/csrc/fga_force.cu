@@ -198,7 +198,6 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
   const Xf xf = load_xf(ds);
   const unsigned ntasks = (unsigned)((M + 31) / 32) * (unsigned)K;
   unsigned long long total = 0;
-  bool overflow = false;
   for (;;) {
     unsigned slot = 0;
     if (lane == 0) slot = atomicAdd(&ds->bh_next, 1u);
@@ -213,7 +212,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
     float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
     unsigned count = 0;
     unsigned steps = 0;
-    bh_task(rec, bodies, front, f, y, valid, eps2, theta2, stk, overflow, hx, hy, hz, lx, ly, lz,
+    bh_task(rec, bodies, front, f, y, valid, eps2, theta2, stk, hx, hy, hz, lx, ly, lz,
             count, steps);
     if (cost && lane == 0) cost[task] = steps + 1u;
     // a task that added no term anywhere in the warp leaves exact zeros: with a
@@ -226,7 +225,6 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
     if (mask && any && lane == 0) atomicOr(&mask[g], 1ull << f);
     total += valid ? count : 0u;
   }
-  if (__any_sync(FULL, overflow) && lane == 0) atomicOr(&ds->status, 1);
   for (int off = 16; off > 0; off >>= 1) total += __shfl_down_sync(FULL, total, off);
   if (lane == 0) {
     if (total) atomicAdd(&ds->interactions, total);

@@ -501,7 +501,7 @@ class Runner {
       o.start_ms = sl.start_ms;
       o.done_ms = now;
       if (o.result.status == FGA_EINTERNAL)
-        copy_message(o.error, sizeof(o.error), "a device check failed (traversal stack or non-finite fit)");
+        copy_message(o.error, sizeof(o.error), "a device check failed: non-finite transform");
       release_slot(sl, s_);
     }
     active_.erase(std::remove_if(active_.begin(), active_.end(),
