@@ -500,7 +500,7 @@ def run_ours_batch(a):
     torch.cuda.synchronize()
     clocks.start()
     launches0 = fga.fga_launch_count()
-    step_ms, inter, regs = [], 0, 0
+    step_ms, inter, regs, setup_ms = [], 0, 0, []
     for k in range(a.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -512,6 +512,7 @@ def run_ours_batch(a):
         step_ms.append(e0.elapsed_time(e1))
         inter += st["interactions"]
         regs += len(res)
+        setup_ms.append(st["elapsed_ms"] - st["force_ms"])  # preparation before the iteration graph
     torch.cuda.synchronize()
     barrier(world)
     launches = fga.fga_launch_count() - launches0
@@ -580,6 +581,7 @@ def run_ours_batch(a):
             "registrations_per_s": regs_all / (t_max / 1e3),
             "one_pair_path": {"registrations_per_s": nb / (seq_ms / 1e3), "ms_per_batch": seq_ms,
                               "note": "the same %d pairs, one fga_register call each" % nb},
+            "setup_ms_per_step": float(np.mean(setup_ms)),
             "p50_ms": float(np.percentile(step_ms, 50)), "p99_ms": float(np.percentile(step_ms, 99)),
             "e2e": {"value": e2e_iall / (e2e_tmax / 1e3) if e2e_tmax > 0 else None,
                     "unit": "interactions/s",

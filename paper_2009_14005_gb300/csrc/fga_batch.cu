@@ -20,6 +20,9 @@
 #include <cstring>
 #include <map>
 #include <vector>
+#include <string>
+#include <thread>
+#include <memory>
 
 #include "fga_batch.cuh"
 #include "fga_device.cuh"
@@ -375,6 +378,34 @@ extern "C" int64_t fga_direct_max_n(int64_t new_value) {
   return new_value > 0 ? g_direct_max_n.exchange(new_value) : g_direct_max_n.load();
 }
 
+namespace {
+
+// One host worker of the batch preparation: its stream, arena and trees.
+struct PrepWorker {
+  cudaStream_t st = nullptr;
+  std::unique_ptr<Scratch> sc;
+  std::vector<fga_tree*> trees;
+  int64_t h2d = 0;
+  int rc = 0;
+  std::string msg;
+  int start(cudaEvent_t ready) {
+    FGA_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    FGA_CUDA_TRY(cudaStreamWaitEvent(st, ready, 0));
+    sc.reset(new Scratch(st));
+    return FGA_OK;
+  }
+  ~PrepWorker() {
+    for (fga_tree* t : trees) fga_tree_destroy(t);
+    sc.reset();
+    if (st) {
+      cudaStreamSynchronize(st);
+      cudaStreamDestroy(st);
+    }
+  }
+};
+
+}  // namespace
+
 extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_params* p,
                                   fga_pair_result* results, fga_stats* stats, void* stream) {
   clear_error();
@@ -403,13 +434,6 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
     iters = std::max(iters, pp[k]->max_iter);
   }
   Scratch sc(s);
-  std::vector<fga_tree*> trees;
-  struct Cleanup {
-    std::vector<fga_tree*>& trees;
-    ~Cleanup() {
-      for (fga_tree* t : trees) fga_tree_destroy(t);
-    }
-  } cleanup{trees};
   // Pairs with the same inputs and the same input-shaping parameters (e.g.
   // the cells of a parameter grid over one pair) share one preparation: the
   // normalised clouds, masses, tree or packed reference and packed template.
@@ -440,26 +464,79 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
   std::vector<double*> mu0(count, nullptr);
   DevState* dsarr = nullptr;
   if (sc.alloc(&dsarr, (size_t)count)) return FGA_ENOMEM;
-  for (int k = 0; k < count; ++k) {
-    const fga_pair& q = pairs[k];
-    if (src[k] != k) continue;
-    if ((rc = prepare_inputs(sc, q.X, q.N, q.Y, q.M, q.mX, q.mY, pp[k], prep[k], h2d, s))) return rc;
-  }
-  // all checks of all pairs with one synchronisation
-  std::vector<int> flags((size_t)8 * count);
+  // Preparation of the distinct inputs (normalisation, masses, checks, tree
+  // or packed reference, packed template) in parallel: host workers with a
+  // stream and an arena each, so that one pair's tree build (which waits for
+  // the GPU between its levels) does not hold up the others. Every output
+  // slot is written by exactly one worker; each worker's memory lives until
+  // the call returns, after the iteration graph has finished.
+  std::vector<int> uniq;
   for (int k = 0; k < count; ++k)
-    if (src[k] == k)
-      FGA_CUDA_TRY(cudaMemcpyAsync(&flags[8 * k], prep[k].flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
-  FGA_CUDA_TRY(cudaStreamSynchronize(s));
-  for (int k = 0; k < count; ++k)
-    if (src[k] == k && (rc = check_pair_flags(&flags[8 * k], "fga_register_batch", k))) return rc;
-  for (int k = 0; k < count; ++k) {
-    if (src[k] != k) continue;
-    fga_tree* t = nullptr;
-    rc = build_inputs(pairs[k], prep[k], pp[k], sc, &t, host[k], &mu0[k], s);
-    if (t) trees.push_back(t);
-    if (rc) return rc;
+    if (src[k] == k) uniq.push_back(k);
+  const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+  const int nw = (int)std::min<size_t>(uniq.size(), std::min(8u, hw));
+  std::vector<std::unique_ptr<PrepWorker>> workers;
+  {
+    int dev = 0;
+    FGA_CUDA_TRY(cudaGetDevice(&dev));
+    cudaEvent_t ready = nullptr;
+    FGA_CUDA_TRY(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    struct EvFree {
+      cudaEvent_t e;
+      ~EvFree() { cudaEventDestroy(e); }
+    } evfree{ready};
+    FGA_CUDA_TRY(cudaEventRecord(ready, s));  // inputs the caller wrote on s
+    for (int w = 0; w < nw; ++w) workers.emplace_back(new PrepWorker);
+    auto work = [&](int w) {
+      PrepWorker& W = *workers[w];
+      cudaSetDevice(dev);
+      clear_error();
+      W.rc = W.start(ready);
+      std::vector<int> mine;
+      for (size_t u = w; u < uniq.size() && !W.rc; u += nw) mine.push_back(uniq[u]);
+      for (int k : mine) {
+        if (W.rc) break;
+        const fga_pair& q = pairs[k];
+        W.rc = prepare_inputs(*W.sc, q.X, q.N, q.Y, q.M, q.mX, q.mY, pp[k], prep[k], W.h2d, W.st);
+      }
+      std::vector<int> flags((size_t)8 * mine.size());
+      for (size_t j = 0; j < mine.size() && !W.rc; ++j)
+        if (cudaMemcpyAsync(&flags[8 * j], prep[mine[j]].flags, 8 * sizeof(int), cudaMemcpyDeviceToHost,
+                            W.st) != cudaSuccess) {
+          set_error("fga_register_batch: reading the input checks failed");
+          W.rc = FGA_ECUDA;
+        }
+      if (!W.rc && cudaStreamSynchronize(W.st) != cudaSuccess) {
+        set_error("fga_register_batch: input preparation failed on the device");
+        W.rc = FGA_ECUDA;
+      }
+      for (size_t j = 0; j < mine.size() && !W.rc; ++j)
+        W.rc = check_pair_flags(&flags[8 * j], "fga_register_batch", mine[j]);
+      for (int k : mine) {
+        if (W.rc) break;
+        fga_tree* t = nullptr;
+        W.rc = build_inputs(pairs[k], prep[k], pp[k], *W.sc, &t, host[k], &mu0[k], W.st);
+        if (t) W.trees.push_back(t);
+      }
+      if (!W.rc && cudaStreamSynchronize(W.st) != cudaSuccess) {
+        set_error("fga_register_batch: input preparation failed on the device");
+        W.rc = FGA_ECUDA;
+      }
+      if (W.rc) W.msg = fga_last_error();
+    };
+    std::vector<std::thread> threads;
+    for (int w = 1; w < nw; ++w) threads.emplace_back(work, w);
+    if (nw > 0) work(0);
+    for (auto& t : threads) t.join();
   }
+  for (auto& W : workers) {
+    h2d += W->h2d;
+    if (W->rc && !rc) {
+      rc = W->rc;
+      set_error(W->msg);
+    }
+  }
+  if (rc) return rc;
   // every pair's own state, velocities, partial sums and block counter in
   // five allocations and one initialisation launch
   {
@@ -561,6 +638,9 @@ extern "C" int fga_register_batch(const fga_pair* pairs, int count, const fga_pa
     cudaGraph_t& g;
     cudaGraphExec_t& e;
     ~GraphCleanup() {
+      // the graph may still run on an error path: finish it before the
+      // memory it uses is released
+      if (cs) cudaStreamSynchronize(cs);
       if (e) cudaGraphExecDestroy(e);
       if (g) cudaGraphDestroy(g);
       if (a) cudaEventDestroy(a);
