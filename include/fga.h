@@ -374,9 +374,10 @@ int fga_get_direct_tile(int size_class, int* bs, int* qpt);
 /* ------------------------------------------------------------------ serving
  * A registration server: a continuous-batching engine on one GPU. Requests
  * (pairs, Algorithm 2 with the server's parameters) are submitted at any
- * time. An admission thread prepares each request on its own stream as soon
- * as the pair fits in the device-memory budget and a slot is free (FIFO:
- * a request waits for all requests submitted before it). The prepared pair
+ * time. Admission threads (cfg->prep_threads, each with its own stream)
+ * prepare each request as soon as the pair fits in the device-memory budget
+ * and a slot is free (FIFO: a request waits for all requests submitted before
+ * it; several are prepared at once). The prepared pair
  * (normalised template, velocities, tree or packed reference, state) stays
  * resident on the device. A runner thread advances all resident pairs
  * together, `iters_per_tick` iterations of every pair per tick (the batch
@@ -401,6 +402,8 @@ typedef struct fga_server_config {
                           when none is held. 0: 4e9 (about 2 ms of GPU time per
                           iteration); < 0: no limit. Fewer pairs sharing the GPU
                           finish sooner; enough of them keep it busy          */
+  int prep_threads;    /* threads preparing admitted requests (each with its own
+                          stream; they take requests in FIFO order); <= 0: 4 */
 } fga_server_config;
 
 typedef struct fga_served {

@@ -106,7 +106,7 @@ class fga_pair_result(ctypes.Structure):
 class fga_server_config(ctypes.Structure):
     _fields_ = [("mem_budget", ctypes.c_int64), ("max_pairs", ctypes.c_int),
                 ("iters_per_tick", ctypes.c_int), ("device", ctypes.c_int),
-                ("max_work", ctypes.c_double)]
+                ("max_work", ctypes.c_double), ("prep_threads", ctypes.c_int)]
 
 
 class fga_served(ctypes.Structure):
@@ -601,11 +601,12 @@ class Server:
     times submit_ms, admit_ms, start_ms, done_ms in ms since creation)."""
 
     def __init__(self, p: fga_params | None = None, mem_budget: int = 0, max_pairs: int = 0,
-                 iters_per_tick: int = 0, device: int = -1, max_work: float = 0.0):
+                 iters_per_tick: int = 0, device: int = -1, max_work: float = 0.0,
+                 prep_threads: int = 0):
         self._h = ctypes.c_void_p()
         self._p = p or params()
         cfg = fga_server_config(int(mem_budget), int(max_pairs), int(iters_per_tick), int(device),
-                                float(max_work))
+                                float(max_work), int(prep_threads))
         _err(lib.fga_server_create(ctypes.byref(self._p), ctypes.byref(cfg), ctypes.byref(self._h)))
         self._keep = {}
 

@@ -73,7 +73,8 @@ struct fga_server {
   fga_server_config cfg{};
   int device = 0;
   int64_t budget = 0;
-  cudaStream_t prep_s = nullptr, run_s = nullptr, read_s = nullptr;
+  std::vector<cudaStream_t> prep_s;  // one per preparation thread
+  cudaStream_t run_s = nullptr, read_s = nullptr;
   Clock::time_point t0;
 
   std::mutex mu;
@@ -88,7 +89,8 @@ struct fga_server {
   int64_t ticks = 0, pair_iters = 0;
   double busy_ms = 0;
   bool stop = false;
-  std::thread admit_thr, run_thr;
+  std::vector<std::thread> admit_thr;
+  std::thread run_thr;
 
   double now_ms() const { return std::chrono::duration<double, std::milli>(Clock::now() - t0).count(); }
 
@@ -112,10 +114,9 @@ struct fga_server {
 
 namespace {
 
-// Prepares one request on the admission stream; on success the slot holds the
+// Prepares one request on a preparation stream; on success the slot holds the
 // resident pair and its state is initialised.
-int prepare_slot(fga_server* S, Slot& sl) {
-  cudaStream_t s = S->prep_s;
+int prepare_slot(fga_server* S, Slot& sl, cudaStream_t s) {
   const fga_pair& q = sl.req.q;
   int64_t h2d = 0;
   Prepared pr;
@@ -147,8 +148,9 @@ void release_slot(Slot& sl, cudaStream_t s) {
   }
 }
 
-void admit_loop(fga_server* S) {
+void admit_loop(fga_server* S, int w) {
   cudaSetDevice(S->device);
+  cudaStream_t ps = S->prep_s[w];
   for (;;) {
     std::unique_ptr<Slot> sl(new Slot);
     {
@@ -170,11 +172,11 @@ void admit_loop(fga_server* S) {
       sl->admit_ms = S->now_ms();
     }
     clear_error();
-    const int rc = prepare_slot(S, *sl);
+    const int rc = prepare_slot(S, *sl, ps);
     std::string msg = rc ? std::string(fga_last_error()) : std::string();
     if (rc) {
-      release_slot(*sl, S->prep_s);
-      cudaStreamSynchronize(S->prep_s);
+      release_slot(*sl, ps);
+      cudaStreamSynchronize(ps);
     }
     std::lock_guard<std::mutex> lk(S->mu);
     --S->preparing;
@@ -569,6 +571,8 @@ extern "C" int fga_server_create(const fga_params* p, const fga_server_config* c
   if (cfg) S->cfg = *cfg;
   if (S->cfg.max_pairs <= 0) S->cfg.max_pairs = 4096;
   if (S->cfg.iters_per_tick <= 0) S->cfg.iters_per_tick = 4;
+  if (S->cfg.prep_threads <= 0) S->cfg.prep_threads = 4;
+  S->cfg.prep_threads = std::min(S->cfg.prep_threads, 64);
   S->max_work = S->cfg.max_work == 0 ? 4e9 : S->cfg.max_work;
   if (S->cfg.device >= 0) {
     FGA_CUDA_TRY(cudaSetDevice(S->cfg.device));
@@ -582,12 +586,13 @@ extern "C" int fga_server_create(const fga_params* p, const fga_server_config* c
     FGA_CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     S->budget = (int64_t)(free_b / 4 * 3);
   }
-  FGA_CUDA_TRY(cudaStreamCreateWithFlags(&S->prep_s, cudaStreamNonBlocking));
+  S->prep_s.assign(S->cfg.prep_threads, nullptr);
+  for (auto& ps : S->prep_s) FGA_CUDA_TRY(cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking));
   FGA_CUDA_TRY(cudaStreamCreateWithFlags(&S->run_s, cudaStreamNonBlocking));
   FGA_CUDA_TRY(cudaStreamCreateWithFlags(&S->read_s, cudaStreamNonBlocking));
   S->t0 = Clock::now();
   fga_server* raw = S.release();
-  raw->admit_thr = std::thread(admit_loop, raw);
+  for (int w = 0; w < raw->cfg.prep_threads; ++w) raw->admit_thr.emplace_back(admit_loop, raw, w);
   raw->run_thr = std::thread(run_loop, raw);
   *out = raw;
   return FGA_OK;
@@ -699,14 +704,17 @@ extern "C" int fga_server_destroy(fga_server* S) {
   S->cv_admit.notify_all();
   S->cv_run.notify_all();
   S->cv_done.notify_all();
-  if (S->admit_thr.joinable()) S->admit_thr.join();
+  for (auto& t : S->admit_thr)
+    if (t.joinable()) t.join();
   if (S->run_thr.joinable()) S->run_thr.join();
   cudaSetDevice(S->device);
   for (auto& sl : S->ready) release_slot(*sl, S->run_s);
   S->ready.clear();
   cudaStreamSynchronize(S->run_s);
-  cudaStreamSynchronize(S->prep_s);
-  cudaStreamDestroy(S->prep_s);
+  for (cudaStream_t ps : S->prep_s) {
+    cudaStreamSynchronize(ps);
+    cudaStreamDestroy(ps);
+  }
   cudaStreamDestroy(S->run_s);
   cudaStreamDestroy(S->read_s);
   delete S;
