@@ -103,6 +103,8 @@ def lib():
         _lib.orc_masses_niv_d.argtypes = [D, L, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, D]
         _lib.orc_kabsch_d.argtypes = [D, D, L, ctypes.c_int, D, D]
+        _lib.orc_masses_knn.argtypes = [D, L, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                        ctypes.c_double, D]
         _lib.orc_masses_rbf.argtypes = [D, L, LP, ctypes.c_int, ctypes.c_double, ctypes.c_double, D]
         _lib.orc_direct_acc.argtypes = [D, D, L, D, L, ctypes.c_double, ctypes.c_double, D, D]
         _lib.orc_tree_build.argtypes = [D, D, L, ctypes.c_int]
@@ -178,6 +180,17 @@ def masses_niv(P, lattice: int = 16, a: float = -5.0, b: float = 5.0, total: flo
     rc = lib().orc_masses_niv_d(_p(P), len(P), dim, lattice, a, b, total, _p(out))
     if rc != 0:
         raise ValueError("bad NIV arguments")
+    return out
+
+
+def masses_knn(P, k: int = 16, dim: int = 3, a: float = -5.0, b: float = 5.0, total: float = 1.0):
+    """Inverse-density masses from the distance to the k-th nearest neighbour
+    (reading in the C source)."""
+    P = _d(P)
+    out = np.empty(len(P))
+    rc = lib().orc_masses_knn(_p(P), len(P), k, dim, a, b, total, _p(out))
+    if rc != 0:
+        raise ValueError("bad kNN-mass arguments")
     return out
 
 

@@ -13,6 +13,9 @@
  *   orc_normalize / orc_denormalize  Appendix, Eqs. A.1-A.3 (and the derivation
  *                                    of dnorm(t) that follows them)
  *   orc_masses_niv                   Sec. IV-F.2, Eq. 18 (NIV measure)
+ *   orc_masses_knn                   Sec. IV-F (point masses from a per-point
+ *                                    feature): inverse local density from the
+ *                                    distance to the k-th nearest neighbour
  *   orc_masses_rbf                   Sec. IV-F.1, Eq. 17 (RBF mass interpolant);
  *                                    with the NIV weights, Eq. 19 (SPM) is
  *                                    their point-wise product
@@ -176,6 +179,52 @@ int orc_masses_niv_d(const double* P, long n, int dim, int lattice, double a, do
 int orc_masses_niv(const double* P, long n, int lattice, double a, double b, double total,
                    double* m_out) {
     return orc_masses_niv_d(P, n, 3, lattice, a, b, total, m_out);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Inverse-density masses from the k-th nearest neighbour                     */
+/* ------------------------------------------------------------------------ */
+
+/* Reading (a smooth-particle mass from the k nearest neighbours): the local
+ * density at P_i is k points per ball reaching its k-th nearest other point,
+ * of radius r_k(i); the mass is inversely proportional to it, m_i ~ r_k(i)^D
+ * (D = dim, the ball's volume up to a constant), r_k floored at
+ * r_min = 1e-6 (b - a) so that repeated points keep a positive mass. Scaled
+ * to sum to `total`. Brute force: every other point, k smallest squared
+ * distances kept sorted. dim 2 uses the x, y components. */
+int orc_masses_knn(const double* P, long n, int k, int dim, double a, double b, double total,
+                   double* m_out) {
+    if (n <= (long)k || k < 1 || k > 64 || (dim != 2 && dim != 3) || !(b > a)) return -1;
+    const double rmin = 1e-6 * (b - a);
+    double wsum = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : wsum)
+    for (long i = 0; i < n; ++i) {
+        double best[64];
+        int have = 0;
+        for (long j = 0; j < n; ++j) {
+            if (j == i) continue;
+            double d2 = 0;
+            for (int c = 0; c < dim; ++c) {
+                double d = P[3 * j + c] - P[3 * i + c];
+                d2 += d * d;
+            }
+            if (have < k) {
+                int q = have++;
+                while (q > 0 && best[q - 1] > d2) { best[q] = best[q - 1]; --q; }
+                best[q] = d2;
+            } else if (d2 < best[k - 1]) {
+                int q = k - 1;
+                while (q > 0 && best[q - 1] > d2) { best[q] = best[q - 1]; --q; }
+                best[q] = d2;
+            }
+        }
+        double r = sqrt(best[k - 1]);
+        if (r < rmin) r = rmin;
+        m_out[i] = dim == 3 ? r * r * r : r * r;
+        wsum += m_out[i];
+    }
+    for (long i = 0; i < n; ++i) m_out[i] = total * m_out[i] / wsum;
+    return 0;
 }
 
 /* ------------------------------------------------------------------------ */
