@@ -58,6 +58,9 @@ def parse_args(argv=None):
     ap.add_argument("--theta", type=float, default=None, help="BH opening parameter")
     ap.add_argument("--pairs", type=int, default=2, help="distinct seeded pairs per rank")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--masses", choices=["default", "niv16", "knn16", "uniform"], default="default",
+                    help="reference masses: the workload's default (NIV lattice 16 for LiDAR), the NIV "
+                         "lattice, inverse density from the 16th nearest neighbour, or uniform")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=24,
                     help="oracle iterations in the CPU baseline's sample (about 10 s on 16 cores for "
@@ -224,6 +227,9 @@ def workload(a):
         v = getattr(a, k)
         if v is not None:
             w[k] = v
+    masses = getattr(a, "masses", "default")
+    w["masses"] = ("niv16" if w["niv"] else "uniform") if masses == "default" else masses
+    w["niv"] = w["masses"] == "niv16"
     return w
 
 
@@ -239,7 +245,10 @@ def workload_config(a):
     return {"workload": name, "N": w["n"], "M": w["n"], "iterations": w["iters"],
             "method": "barnes-hut" if w["method"] == "bh" else "all-pairs",
             "theta": w["theta"] if w["method"] == "bh" else None,
-            "masses": ("NIV lattice 16 (reference), uniform (template)" if w["niv"] else "uniform"),
+            "masses": {"niv16": "NIV lattice 16 (reference), uniform (template)",
+                       "knn16": "inverse density from the 16th nearest neighbour (reference), uniform "
+                                "(template)",
+                       "uniform": "uniform"}[w["masses"]],
             "eps": w["eps"], "eta": w["eta"], "dt": 0.1, "G": w["G"], "pairs_per_rank": a.pairs,
             "l2": "flushed between steps (256 MB device write outside the timed events)",
             "inputs": "resident in HBM at the start of each timed step"}
@@ -310,7 +319,8 @@ def lib_params(fga, a):
     w = workload(a)
     return fga.params(method={"bh": fga.FGA_BH, "direct": fga.FGA_DIRECT, "auto": fga.FGA_AUTO}[w["method"]],
                       theta=w["theta"], max_iter=w["iters"], G=w["G"], eps=w["eps"], eta=w["eta"],
-                      mass_mode=fga.FGA_MASS_NIV if w["niv"] else fga.FGA_MASS_UNIFORM, profile=1)
+                      mass_mode={"niv16": fga.FGA_MASS_NIV, "knn16": fga.FGA_MASS_KNN,
+                                 "uniform": fga.FGA_MASS_UNIFORM}[w["masses"]], lattice=16, profile=1)
 
 
 def cpu_sample(pair, a, iters):
@@ -330,8 +340,8 @@ def cpu_sample(pair, a, iters):
         keep = int(max(1, min(len(Y), 2e10 / (len(X) * iters))))
         Y = Y[:keep]
     p = oracle.Params(method=oracle.FGA_BH if w["method"] == "bh" else oracle.FGA_DIRECT,
-                      theta=w["theta"], max_iter=iters, niv_masses=w["niv"], G=w["G"], eps=w["eps"],
-                      eta=w["eta"])
+                      theta=w["theta"], max_iter=iters, niv_masses=w["niv"],
+                      knn_masses=w["masses"] == "knn16", lattice=16, G=w["G"], eps=w["eps"], eta=w["eta"])
     t0 = time.perf_counter()
     o = oracle.register_full(X, Y, p)
     dt = time.perf_counter() - t0

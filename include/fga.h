@@ -51,6 +51,8 @@ extern "C" {
 #define FGA_MASS_NIV 1     /* normalised intrinsic volume, Eq. 18       */
 #define FGA_MASS_RBF 2     /* landmark RBF interpolant, Eq. 17 (fga_masses_landmarks only) */
 #define FGA_MASS_SPM 3     /* smooth-particle masses, Eq. 19 (fga_masses_landmarks only)   */
+#define FGA_MASS_KNN 4     /* inverse local density from the k-th nearest neighbour:
+                              m_i ~ r_k(i)^D, k = `lattice` (8, 16 or 32)          */
 
 typedef struct fga_params {
   float G;           /* gravitational constant (paper default 66.7)             */
@@ -65,8 +67,9 @@ typedef struct fga_params {
   float a, b;        /* normalisation range (-5, 5)                             */
   int velocity_mode; /* FGA_VEL_UNCONSTRAINED or FGA_VEL_RIGID                  */
   int max_depth;     /* BH tree depth limit, 1..20 (20)                         */
-  int mass_mode;     /* reference masses in fga_register: FGA_MASS_UNIFORM/_NIV  */
-  int lattice;       /* NIV lattice resolution varrho (16)                      */
+  int mass_mode;     /* reference masses in fga_register: FGA_MASS_UNIFORM, _NIV
+                        or _KNN                                                */
+  int lattice;       /* NIV lattice resolution varrho (16), or k for FGA_MASS_KNN */
   int profile;       /* 1: time every force-kernel launch with CUDA events on the
                         launch stream (reported in fga_stats.force_ms)           */
   int dim;           /* D: 3 (default), or 2 for planar clouds. With 2, the
@@ -134,7 +137,9 @@ void fga_denormalize(const double R[9], const double t_norm[3], const double inf
 
 /* ----------------------------------------------------------------- Sec. IV-F */
 /* Point masses (boundary conditions, Sec. IV-F), scaled so that they sum to
- * `total`. mode = FGA_MASS_UNIFORM gives total/n each; FGA_MASS_NIV evaluates
+ * `total`. mode = FGA_MASS_KNN: m_i ~ r_k(i)^3, r_k the distance to the k-th
+ * nearest other point (k = lattice: 8, 16 or 32; n > k; r_k >= 1e-6 (b-a)).
+ * mode = FGA_MASS_UNIFORM gives total/n each; FGA_MASS_NIV evaluates
  * Eq. 18 on a lattice^3 lattice over [a, b]^3 (points are expected inside the
  * normalised domain; outside points are clamped to the border cells): each
  * point carries a ball of radius (b-a)/(2*3*lattice), a cell holding n points

@@ -79,6 +79,7 @@ class Params:
     b: float = 5.0
     lattice: int = 16
     niv_masses: bool = False
+    knn_masses: bool = False  # inverse-density masses from the k-th neighbour, k = lattice
     dim: int = 3  # 2: clouds given as (n, 2), registered in the plane
 
     def _c(self) -> _Params:
@@ -329,7 +330,9 @@ def register(Xn, mX, Yn, mY, params: Params, V0=None, want_traj: bool = False,
 
 def default_masses(Xn, Yn, params: Params):
     """Masses per the module docstring: X sums to 1 (uniform or NIV), Y mean dt."""
-    if params.niv_masses:
+    if params.knn_masses:
+        mX = masses_knn(Xn, params.lattice, params.dim, params.a, params.b, 1.0)
+    elif params.niv_masses:
         mX = masses_niv(Xn, params.lattice, params.a, params.b, 1.0, dim=params.dim)
     else:
         mX = masses_uniform(len(Xn), 1.0)

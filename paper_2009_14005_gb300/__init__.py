@@ -45,6 +45,7 @@ FGA_MASS_UNIFORM = 0
 FGA_MASS_NIV = 1
 FGA_MASS_RBF = 2
 FGA_MASS_SPM = 3
+FGA_MASS_KNN = 4
 FGA_MAX_LANDMARKS = 512
 
 SYMBOLS = [

@@ -199,8 +199,12 @@ int check_register_params(const fga_params* p) {
     set_error("b must exceed a");
     return FGA_EINVAL;
   }
-  if (p->mass_mode != FGA_MASS_UNIFORM && p->mass_mode != FGA_MASS_NIV) {
+  if (p->mass_mode != FGA_MASS_UNIFORM && p->mass_mode != FGA_MASS_NIV && p->mass_mode != FGA_MASS_KNN) {
     set_error("bad mass_mode");
+    return FGA_EINVAL;
+  }
+  if (p->mass_mode == FGA_MASS_KNN && p->lattice != 8 && p->lattice != 16 && p->lattice != 32) {
+    set_error("k (lattice) for FGA_MASS_KNN must be 8, 16 or 32");
     return FGA_EINVAL;
   }
   if (p->mass_mode == FGA_MASS_NIV && (p->lattice < 1 || p->lattice > 256)) {
@@ -394,8 +398,9 @@ int fga_masses(const float* pts, int64_t n, int mode, int lattice, float a, floa
   clear_error();
   cudaStream_t s = (cudaStream_t)stream;
   if (n <= 0 || !pts || !masses_out || !(total > 0) || !std::isfinite(total) ||
-      (mode != FGA_MASS_UNIFORM && mode != FGA_MASS_NIV) ||
-      (mode == FGA_MASS_NIV && (lattice < 1 || lattice > 256 || !(b > a)))) {
+      (mode != FGA_MASS_UNIFORM && mode != FGA_MASS_NIV && mode != FGA_MASS_KNN) ||
+      (mode == FGA_MASS_NIV && (lattice < 1 || lattice > 256 || !(b > a))) ||
+      (mode == FGA_MASS_KNN && ((lattice != 8 && lattice != 16 && lattice != 32) || n <= lattice || !(b > a)))) {
     set_error("fga_masses: bad arguments");
     return FGA_EINVAL;
   }

@@ -259,6 +259,46 @@ __global__ void k_niv_assign(const float* __restrict__ p, int64_t n, double a, d
     out[i] = (float)(w[niv_cell(p, i, a, h, L, dim)] * inv);
 }
 
+// Inverse-density weight of every point from its k-th nearest other point:
+// w_i = max(r_k(i), r_min)^dim (brute force over tiles of all points in shared
+// memory; the k smallest squared distances of a point are kept sorted in
+// registers by an unrolled insertion).
+template <int K>
+__global__ void __launch_bounds__(256) k_knn_weight(const float* __restrict__ p, int64_t n, int dim,
+                                                    float rmin, float* __restrict__ w) {
+  __shared__ float4 tile[256];
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const bool valid = i < n;
+  const float x = valid ? p[3 * i] : 0.f, y = valid ? p[3 * i + 1] : 0.f;
+  const float z = (valid && dim == 3) ? p[3 * i + 2] : 0.f;
+  float best[K];
+#pragma unroll
+  for (int q = 0; q < K; ++q) best[q] = FLT_MAX;
+  for (int64_t base = 0; base < n; base += 256) {
+    const int64_t j = base + threadIdx.x;
+    tile[threadIdx.x] = j < n ? make_float4(p[3 * j], p[3 * j + 1], dim == 3 ? p[3 * j + 2] : 0.f, 0.f)
+                              : make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    const int cnt = n - base < 256 ? (int)(n - base) : 256;
+    for (int c = 0; c < cnt; ++c) {
+      const float4 q4 = tile[c];
+      const float dx = q4.x - x, dy = q4.y - y, dz = q4.z - z;
+      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      if (d2 < best[K - 1] && base + c != i) {
+        // new[q] = max(old[q-1], min(old[q], d2)), from the top down
+#pragma unroll
+        for (int q = K - 1; q > 0; --q) best[q] = fmaxf(best[q - 1], fminf(best[q], d2));
+        best[0] = fminf(best[0], d2);
+      }
+    }
+    __syncthreads();
+  }
+  if (valid) {
+    const float r = fmaxf(sqrtf(best[K - 1]), rmin);
+    w[i] = dim == 3 ? r * r * r : r * r;
+  }
+}
+
 // (x, y) pairs -> (x, y, 0): a planar cloud in the plane z = 0.
 __global__ void k_embed2(const float* __restrict__ in, int64_t n, float* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
@@ -283,6 +323,23 @@ int embed_planar(const float* in2, int64_t n, float* out3, cudaStream_t s) {
 
 int masses_device(const float* pts, int64_t n, int mode, int lattice, float a, float b,
                   double total, float* out, cudaStream_t s, int dim) {
+  if (mode == FGA_MASS_KNN) {
+    float* w = nullptr;
+    int rc = dev_alloc_n(&w, (size_t)n, s);
+    if (rc) return rc;
+    const float rmin = 1e-6f * (b - a);
+    const unsigned g = (unsigned)((n + 255) / 256);
+    if (lattice == 8)
+      k_knn_weight<8><<<g, 256, 0, s>>>(pts, n, dim, rmin, w);
+    else if (lattice == 32)
+      k_knn_weight<32><<<g, 256, 0, s>>>(pts, n, dim, rmin, w);
+    else
+      k_knn_weight<16><<<g, 256, 0, s>>>(pts, n, dim, rmin, w);
+    FGA_LAUNCH_CHECK("knn_weight");
+    rc = rescale_masses(w, n, total, out, s);
+    dev_free(w, s);
+    return rc;
+  }
   if (mode == FGA_MASS_UNIFORM) {
     k_fill<<<red_grid(n), RB, 0, s>>>(out, n, (float)(total / (double)n));
     FGA_LAUNCH_CHECK("fill");
