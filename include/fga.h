@@ -43,6 +43,10 @@ extern "C" {
 #define FGA_DIRECT 0 /* all-pairs sum of Eq. 6                          */
 #define FGA_BH 1     /* Barnes-Hut tree (Algorithm 1) + BHForce (Eq. 15) */
 #define FGA_AUTO 2   /* FGA_DIRECT when N <= fga_direct_max_n(0), else FGA_BH */
+#define FGA_WALK_AUTO 0 /* by template size: per-lane walks while there are too few
+                           64-point groups to keep every resident warp busy */
+#define FGA_WALK_LANE 1
+#define FGA_WALK_COOP 2
 
 #define FGA_VEL_UNCONSTRAINED 0 /* velocities of Eq. 9 persist between iterations */
 #define FGA_VEL_RIGID 1         /* velocities replaced by the rigid motion        */
@@ -78,6 +82,12 @@ typedef struct fga_params {
                         are registered in the plane (quadtree, 2-D NIV discs,
                         the 2 x 2 rigid fit of Eq. 14), and R_out / t_out keep
                         the 3-D layout: R = diag(R2, 1), t = (t2, ~0)         */
+  int bh_walk;       /* Barnes-Hut traversal of the one-pair path (the result is
+                        the same up to FP32 rounding order): FGA_WALK_AUTO (0),
+                        FGA_WALK_LANE (one walk per template point) or
+                        FGA_WALK_COOP (one walk per 64 points, each point
+                        judging every node the walk visits); the batch and
+                        server paths always use FGA_WALK_COOP                 */
 } fga_params;
 
 /* Fills `p` with the paper's defaults (Sec. V, parameter settings):

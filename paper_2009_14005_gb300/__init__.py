@@ -39,6 +39,9 @@ FGA_EINTERNAL = -5
 FGA_DIRECT = 0
 FGA_BH = 1
 FGA_AUTO = 2
+FGA_WALK_AUTO = 0  # Barnes-Hut walk by template size
+FGA_WALK_LANE = 1  # one walk per template point
+FGA_WALK_COOP = 2  # one walk per 64 template points
 FGA_VEL_UNCONSTRAINED = 0
 FGA_VEL_RIGID = 1
 FGA_MASS_UNIFORM = 0
@@ -68,7 +71,8 @@ class fga_params(ctypes.Structure):
                 ("normalize", ctypes.c_int), ("a", ctypes.c_float), ("b", ctypes.c_float),
                 ("velocity_mode", ctypes.c_int), ("max_depth", ctypes.c_int),
                 ("mass_mode", ctypes.c_int), ("lattice", ctypes.c_int),
-                ("profile", ctypes.c_int), ("dim", ctypes.c_int)]
+                ("profile", ctypes.c_int), ("dim", ctypes.c_int),
+                ("bh_walk", ctypes.c_int)]
 
 
 class fga_stats(ctypes.Structure):

@@ -121,6 +121,10 @@ int check_params(const fga_params* p, bool need_tree) {
     set_error("dim must be 2 or 3");
     return FGA_EINVAL;
   }
+  if (p->bh_walk != FGA_WALK_AUTO && p->bh_walk != FGA_WALK_LANE && p->bh_walk != FGA_WALK_COOP) {
+    set_error("bh_walk must be FGA_WALK_AUTO, FGA_WALK_LANE or FGA_WALK_COOP");
+    return FGA_EINVAL;
+  }
   if (p->max_iter < 0) {
     set_error("max_iter must be >= 0");
     return FGA_EINVAL;
@@ -310,6 +314,7 @@ struct fga_state {
   int queued = 0;
   unsigned* bh_cost = nullptr;   // BH: step count of every task in the last launch
   unsigned* bh_order = nullptr;  // BH: heavy-first task order derived from bh_cost
+  int bh_kind = 0;               // BH: walk of the force launch (bh_walk_kind)
   unsigned bh_ntasks = 0;
   int bh_launches = 0;
   bool bh_have_order = false;
@@ -338,6 +343,7 @@ void fga_params_default(fga_params* p) {
   p->lattice = 16;
   p->profile = 0;
   p->dim = 3;
+  p->bh_walk = FGA_WALK_AUTO;
 }
 
 const char* fga_last_error(void) { return g_err.c_str(); }
@@ -468,7 +474,7 @@ int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N,
   if (sc.alloc(&fb.hi, (size_t)fb.S * M) || sc.alloc(&fb.lo, (size_t)fb.S * M)) return FGA_ENOMEM;
   if ((rc = launch_state_init(ds, nullptr, s))) return rc;
   if (tree)
-    rc = launch_bh(tree, Y0, M, ds, p->eps, p->theta, fb, s);
+    rc = launch_bh(tree, Y0, M, ds, p->eps, p->theta, fb, s, bh_walk_kind(M, p->bh_walk));
   else
     rc = launch_direct(X4, N, Y0, M, ds, p->eps, plan, fb, s);
   if (rc) return rc;
@@ -520,7 +526,8 @@ static int state_create_checked(const float* Xn, const float* mX, int64_t N, con
     return fail(FGA_ENOMEM);
   if (bh && dev_alloc_n(&st->perm, M, s)) return fail(FGA_ENOMEM);
   if (bh) {
-    st->bh_ntasks = (unsigned)((M + 31) / 32) * (unsigned)st->tree->n_front;
+    st->bh_kind = bh_walk_kind(M, p->bh_walk);
+    st->bh_ntasks = bh_tasks(M, st->tree->n_front, bh_points_per_lane(st->bh_kind));
     if (dev_alloc_n(&st->bh_cost, st->bh_ntasks, s) ||
         dev_alloc_n(&st->bh_order, (size_t)st->bh_ntasks + TASK_ORDER_SCRATCH, s))
       return fail(FGA_ENOMEM);
@@ -566,7 +573,7 @@ static int step_impl(fga_state* st, int n_iter, cudaStream_t s) {
     int rc;
     if (p.profile) FGA_CUDA_TRY(cudaEventRecord(st->events[2 * st->timed], s));
     if (p.method == FGA_BH) {
-      rc = launch_bh(st->tree, st->Y0, st->M, st->ds, p.eps, p.theta, st->fb, s,
+      rc = launch_bh(st->tree, st->Y0, st->M, st->ds, p.eps, p.theta, st->fb, s, st->bh_kind,
                      st->bh_have_order ? st->bh_order : nullptr, st->bh_cost);
       // heavy-first order for the following launches, refreshed on a schedule
       // (the task costs drift slowly as the template moves)

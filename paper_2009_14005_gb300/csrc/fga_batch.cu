@@ -4,11 +4,12 @@
 //
 // Force launch: the warp tasks of all pairs are numbered consecutively, pair
 // by pair (a prefix sum over the pairs maps a task to its pair by binary
-// search); warps take tasks from a device counter. A Barnes-Hut task is (pair, 32 template points,
-// frontier cell) and runs the same per-lane BHForce walk as the single-pair
-// kernel. An all-pairs task is (pair, 32 template points, chunk of up to
-// BATCH_CHUNK reference points): the warp stages 32 sources at a time in
-// shared memory and every lane adds them to its own point (Eq. 6).
+// search); warps take tasks from a device counter. A Barnes-Hut task is (pair,
+// 64 template points, frontier cell) and runs the same cooperative BHForce
+// walk as the single-pair kernel. An all-pairs task is (pair, 64 template
+// points, chunk of up to BATCH_CHUNK reference points): the warp stages 32
+// sources at a time in shared memory and every lane adds them to its two
+// points (Eq. 6).
 // Epilogue launch: blocks are assigned to pairs the same way; each pair's blocks run the
 // ODE step and reductions, and the pair's last block runs its rigid fit, so
 // the rigid fits of all pairs run in parallel. A pair whose convergence test
@@ -51,10 +52,8 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch
                                                                      unsigned ntasks, unsigned* ctr,
                                                                      const unsigned* __restrict__ order,
                                                                      unsigned* __restrict__ cost) {
-  __shared__ unsigned s_stack[BATCH_WARPS][BH_DEPTH][32];
   __shared__ float4 s_tile[BATCH_WARPS][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned* const stk = &s_stack[w][0][lane];
   for (;;) {
     unsigned slot = 0;
     if (lane == 0) slot = atomicAdd(&ctr[0], 1u);
@@ -73,20 +72,29 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch
     const unsigned f = local - grp * (unsigned)P.K;
     const Xf xf = load_xf(ds);
     if (P.method == FGA_BH) {
-      // 32 template points, one per lane, against frontier cell f
-      const int64_t i = (int64_t)grp * 32 + lane;
-      const bool valid = i < M;
-      const float3 y = place(xf, P.Y0[valid ? i : 0]);
-      float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-      unsigned count = 0, steps = 0;
-      bh_task(P.rec, P.bodies, P.front, f, y, valid, eps2, theta2, stk, hx, hy, hz, lx, ly,
-              lz, count, steps);
-      if (cost && lane == 0) cost[task] = steps + 1u;
-      if (valid) {
-        P.hi[(int64_t)f * M + i] = make_float4(hx, hy, hz, 0.f);
-        P.lo[(int64_t)f * M + i] = make_float4(lx, ly, lz, 0.f);
+      // 32 * BATCH_BH_NP template points against frontier cell f (one walk for all)
+      int64_t i[BATCH_BH_NP];
+      bool valid[BATCH_BH_NP];
+      float3 y[BATCH_BH_NP];
+#pragma unroll
+      for (int q = 0; q < BATCH_BH_NP; ++q) {
+        i[q] = (int64_t)grp * (32 * BATCH_BH_NP) + 32 * q + lane;
+        valid[q] = i[q] < M;
+        y[q] = place(xf, P.Y0[valid[q] ? i[q] : 0]);
       }
-      unsigned long long c = valid ? count : 0u;
+      float h[BATCH_BH_NP][3] = {}, lo[BATCH_BH_NP][3] = {};
+      unsigned cnt[BATCH_BH_NP] = {}, steps = 0;
+      bh_walk<BATCH_BH_NP>(P.rec, P.bodies, P.front, f, y, valid, eps2, theta2, h, lo, cnt, steps);
+      if (cost && lane == 0) cost[task] = steps + 1u;
+      unsigned long long c = 0;
+#pragma unroll
+      for (int q = 0; q < BATCH_BH_NP; ++q) {
+        if (valid[q]) {
+          P.hi[(int64_t)f * M + i[q]] = make_float4(h[q][0], h[q][1], h[q][2], 0.f);
+          P.lo[(int64_t)f * M + i[q]] = make_float4(lo[q][0], lo[q][1], lo[q][2], 0.f);
+          c += cnt[q];
+        }
+      }
       for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(FULL, c, off);
       if (lane == 0 && c) atomicAdd(&ds->interactions, c);
     } else {
@@ -360,7 +368,7 @@ bool batch_layout(const std::vector<PairDev>& pairs, std::vector<unsigned>& task
   block_start.assign(pairs.size() + 1, 0u);
   int64_t nt = 0, nb = 0;
   for (size_t k = 0; k < pairs.size(); ++k) {
-    const int64_t gs = pairs[k].method == FGA_BH ? 32 : 64;  // template points per task
+    const int64_t gs = pairs[k].method == FGA_BH ? 32 * BATCH_BH_NP : 64;  // template points per task
     nt += (pairs[k].M + gs - 1) / gs * (int64_t)pairs[k].K;
     nb += pairs[k].nblk;
     if (nt >= ((int64_t)1 << 31) || nb >= ((int64_t)1 << 31)) return false;

@@ -461,6 +461,159 @@ __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const fl
   comp_add(hz, lz, pz);
 }
 
+// The saved ranges of the cooperative walk are spread over the warp's lanes
+// (lane k holds entry k); at most 20 are ever saved (see BH_DEPTH).
+static_assert(BH_DEPTH <= 32, "one saved range per lane");
+
+// The per-point BHForce of Algorithm 2 for the 32 * NP template points of a
+// warp (NP per lane), restricted to frontier cell f, walked once for the
+// whole warp. Every point still takes exactly its own terms: a node is judged
+// by the points that rejected all of its ancestors (bit masks m[q] over the
+// lanes, one per point slot q); a point accepting the node adds its monopole,
+// and the node's children are visited when at least one point rejected it,
+// with the masks of the points that did. Nodes are visited depth first in
+// child order, so each point adds its terms in the order of its own walk.
+// The control flow is the same in every lane: a node's record is one
+// broadcast load, and its bookkeeping (range, masks, saved ranges) is paid
+// once for the warp's points instead of once per point.
+// Adds into the compensated accumulators h[q], l[q] of point slot q and the
+// term counts cnt[q]; `steps` gains the number of nodes visited (the task's
+// cost).
+template <int NP>
+__device__ __forceinline__ void bh_walk(const float4* __restrict__ rec, const float4* __restrict__ bodies,
+                                        const FrontCell* __restrict__ front, unsigned f,
+                                        const float3 (&y)[NP], const bool (&valid)[NP], float eps2,
+                                        float theta2, float (&h)[NP][3], float (&l)[NP][3],
+                                        unsigned (&cnt)[NP], unsigned& steps) {
+  const int lane = threadIdx.x & 31;
+  const unsigned bit = 1u << lane;
+  float p[NP][3];
+  bool live[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    p[q][0] = p[q][1] = p[q][2] = 0.f;
+    live[q] = valid[q];
+  }
+  {
+    const int npath = front[f].npath;
+    const unsigned first_mask = front[f].first_mask;
+    for (int j = 0; j < npath; ++j) {
+      const int a = front[f].path[j];
+      const float4 cm = rec[2 * a];
+      const float l2 = rec[2 * a + 1].x;
+      const bool own = (first_mask >> j) & 1u;
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const float dx = cm.x - y[q].x, dy = cm.y - y[q].y, dz = cm.z - y[q].z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const bool accept = live[q] && l2 < theta2 * d2;
+        if (own) {
+          const float inv = rsqrt_fast(d2 + eps2);
+          const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
+          p[q][0] = fmaf(wgt, dx, p[q][0]);
+          p[q][1] = fmaf(wgt, dy, p[q][1]);
+          p[q][2] = fmaf(wgt, dz, p[q][2]);
+          cnt[q] += accept;
+        }
+        live[q] = live[q] && !accept;
+      }
+    }
+  }
+  unsigned m[NP], sm[NP], any = 0u;
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    m[q] = __ballot_sync(FULL, live[q]);
+    sm[q] = 0u;
+    any |= m[q];
+  }
+  // current sibling range e = next cell << 4 | cells left; saved ranges and
+  // their masks: entry k in lane k's se, sm[]
+  unsigned e = any != 0u ? (((unsigned)front[f].node << 4) | 1u) : 0u;
+  unsigned se = 0u;
+  int sp = 0;
+  while ((e & 15u) != 0u) {
+    ++steps;
+    const int v = (int)(e >> 4);
+    e += 15u;
+    const float4 cm = rec[2 * v];
+    const float4 ri = rec[2 * v + 1];
+    const int nchild = __float_as_int(ri.z);
+    bool rej[NP];
+    unsigned r[NP], rany = 0u;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const bool act = (m[q] & bit) != 0u;
+      const float dx = cm.x - y[q].x, dy = cm.y - y[q].y, dz = cm.z - y[q].z;
+      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      // single-particle leaves carry l^2 = -1: always accepted (one exact term)
+      const bool accept = act && ri.x < theta2 * d2;
+      const float inv = rsqrt_fast(d2 + eps2);
+      const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
+      p[q][0] = fmaf(wgt, dx, p[q][0]);
+      p[q][1] = fmaf(wgt, dy, p[q][1]);
+      p[q][2] = fmaf(wgt, dz, p[q][2]);
+      cnt[q] += accept;
+      rej[q] = act && !accept;
+      r[q] = __ballot_sync(FULL, rej[q]);
+      rany |= r[q];
+    }
+    if (rany != 0u) {
+      if (nchild > 0) {
+        // descend: save the rest of the current range, continue with the
+        // children, judged by the points that rejected this cell
+        if ((e & 15u) != 0u) {
+          if (lane == sp) {
+            se = e;
+#pragma unroll
+            for (int q = 0; q < NP; ++q) sm[q] = m[q];
+          }
+          ++sp;
+        }
+        e = ((unsigned)__float_as_int(ri.y) << 4) | (unsigned)nchild;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) m[q] = r[q];
+      } else if (nchild < -1) {
+        // leaf holding several particles, rejected by these points: add each exactly (rare)
+        const int b0 = __float_as_int(ri.y), nb = -nchild;
+        for (int b = 0; b < nb; ++b) {
+          const float4 qb = bodies[b0 + b];
+#pragma unroll
+          for (int q = 0; q < NP; ++q) {
+            const float ex = qb.x - y[q].x, ey = qb.y - y[q].y, ez = qb.z - y[q].z;
+            const float iq = rsqrt_fast(fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, eps2))));
+            const float wq = rej[q] ? qb.w * (iq * iq * iq) : 0.f;
+            p[q][0] = fmaf(wq, ex, p[q][0]);
+            p[q][1] = fmaf(wq, ey, p[q][1]);
+            p[q][2] = fmaf(wq, ez, p[q][2]);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < NP; ++q) cnt[q] += rej[q] ? (unsigned)nb : 0u;
+      }
+    }
+    // range exhausted: resume the innermost saved range
+    if ((e & 15u) == 0u && sp > 0) {
+      --sp;
+      e = __shfl_sync(FULL, se, sp);
+#pragma unroll
+      for (int q = 0; q < NP; ++q) m[q] = __shfl_sync(FULL, sm[q], sp);
+    }
+    if ((steps & 31u) == 0u) {
+#pragma unroll
+      for (int q = 0; q < NP; ++q)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          comp_add(h[q][c], l[q][c], p[q][c]);
+          p[q][c] = 0.f;
+        }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) comp_add(h[q][c], l[q][c], p[q][c]);
+}
+
 // ------------------------------------------------------------------ epilogue stages
 constexpr int EPI_BS = 256;  // threads per epilogue block
 

@@ -168,10 +168,12 @@ int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const
 // same sector. Warps hold 32 Morton-neighbouring points, so their walks touch
 // mostly the same cells and the loads are served by L1.
 //
-// Work is split into tasks (32-point group, frontier cell): a task first
-// judges the frontier cell's ancestors (a lane accepting one stops; the
-// monopole is added by the task owning the ancestor's first frontier cell),
-// then walks the frontier cell's subtree. Tasks are handed out dynamically
+// Work is split into tasks (group of template points, frontier cell): a task
+// first judges the frontier cell's ancestors (a point accepting one stops;
+// the monopole is added by the task owning the ancestor's first frontier
+// cell), then walks the frontier cell's subtree. Two walks: per lane (32-point
+// groups, bh_task) or cooperative (64-point groups, one walk for the warp,
+// bh_walk<2>), chosen by bh_walk_kind. Tasks are handed out dynamically
 // from a counter in DevState; the last warp to finish resets it.
 #ifndef FGA_BH_WARPS
 #define FGA_BH_WARPS 4
@@ -181,6 +183,9 @@ static constexpr int BH_WARPS = FGA_BH_WARPS;
 #ifndef FGA_BH_MINBLOCKS
 #define FGA_BH_MINBLOCKS 8  // resident blocks per SM the register budget is sized for
 #endif
+// NP = 0: one template point per lane, each lane walking its own point
+// (bh_task); NP > 0: NP points per lane, one walk for the warp (bh_walk).
+template <int NP>
 __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const float4* __restrict__ rec,
                                                          const float4* __restrict__ bodies,
                                                          const float4* __restrict__ Y0, int64_t M,
@@ -191,12 +196,13 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
                                                          const unsigned* __restrict__ order,
                                                          unsigned* __restrict__ cost,
                                                          unsigned long long* __restrict__ mask) {
+  constexpr int PL = NP == 0 ? 1 : NP;  // template points per lane
   if (ds->done) return;
-  __shared__ unsigned s_stack[BH_WARPS][BH_DEPTH][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned* const stk = &s_stack[w][0][lane];
+  const int lane = threadIdx.x & 31;
+  __shared__ unsigned s_stack[NP == 0 ? BH_WARPS : 1][NP == 0 ? BH_DEPTH : 1][32];
+  unsigned* const stk = &s_stack[NP == 0 ? threadIdx.x >> 5 : 0][0][lane];
   const Xf xf = load_xf(ds);
-  const unsigned ntasks = (unsigned)((M + 31) / 32) * (unsigned)K;
+  const unsigned ntasks = bh_tasks(M, K, PL);
   unsigned long long total = 0;
   for (;;) {
     unsigned slot = 0;
@@ -206,24 +212,38 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
     unsigned task = order ? order[slot] : slot;
     if (task >= ntasks) task = slot;  // never index past the task range
     const unsigned g = task / (unsigned)K, f = task % (unsigned)K;
-    const int64_t i = (int64_t)g * 32 + lane;
-    const bool valid = i < M;
-    const float3 y = place(xf, Y0[valid ? i : 0]);
-    float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
-    unsigned count = 0;
-    unsigned steps = 0;
-    bh_task(rec, bodies, front, f, y, valid, eps2, theta2, stk, hx, hy, hz, lx, ly, lz,
-            count, steps);
-    if (cost && lane == 0) cost[task] = steps + 1u;
-    // a task that added no term anywhere in the warp leaves exact zeros: with a
-    // mask its slot is neither written here nor read by the epilogue
-    const bool any = !mask || __any_sync(FULL, valid && count > 0u);
-    if (any && valid) {
-      hi_out[(int64_t)f * M + i] = make_float4(hx, hy, hz, 0.f);
-      lo_out[(int64_t)f * M + i] = make_float4(lx, ly, lz, 0.f);
+    int64_t i[PL];
+    bool valid[PL];
+    float3 y[PL];
+    float h[PL][3], lo[PL][3];
+    unsigned cnt[PL];
+#pragma unroll
+    for (int q = 0; q < PL; ++q) {
+      i[q] = (int64_t)g * (32 * PL) + 32 * q + lane;
+      valid[q] = i[q] < M;
+      y[q] = place(xf, Y0[valid[q] ? i[q] : 0]);
+      h[q][0] = h[q][1] = h[q][2] = lo[q][0] = lo[q][1] = lo[q][2] = 0.f;
+      cnt[q] = 0u;
     }
-    if (mask && any && lane == 0) atomicOr(&mask[g], 1ull << f);
-    total += valid ? count : 0u;
+    unsigned steps = 0;
+    if constexpr (NP == 0)
+      bh_task(rec, bodies, front, f, y[0], valid[0], eps2, theta2, stk, h[0][0], h[0][1], h[0][2],
+              lo[0][0], lo[0][1], lo[0][2], cnt[0], steps);
+    else
+      bh_walk<NP>(rec, bodies, front, f, y, valid, eps2, theta2, h, lo, cnt, steps);
+    if (cost && lane == 0) cost[task] = steps + 1u;
+#pragma unroll
+    for (int q = 0; q < PL; ++q) {
+      // a 32-point slice in which no point added a term leaves exact zeros:
+      // with a mask its slot is neither written here nor read by the epilogue
+      const bool any = !mask || __any_sync(FULL, valid[q] && cnt[q] > 0u);
+      if (any && valid[q]) {
+        hi_out[(int64_t)f * M + i[q]] = make_float4(h[q][0], h[q][1], h[q][2], 0.f);
+        lo_out[(int64_t)f * M + i[q]] = make_float4(lo[q][0], lo[q][1], lo[q][2], 0.f);
+      }
+      if (mask && any && lane == 0) atomicOr(&mask[(size_t)PL * g + q], 1ull << f);
+      total += valid[q] ? cnt[q] : 0u;
+    }
   }
   for (int off = 16; off > 0; off >>= 1) total += __shfl_down_sync(FULL, total, off);
   if (lane == 0) {
@@ -239,29 +259,42 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
   }
 }
 
+template <int NP>
 static int bh_grid(int64_t M, int K) {
   static std::atomic<int> cached{0};
   int per_sm = cached.load();
   if (per_sm == 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bh, BH_WARPS * 32, 0) != cudaSuccess || b < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bh<NP>, BH_WARPS * 32, 0) != cudaSuccess || b < 1) {
       cudaGetLastError();
       b = 1;
     }
     per_sm = b;
     cached.store(b);
   }
-  const int64_t tasks = (M + 31) / 32 * K;
+  const int64_t tasks = bh_tasks(M, K, NP == 0 ? 1 : NP);
   const int64_t need = (tasks + BH_WARPS - 1) / BH_WARPS;
   return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)per_sm * sm_count()));
 }
 
+int bh_walk_kind(int64_t M, int walk) {
+  if (walk == FGA_WALK_LANE) return 0;
+  if (walk == FGA_WALK_COOP) return 2;
+  const int64_t warps = (int64_t)sm_count() * 32;
+  return M >= (int64_t)FGA_BH_COOP_POINTS_PER_WARP * warps ? 2 : 0;
+}
+
 int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, float eps,
-              float theta, ForceBuffers& fb, cudaStream_t s, const unsigned* order, unsigned* cost) {
-  k_bh<<<bh_grid(M, t->n_front), BH_WARPS * 32, 0, s>>>(t->node_rec, t->bodies, Y0, M, t->front,
-                                                        t->n_front, ds, eps * eps, theta * theta,
-                                                        fb.hi, fb.lo, order, cost,
-                                                        t->n_front <= 64 ? fb.mask : nullptr);
+              float theta, ForceBuffers& fb, cudaStream_t s, int kind, const unsigned* order, unsigned* cost) {
+  unsigned long long* mask = t->n_front <= 64 ? fb.mask : nullptr;
+  if (kind == 2)
+    k_bh<2><<<bh_grid<2>(M, t->n_front), BH_WARPS * 32, 0, s>>>(t->node_rec, t->bodies, Y0, M, t->front,
+                                                               t->n_front, ds, eps * eps, theta * theta,
+                                                               fb.hi, fb.lo, order, cost, mask);
+  else
+    k_bh<0><<<bh_grid<0>(M, t->n_front), BH_WARPS * 32, 0, s>>>(t->node_rec, t->bodies, Y0, M, t->front,
+                                                               t->n_front, ds, eps * eps, theta * theta,
+                                                               fb.hi, fb.lo, order, cost, mask);
   FGA_LAUNCH_CHECK("bh");
   fb.S = t->n_front;
   return FGA_OK;

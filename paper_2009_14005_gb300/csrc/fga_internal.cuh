@@ -195,14 +195,33 @@ void get_direct_tile(int size_class, int* bs, int* qpt);
 
 int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const DevState* ds,
                   float eps, const DirectPlan& plan, ForceBuffers& fb, cudaStream_t s);
-// order: heavy-first task order from launch_task_order, or null (task index
-// order); cost: where each task's step count is recorded, or null.
+// kind: the walk (bh_walk_kind); order: heavy-first
+// task order from launch_task_order, or null (task index order); cost: where
+// each task's step count is recorded, or null.
 int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, float eps,
-              float theta, ForceBuffers& fb, cudaStream_t s, const unsigned* order = nullptr,
+              float theta, ForceBuffers& fb, cudaStream_t s, int kind, const unsigned* order = nullptr,
               unsigned* cost = nullptr);
 // Heavy-first order of ntasks tasks from their recorded costs. `order` must
 // hold ntasks + TASK_ORDER_SCRATCH entries (the tail is the sort's scratch).
 constexpr unsigned TASK_ORDER_SCRATCH = 8192;
+
+// Barnes-Hut tasks are (group of 32 * pl template points, frontier cell),
+// pl points per lane (points g*32*pl + 32*q + lane, q < pl).
+// bh_walk_kind(M, walk): 0 for per-lane walks (pl = 1), 2 for the
+// cooperative walk with two points per lane (pl = 2); `walk` is
+// fga_params.bh_walk. The cooperative walk costs fewer instructions per point
+// but makes half as many tasks, each longer; FGA_WALK_AUTO takes it when the
+// template has at least FGA_BH_COOP_POINTS_PER_WARP points per resident warp,
+// so that the heaviest tasks (a group's own near field) still spread over
+// every warp.
+#ifndef FGA_BH_COOP_POINTS_PER_WARP
+#define FGA_BH_COOP_POINTS_PER_WARP 48
+#endif
+int bh_walk_kind(int64_t M, int walk);
+inline int bh_points_per_lane(int kind) { return kind == 0 ? 1 : kind; }
+__host__ __device__ inline unsigned bh_tasks(int64_t M, int K, int pl) {
+  return (unsigned)((M + 32 * pl - 1) / (32 * pl)) * (unsigned)K;
+}
 int launch_task_order(const unsigned* cost, unsigned ntasks, unsigned* order, cudaStream_t s);
 // Refreshed after the first two force launches and then every
 // FGA_BH_REORDER_EVERY launches (0: never, tasks run in index order).

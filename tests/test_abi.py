@@ -62,3 +62,20 @@ def test_errors_without_gpu_work(fga):
     code = fga.lib.fga_state_create(None, None, 0, None, None, 0, None, ctypes.byref(fga.params()),
                                     ctypes.byref(ctypes.c_void_p()), None)
     assert code == fga.FGA_EINVAL
+
+
+def test_params_struct_matches_the_header(fga):
+    # fga_params_default fills every field, the last one included
+    p = fga.params()
+    assert p.dim == 3 and p.bh_walk == fga.FGA_WALK_AUTO
+    assert ctypes.sizeof(fga.fga_params) == 4 * len(fga.fga_params._fields_)
+
+
+def test_bad_walk_is_rejected_without_gpu_work(fga):
+    X = np.zeros((8, 3), dtype=np.float32)
+    R, t = (ctypes.c_double * 9)(), (ctypes.c_double * 3)()
+    p = fga.params(bh_walk=7)
+    code = fga.lib.fga_register(X.ctypes.data, 8, X.ctypes.data, 8, None, None, ctypes.byref(p), R, t,
+                                None, None)
+    assert code == fga.FGA_EINVAL
+    assert "bh_walk" in fga.lib.fga_last_error().decode()

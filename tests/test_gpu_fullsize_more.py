@@ -7,6 +7,11 @@ can compute one by one.
 * Batch: the benchmark's 256-pair batch (N, M log-uniform in [500, 50k])
   registered in one call in the benchmark's launch configuration; pairs the
   oracle finishes in seconds are checked against the oracle's registration.
+* Grid: the 10^4-cell (G, eps, eta) sweep over one 1k-point box pair in one
+  batch; well-conditioned sampled cells against the oracle.
+* Serving: a 24-request Poisson trace (N, M log-uniform in [1k, 500k]) through
+  the server; every result against the one-pair path, the two cheapest
+  requests against the oracle.
 """
 import numpy as np
 import pytest
@@ -95,3 +100,76 @@ def test_full_batch_pairs_match_oracle(fga, orc):
         dt = float(np.linalg.norm(res[k]["t"] - o["t"])) / diag
         assert dphi <= 0.01 and dt <= 1e-4, (k, sizes[k], dphi, dt)
         assert res[k]["iterations"] == 100
+
+
+def test_full_grid_cells_match_oracle(fga, orc):
+    # the grid workload: a 1k-point box under 10^4 (G, eps, eta) cells in one batch
+    import bench
+    X, Y, R_gt, t_gt = synth.box_pair(0, n=1000, deg=30.0)
+    Xd, Yd = _cuda(X), _cuda(Y)
+    cells = bench.grid_cells(10_000)
+    ps = [fga.params(method=fga.FGA_DIRECT, G=float(g), eps=float(e), eta=float(h), max_iter=100)
+          for g, e, h in cells]
+    res, st = fga.fga_register_batch([(Xd, Yd, None, None, c) for c in ps],
+                                     fga.params(method=fga.FGA_DIRECT, max_iter=100))
+    assert len(res) == 10_000 and all(r["iterations"] == 100 for r in res)
+    assert st["interactions"] == 10_000 * 100 * 1000 * 1000
+    assert all(np.isfinite(r["R"]).all() and np.isfinite(r["t"]).all() for r in res)
+    import oracle
+    diag = float(np.linalg.norm(X.max(0) - X.min(0)))
+    # The stiff corner of the grid (large G, small eps) is chaotic: there a
+    # 1e-6 * diag nudge of Y moves the oracle's own result by degrees, so FP32
+    # and FP64 trajectories cannot agree. Compare the cells whose oracle result
+    # is stable under that nudge (about nine in ten).
+    Yp = Y + np.random.default_rng(9).normal(size=Y.shape) * 1e-6 * diag
+    rng = np.random.default_rng(3)
+    checked = 0
+    for k in rng.choice(len(cells), 12, replace=False):
+        g, e, h = cells[k]
+        po = orc.Params(method=orc.FGA_DIRECT, G=g, eps=e, eta=h, max_iter=100)
+        o = orc.register_full(X, Y, po)
+        o2 = orc.register_full(X, Yp, po)
+        if oracle.rotation_error_deg(o["R"], o2["R"]) > 1e-3 or np.linalg.norm(o["t"] - o2["t"]) > 1e-5 * diag:
+            continue
+        checked += 1
+        assert oracle.rotation_error_deg(res[k]["R"], o["R"]) <= 0.01, cells[k]
+        assert np.linalg.norm(res[k]["t"] - o["t"]) <= 1e-4 * diag, cells[k]
+    assert checked >= 8, checked
+
+
+def test_served_trace_matches_one_pair_path(fga, orc):
+    # the serve workload's request trace (sizes 1k-500k, overlap 30-100 %)
+    trace = synth.serve_trace(1000, 24, rate=200.0, lo=1000, hi=500_000)
+    p = fga.params(method=fga.FGA_AUTO, theta=0.5, max_iter=100, G=66.7, eps=0.2, eta=0.2)
+    old = fga.fga_direct_max_n(4096)
+    try:
+        dev = [(_cuda(X), _cuda(Y)) for _, X, Y, _, _ in trace]
+        with fga.Server(p, iters_per_tick=4) as srv:
+            tickets = {srv.submit(X, Y): k for k, (X, Y) in enumerate(dev)}
+            got = srv.drain()
+        alone = [fga.fga_register(X, Y, p) for X, Y in dev]
+    finally:
+        fga.fga_direct_max_n(old)
+    assert len(got) == len(trace)
+    import oracle
+    for r in got:
+        k = tickets[r["ticket"]]
+        X = trace[k][1]
+        diag = float(np.linalg.norm(X.max(0) - X.min(0)))
+        R1, t1, _ = alone[k]
+        assert r["status"] in (fga.FGA_OK, fga.FGA_EDEGENERATE)
+        assert r["iterations"] == alone[k][2]["iterations"]
+        assert r["method"] == (fga.FGA_DIRECT if len(X) <= 4096 else fga.FGA_BH)
+        assert oracle.rotation_error_deg(r["R"], R1) <= 0.01, (k, len(X))
+        assert np.linalg.norm(r["t"] - t1) <= 1e-4 * diag
+    # the smallest requests against the oracle
+    small = sorted(range(len(trace)), key=lambda k: len(trace[k][1]) * len(trace[k][2]))[:2]
+    for k in small:
+        _, X, Y, _, _ = trace[k]
+        method = orc.FGA_DIRECT if len(X) <= 4096 else orc.FGA_BH
+        o = orc.register_full(X, Y, orc.Params(method=method, theta=0.5, max_iter=100,
+                                               G=66.7, eps=0.2, eta=0.2))
+        r = next(r for r in got if tickets[r["ticket"]] == k)
+        diag = float(np.linalg.norm(X.max(0) - X.min(0)))
+        assert oracle.rotation_error_deg(r["R"], o["R"]) <= 0.01, (k, len(X), len(Y))
+        assert np.linalg.norm(r["t"] - o["t"]) <= 1e-4 * diag

@@ -127,12 +127,17 @@ def test_direct_forces_with_template_masses(fga, orc):
 
 # --------------------------------------------------------------------------- BHForce
 
+WALKS = {"lane": 1, "coop": 2}  # fga_params.bh_walk: per-point walks, one walk per 64 points
+
+
+@pytest.mark.parametrize("walk", list(WALKS))
 @pytest.mark.parametrize("theta", [0.0, 0.3, 0.5, 0.8])
-def test_bh_forces_match_oracle(fga, orc, theta):
+def test_bh_forces_match_oracle(fga, orc, theta, walk):
+    # 2000 template points: 31 full 64-point groups and a ragged 16-point tail
     X, Y, _, _ = synth.lidar_pair(4, n=20000, m=2000)
     Xn, Yn, _ = _norm_pair(orc, X, Y)
     mX = _f32(orc.masses_niv(Xn))
-    p = fga.params(theta=theta, eps=0.2)
+    p = fga.params(theta=theta, eps=0.2, bh_walk=WALKS[walk])
     tree_o = orc.Tree(Xn, mX)
     a_bo, c_o = tree_o.bh_acc(Yn, p.G, 0.2, theta)
     a_d = orc.direct_acc(Xn, mX, Yn, p.G, 0.2)
@@ -149,6 +154,26 @@ def test_bh_forces_match_oracle(fga, orc, theta):
     assert close.mean() > 0.99
     if theta == 0.0:
         assert cnt == len(Xn) * len(Yn)
+
+
+@pytest.mark.parametrize("m", [1, 31, 33, 64, 65, 1000])
+def test_bh_walks_take_the_same_terms(fga, orc, m):
+    # Both walks judge every (point, node) pair with the same FP32 arithmetic,
+    # in the same depth-first order: the term counts agree exactly, the
+    # forces up to the rounding of the compensated partial sums.
+    X, Y, _, _ = synth.lidar_pair(6, n=12000, m=max(m, 2))
+    Xn, Yn, _ = _norm_pair(orc, X, Y[:m])
+    mX = _f32(orc.masses_niv(Xn))
+    out = {}
+    for walk, code in WALKS.items():
+        p = fga.params(theta=0.5, eps=0.2, bh_walk=code)
+        t = fga.fga_tree_build(_cuda(Xn), _cuda(mX), p)
+        out[walk] = fga.fga_forces(t, None, None, _cuda(Yn), None, p, want_count=True)
+    (a1, c1), (a2, c2) = out["lane"], out["coop"]
+    assert c1 == c2
+    a1, a2 = a1.cpu().numpy().astype(np.float64), a2.cpu().numpy().astype(np.float64)
+    scale = np.linalg.norm(a1, axis=1).max()
+    np.testing.assert_allclose(a2, a1, rtol=0, atol=2e-6 * scale)
 
 
 # --------------------------------------------------------------------------- Algorithm 2
@@ -186,11 +211,13 @@ def test_register_box_recovers_ground_truth_and_matches(fga, orc, vm):
     assert gphi < 0.01 and gt < 1e-4
 
 
-def test_register_bh_lidar_matches_oracle(fga, orc):
+@pytest.mark.parametrize("walk", list(WALKS))
+def test_register_bh_lidar_matches_oracle(fga, orc, walk):
     X, Y, _, _ = synth.lidar_pair(5, n=6000)
     po = orc.Params(method=orc.FGA_BH, theta=0.5, max_iter=200, niv_masses=True)
     o = orc.register_full(X, Y, po)
-    p = fga.params(method=fga.FGA_BH, theta=0.5, max_iter=200, mass_mode=fga.FGA_MASS_NIV)
+    p = fga.params(method=fga.FGA_BH, theta=0.5, max_iter=200, mass_mode=fga.FGA_MASS_NIV,
+                   bh_walk=WALKS[walk])
     R, t, st = fga.fga_register(_cuda(X), _cuda(Y), p)
     dphi, dt = _gt_errors(R, t, o["R"], o["t"], X)
     assert dphi <= 0.01 and dt <= 1e-4, (dphi, dt)
