@@ -209,6 +209,17 @@ int64_t fga_tree_node_count(const fga_tree* t);
 int64_t fga_tree_export(const fga_tree* t, int64_t cap, int64_t* ints, double* dbls,
                         int64_t* leaf_of, void* stream);
 
+/* Host copy of the records the per-point BHForce walk (Algorithm 2) reads:
+ * the tree in depth-first pre-order, children in octant order, 8 floats per
+ * record: CoM x, y, z, mass, l^2 (-1 for a single-particle leaf), then as
+ * int32 bits the record count of the subtree (the walk's skip), the child
+ * count (> 0), -1 for a single-particle leaf or -nb for a leaf with nb >= 2
+ * particles, and that leaf's first particle (Morton order). A leaf with
+ * nb >= 2 particles is followed by nb single-particle records, one per
+ * particle. out: host, cap x 8 floats. Synchronises `stream`. Returns the
+ * record count or an FGA_E* code; cap = 0 returns the count only. */
+int64_t fga_tree_preorder(const fga_tree* t, int64_t cap, float* out, void* stream);
+
 /* ----------------------------------------------------------------- Sec. IV-C/E */
 /* Gravitational force on every template point, Eq. 6:
  *   F_i = G m_Yi sum_j m_Xj (X_j - Y_i) / (|X_j - Y_i|^2 + eps^2)^(3/2),

@@ -54,7 +54,7 @@ FGA_MAX_LANDMARKS = 512
 SYMBOLS = [
     "fga_params_default", "fga_last_error", "fga_launch_count", "fga_normalize",
     "fga_denormalize", "fga_masses", "fga_tree_build", "fga_tree_destroy",
-    "fga_tree_node_count", "fga_tree_export", "fga_forces", "fga_state_create", "fga_step",
+    "fga_tree_node_count", "fga_tree_export", "fga_tree_preorder", "fga_forces", "fga_state_create", "fga_step",
     "fga_state_get", "fga_state_trajectory", "fga_state_destroy", "fga_register",
     "fga_forces_direct_static", "fga_register_batch", "fga_direct_max_n",
     "fga_server_create", "fga_server_submit", "fga_server_poll", "fga_server_stats_get",
@@ -177,6 +177,7 @@ def _load():
         "fga_tree_destroy": (None, [P]),
         "fga_tree_node_count": (I64, [P]),
         "fga_tree_export": (I64, [P, I64, P, P, P, VP]),
+        "fga_tree_preorder": (I64, [P, I64, P, VP]),
         "fga_forces": (ctypes.c_int, [P, P, P, I64, P, P, I64, PP, P, ctypes.POINTER(I64), VP]),
         "fga_state_create": (ctypes.c_int, [P, P, I64, P, P, I64, P, PP,
                                             ctypes.POINTER(ctypes.c_void_p), VP]),
@@ -353,6 +354,20 @@ class Tree:
         return dict(depth=ints[:, 0], cell=ints[:, 1:4], npts=ints[:, 4], is_leaf=ints[:, 5] != 0,
                     parent=ints[:, 6], mass=dbls[:, 0], com=dbls[:, 1:4], l=dbls[:, 4],
                     leaf_of=leaf_of)
+
+    def preorder(self, stream=None):
+        """The walk's depth-first records: dict of com (n x 3), mass, l2 and the
+        int fields size (subtree record count), count, first."""
+        n = int(lib.fga_tree_preorder(self._h, 0, None, _stream(stream)))
+        if n < 0:
+            _err(n)
+        rec = np.zeros((n, 8), dtype=np.float32)
+        got = lib.fga_tree_preorder(self._h, n, rec.ctypes.data_as(ctypes.c_void_p), _stream(stream))
+        if got < 0:
+            _err(int(got))
+        bits = rec.view(np.int32)
+        return dict(com=rec[:, 0:3], mass=rec[:, 3], l2=rec[:, 4], size=bits[:, 5].copy(),
+                    count=bits[:, 6].copy(), first=bits[:, 7].copy())
 
     def close(self):
         if self._h:

@@ -5,8 +5,8 @@
 // Force launch: the warp tasks of all pairs are numbered consecutively, pair
 // by pair (a prefix sum over the pairs maps a task to its pair by binary
 // search); warps take tasks from a device counter. A Barnes-Hut task is (pair,
-// 64 template points, frontier cell) and runs the same cooperative BHForce
-// walk as the single-pair kernel. An all-pairs task is (pair, 64 template
+// 32 template points, frontier cell) and runs the same per-lane BHForce walk
+// over depth-first records as the single-pair kernel. An all-pairs task is (pair, 64 template
 // points, chunk of up to BATCH_CHUNK reference points): the warp stages 32
 // sources at a time in shared memory and every lane adds them to its two
 // points (Eq. 6).
@@ -72,29 +72,19 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch
     const unsigned f = local - grp * (unsigned)P.K;
     const Xf xf = load_xf(ds);
     if (P.method == FGA_BH) {
-      // 32 * BATCH_BH_NP template points against frontier cell f (one walk for all)
-      int64_t i[BATCH_BH_NP];
-      bool valid[BATCH_BH_NP];
-      float3 y[BATCH_BH_NP];
-#pragma unroll
-      for (int q = 0; q < BATCH_BH_NP; ++q) {
-        i[q] = (int64_t)grp * (32 * BATCH_BH_NP) + 32 * q + lane;
-        valid[q] = i[q] < M;
-        y[q] = place(xf, P.Y0[valid[q] ? i[q] : 0]);
-      }
-      float h[BATCH_BH_NP][3] = {}, lo[BATCH_BH_NP][3] = {};
-      unsigned cnt[BATCH_BH_NP] = {}, steps = 0;
-      bh_walk<BATCH_BH_NP>(P.rec, P.bodies, P.front, f, y, valid, eps2, theta2, h, lo, cnt, steps);
+      // 32 template points, one per lane, against frontier cell f
+      const int64_t i = (int64_t)grp * BATCH_BH_GROUP + lane;
+      const bool valid = i < M;
+      const float3 y = place(xf, P.Y0[valid ? i : 0]);
+      float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
+      unsigned count = 0, steps = 0;
+      bh_task_pre(P.pre, P.front, f, y, valid, eps2, theta2, hx, hy, hz, lx, ly, lz, count, steps);
       if (cost && lane == 0) cost[task] = steps + 1u;
-      unsigned long long c = 0;
-#pragma unroll
-      for (int q = 0; q < BATCH_BH_NP; ++q) {
-        if (valid[q]) {
-          P.hi[(int64_t)f * M + i[q]] = make_float4(h[q][0], h[q][1], h[q][2], 0.f);
-          P.lo[(int64_t)f * M + i[q]] = make_float4(lo[q][0], lo[q][1], lo[q][2], 0.f);
-          c += cnt[q];
-        }
+      if (valid) {
+        P.hi[(int64_t)f * M + i] = make_float4(hx, hy, hz, 0.f);
+        P.lo[(int64_t)f * M + i] = make_float4(lx, ly, lz, 0.f);
       }
+      unsigned long long c = valid ? count : 0u;
       for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(FULL, c, off);
       if (lane == 0 && c) atomicAdd(&ds->interactions, c);
     } else {
@@ -260,9 +250,11 @@ int64_t pair_bytes_bound(int64_t N, int64_t M, int method, const fga_params* p) 
   int64_t prep = 2 * (12 * (N + M)) + 4 * (N + M) + 8 * pad;
   int64_t keep = 3 * f4 * M + 8 * (int64_t)epilogue_blocks(M) * NRED + (int64_t)sizeof(DevState) + 8 * pad;
   if (method == FGA_BH) {
-    // tree: bodies, index, keys, node arrays (<= 2N nodes), records, sort scratch
+    // tree: bodies, index, keys, node arrays (<= 2N nodes: CoM, info, body
+    // range, subtree size and position), depth-first records (<= 2N cells plus
+    // <= N particle records), sort scratch
     const int64_t nodes = 2 * N + 64;
-    int64_t tree = f4 * N + 4 * N + 8 * N + nodes * (f4 + 16 + 2 * f4) + 2 * 16 * N +
+    int64_t tree = f4 * N + 4 * N + 8 * N + nodes * (f4 + 16 + 8 + 8) + 2 * f4 * (nodes + N) + 2 * 16 * N +
                    (int64_t)batch_front_target(N) * (int64_t)sizeof(FrontCell) + 32 * pad;
     keep += tree + 4 * M + 2 * f4 * (int64_t)batch_front_target(N) * M;
   } else {
@@ -290,8 +282,7 @@ int build_inputs(const fga_pair& q, const Prepared& pr, const fga_params* p, Scr
     int* perm = nullptr;
     if (sc.alloc(&perm, q.M)) return FGA_ENOMEM;
     if ((rc = pack_template(pr.Yn, pr.mYn, p->dt, q.M, true, Y0, perm, s))) return rc;
-    P.rec = t->node_rec;
-    P.bodies = t->bodies;
+    P.pre = t->node_pre;
     P.front = t->front;
     P.K = t->n_front;
   } else {
@@ -368,7 +359,7 @@ bool batch_layout(const std::vector<PairDev>& pairs, std::vector<unsigned>& task
   block_start.assign(pairs.size() + 1, 0u);
   int64_t nt = 0, nb = 0;
   for (size_t k = 0; k < pairs.size(); ++k) {
-    const int64_t gs = pairs[k].method == FGA_BH ? 32 * BATCH_BH_NP : 64;  // template points per task
+    const int64_t gs = pairs[k].method == FGA_BH ? BATCH_BH_GROUP : 64;  // template points per task
     nt += (pairs[k].M + gs - 1) / gs * (int64_t)pairs[k].K;
     nb += pairs[k].nblk;
     if (nt >= ((int64_t)1 << 31) || nb >= ((int64_t)1 << 31)) return false;

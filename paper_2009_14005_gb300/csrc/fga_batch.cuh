@@ -10,16 +10,15 @@
 namespace fga {
 
 constexpr int BATCH_CHUNK = 2048;  // reference points per all-pairs task
-constexpr int BATCH_BH_NP = 2;     // template points per lane of a Barnes-Hut task
+constexpr int BATCH_BH_GROUP = 32;  // template points per Barnes-Hut task (one per lane)
 constexpr int BATCH_WARPS = 4;
 
 // Everything the two batch kernels need about one pair, in device memory.
 struct PairDev {
   int method;                 // FGA_DIRECT or FGA_BH
   int K;                      // BH: frontier cells; direct: source chunks
-  const float4* rec;          // BH: interleaved cell records
-  const float4* bodies;       // BH: bodies in Morton order
-  const FrontCell* front;     // BH: frontier
+  const float4* pre;          // BH: depth-first cell records
+  const FrontCell* front;     // BH: frontier (record indices)
   const float4* X4;           // direct: reference points and masses
   int64_t N, M;
   const float4* Y0;           // template points and masses
@@ -52,7 +51,7 @@ int build_state(const fga_params* p, const double* mu0, Scratch& keep, DevState*
 
 // Work layout of a batch of pairs (in the order of `pairs`): pair k owns warp
 // tasks task_start[k] .. task_start[k+1]-1 (task = group * K + f: a group of
-// 64 template points and frontier cell f for Barnes-Hut, of 64 points and
+// 32 template points and frontier cell f for Barnes-Hut, of 64 points and
 // reference chunk f for the all-pairs sum) and epilogue blocks
 // block_start[k] .. block_start[k+1]-1. Both arrays get pairs.size() + 1
 // entries. Returns false if a count exceeds 2^31.

@@ -355,27 +355,32 @@ static __device__ void rigid_step(const double* red, int64_t M, DevState* ds, co
 }
 
 
-// ------------------------------------------------------------------ BHForce walk of one task
-// Per-lane BHForce of Algorithm 2 for template point y, restricted to frontier
-// cell f: the cell's ancestors first (a lane accepting one stops; the
-// monopole is added only when f owns the ancestor's first frontier cell),
-// then the depth-first walk of f's subtree with pending sibling ranges in
-// shared memory (stk: this lane's column, stride 32, depth bh_depth).
-// Adds into the compensated accumulators (hx, lx), ... and the term count;
-// `steps` gains the number of warp-wide walk steps (the task's cost).
-// A lane with valid == false takes part in the warp-wide loop but adds nothing.
-// Saved ranges per lane. A walk saves at most one range per tree level it
-// descends below the frontier cell, and the tree has at most 21 levels (depth
-// 0..20: 20-bit keys per axis, max_depth <= 20), so at most 20 ranges are ever
-// saved; the min() in the walk only keeps every index provably in bounds.
+// ------------------------------------------------------------------ BHForce walks of one task
+// Saved sibling ranges of the cooperative walk. A walk saves at most one
+// range per tree level it descends below the frontier cell, and the tree has
+// at most 21 levels (depth 0..20: 20-bit keys per axis, max_depth <= 20), so
+// at most 20 ranges are ever saved.
 constexpr int BH_DEPTH = 24;
-static_assert(BH_DEPTH > 20, "the BH walk stack must hold one range per tree level");
+static_assert(BH_DEPTH > 20, "the BH walk must hold one saved range per tree level");
 
-__device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const float4* __restrict__ bodies,
-                                        const FrontCell* __restrict__ front, unsigned f, float3 y,
-                                        bool valid, float eps2, float theta2, unsigned* stk,
-                                        float& hx, float& hy, float& hz, float& lx,
-                                        float& ly, float& lz, unsigned& count, unsigned& steps) {
+// Per-lane BHForce of Algorithm 2 for template point y, restricted to
+// frontier cell f, over the depth-first (pre-order) records: the cell's
+// ancestors first (a lane accepting one stops; the monopole is added only
+// when f owns the ancestor's first frontier cell), then the records
+// [front[f].node, front[f].end) of f's subtree. Pre-order needs no stack: a
+// record whose cell the point accepts adds its monopole and the walk skips
+// its subtree (the next record is `size` further on); a rejected cell's
+// first child is the next record. Single-particle records carry l^2 = -1 and
+// are always accepted; a leaf holding several particles is followed by one
+// record per particle, so rejecting it adds each particle exactly. Terms are
+// added in the depth-first order of the per-point walk.
+// Adds into the compensated accumulators (hx, lx), ... and the term count;
+// `steps` is the warp's longest walk (the task's cost). A lane with
+// valid == false adds nothing.
+__device__ __forceinline__ void bh_task_pre(const float4* __restrict__ pre, const FrontCell* __restrict__ front,
+                                            unsigned f, float3 y, bool valid, float eps2, float theta2,
+                                            float& hx, float& hy, float& hz, float& lx, float& ly,
+                                            float& lz, unsigned& count, unsigned& steps) {
   float px = 0.f, py = 0.f, pz = 0.f;
   bool live = valid;
   {
@@ -383,8 +388,8 @@ __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const fl
     const unsigned first_mask = front[f].first_mask;
     for (int j = 0; j < npath; ++j) {
       const int a = front[f].path[j];
-      const float4 cm = rec[2 * a];
-      const float l2 = rec[2 * a + 1].x;
+      const float4 cm = pre[2 * a];
+      const float l2 = pre[2 * a + 1].x;
       const float dx = cm.x - y.x, dy = cm.y - y.y, dz = cm.z - y.z;
       const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       const bool accept = live && l2 < theta2 * d2;
@@ -399,57 +404,23 @@ __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const fl
       live = live && !accept;
     }
   }
-  // per-lane walk of the frontier cell's subtree. The current sibling range is
-  // one word, e = next cell << 4 | cells left (at most 8), so advancing is
-  // e += 15; saved ranges use the same form.
-  unsigned e = live ? (((unsigned)front[f].node << 4) | 1u) : 0u;
-  int sp = 0;  // saved ranges in shared memory
-  while (__any_sync(FULL, (e & 15u) != 0u)) {
-    ++steps;
-    if ((e & 15u) != 0u) {
-      const int v = (int)(e >> 4);
-      e += 15u;
-      const float4 cm = rec[2 * v];
-      const float4 ri = rec[2 * v + 1];
-      const int nchild = __float_as_int(ri.z);
-      const float dx = cm.x - y.x, dy = cm.y - y.y, dz = cm.z - y.z;
-      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      // single-particle leaves carry l^2 = -1 in the traversal record, so the
-      // test accepts them (one exact term) without a separate leaf check
-      const bool accept = ri.x < theta2 * d2;
-      const float inv = rsqrt_fast(d2 + eps2);
-      const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
-      px = fmaf(wgt, dx, px);
-      py = fmaf(wgt, dy, py);
-      pz = fmaf(wgt, dz, pz);
-      count += accept;
-      // descend into an internal cell that fails the test: save the rest of
-      // the current range, continue with the children (branch-free)
-      const bool descend = !accept && nchild > 0;
-      const bool save = descend && (e & 15u) != 0u;
-      if (save) stk[32 * min(sp, BH_DEPTH - 1)] = e;
-      sp += save;
-      e = descend ? (((unsigned)__float_as_int(ri.y) << 4) | (unsigned)nchild) : e;
-      if (!accept && nchild < -1) {
-        // leaf holding several particles: add each exactly (rare)
-        const int b0 = __float_as_int(ri.y), nb = -nchild;
-        for (int b = 0; b < nb; ++b) {
-          const float4 q = bodies[b0 + b];
-          const float ex = q.x - y.x, ey = q.y - y.y, ez = q.z - y.z;
-          const float iq = rsqrt_fast(fmaf(ex, ex, fmaf(ey, ey, fmaf(ez, ez, eps2))));
-          const float wq = q.w * (iq * iq * iq);
-          px = fmaf(wq, ex, px);
-          py = fmaf(wq, ey, py);
-          pz = fmaf(wq, ez, pz);
-        }
-        count += (unsigned)nb;
-      }
-      // range exhausted: resume the innermost saved range
-      const bool pop = (e & 15u) == 0u && sp > 0;
-      sp -= pop;
-      e = pop ? stk[32 * min(sp, BH_DEPTH - 1)] : e;
-    }
-    if ((steps & 31u) == 0u) {
+  const int end = front[f].end;
+  int v = live ? front[f].node : end;
+  unsigned n = 0;
+  while (v < end) {
+    const float4 cm = pre[2 * v];
+    const float4 ri = pre[2 * v + 1];
+    const float dx = cm.x - y.x, dy = cm.y - y.y, dz = cm.z - y.z;
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const bool accept = ri.x < theta2 * d2;
+    const float inv = rsqrt_fast(d2 + eps2);
+    const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
+    px = fmaf(wgt, dx, px);
+    py = fmaf(wgt, dy, py);
+    pz = fmaf(wgt, dz, pz);
+    count += accept;
+    v += accept ? __float_as_int(ri.y) : 1;
+    if ((++n & 31u) == 0u) {
       comp_add(hx, lx, px);
       comp_add(hy, ly, py);
       comp_add(hz, lz, pz);
@@ -459,6 +430,7 @@ __device__ __forceinline__ void bh_task(const float4* __restrict__ rec, const fl
   comp_add(hx, lx, px);
   comp_add(hy, ly, py);
   comp_add(hz, lz, pz);
+  steps += __reduce_max_sync(FULL, n);
 }
 
 // The saved ranges of the cooperative walk are spread over the warp's lanes
@@ -480,9 +452,8 @@ static_assert(BH_DEPTH <= 32, "one saved range per lane");
 // term counts cnt[q]; `steps` gains the number of nodes visited (the task's
 // cost).
 template <int NP>
-__device__ __forceinline__ void bh_walk(const float4* __restrict__ rec, const float4* __restrict__ bodies,
-                                        const FrontCell* __restrict__ front, unsigned f,
-                                        const float3 (&y)[NP], const bool (&valid)[NP], float eps2,
+__device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const FrontCell* __restrict__ front,
+                                        unsigned f, const float3 (&y)[NP], const bool (&valid)[NP], float eps2,
                                         float theta2, float (&h)[NP][3], float (&l)[NP][3],
                                         unsigned (&cnt)[NP], unsigned& steps) {
   const int lane = threadIdx.x & 31;
@@ -499,8 +470,8 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ rec, const fl
     const unsigned first_mask = front[f].first_mask;
     for (int j = 0; j < npath; ++j) {
       const int a = front[f].path[j];
-      const float4 cm = rec[2 * a];
-      const float l2 = rec[2 * a + 1].x;
+      const float4 cm = pre[2 * a];
+      const float l2 = pre[2 * a + 1].x;
       const bool own = (first_mask >> j) & 1u;
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
@@ -526,18 +497,18 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ rec, const fl
     sm[q] = 0u;
     any |= m[q];
   }
-  // current sibling range e = next cell << 4 | cells left; saved ranges and
-  // their masks: entry k in lane k's se, sm[]
+  // current sibling range e = next record << 4 | cells left (siblings are a
+  // subtree size apart); saved ranges and their masks: entry k in lane k's se, sm[]
   unsigned e = any != 0u ? (((unsigned)front[f].node << 4) | 1u) : 0u;
   unsigned se = 0u;
   int sp = 0;
   while ((e & 15u) != 0u) {
     ++steps;
     const int v = (int)(e >> 4);
-    e += 15u;
-    const float4 cm = rec[2 * v];
-    const float4 ri = rec[2 * v + 1];
+    const float4 cm = pre[2 * v];
+    const float4 ri = pre[2 * v + 1];
     const int nchild = __float_as_int(ri.z);
+    e += ((unsigned)__float_as_int(ri.y) << 4) - 1u;  // next sibling
     bool rej[NP];
     unsigned r[NP], rany = 0u;
 #pragma unroll
@@ -545,7 +516,7 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ rec, const fl
       const bool act = (m[q] & bit) != 0u;
       const float dx = cm.x - y[q].x, dy = cm.y - y[q].y, dz = cm.z - y[q].z;
       const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      // single-particle leaves carry l^2 = -1: always accepted (one exact term)
+      // single-particle records carry l^2 = -1: always accepted (one exact term)
       const bool accept = act && ri.x < theta2 * d2;
       const float inv = rsqrt_fast(d2 + eps2);
       const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
@@ -560,7 +531,8 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ rec, const fl
     if (rany != 0u) {
       if (nchild > 0) {
         // descend: save the rest of the current range, continue with the
-        // children, judged by the points that rejected this cell
+        // children (the first follows its parent), judged by the points that
+        // rejected this cell
         if ((e & 15u) != 0u) {
           if (lane == sp) {
             se = e;
@@ -569,14 +541,15 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ rec, const fl
           }
           ++sp;
         }
-        e = ((unsigned)__float_as_int(ri.y) << 4) | (unsigned)nchild;
+        e = ((unsigned)(v + 1) << 4) | (unsigned)nchild;
 #pragma unroll
         for (int q = 0; q < NP; ++q) m[q] = r[q];
       } else if (nchild < -1) {
-        // leaf holding several particles, rejected by these points: add each exactly (rare)
-        const int b0 = __float_as_int(ri.y), nb = -nchild;
-        for (int b = 0; b < nb; ++b) {
-          const float4 qb = bodies[b0 + b];
+        // leaf holding several particles, rejected by these points: each
+        // particle exactly, from the single-particle records that follow it (rare)
+        const int nb = -nchild;
+        for (int b = 1; b <= nb; ++b) {
+          const float4 qb = pre[2 * (v + b)];
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
             const float ex = qb.x - y[q].x, ey = qb.y - y[q].y, ez = qb.z - y[q].z;

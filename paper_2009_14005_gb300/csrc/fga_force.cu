@@ -183,11 +183,11 @@ static constexpr int BH_WARPS = FGA_BH_WARPS;
 #ifndef FGA_BH_MINBLOCKS
 #define FGA_BH_MINBLOCKS 8  // resident blocks per SM the register budget is sized for
 #endif
-// NP = 0: one template point per lane, each lane walking its own point
-// (bh_task); NP > 0: NP points per lane, one walk for the warp (bh_walk).
+// NP = 0: one template point per lane, each lane walking its own point over
+// the depth-first records (bh_task_pre); NP > 0: NP points per lane, one
+// walk for the warp (bh_walk).
 template <int NP>
-__global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const float4* __restrict__ rec,
-                                                         const float4* __restrict__ bodies,
+__global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const float4* __restrict__ pre,
                                                          const float4* __restrict__ Y0, int64_t M,
                                                          const FrontCell* __restrict__ front, int K,
                                                          DevState* __restrict__ ds, float eps2,
@@ -199,8 +199,6 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
   constexpr int PL = NP == 0 ? 1 : NP;  // template points per lane
   if (ds->done) return;
   const int lane = threadIdx.x & 31;
-  __shared__ unsigned s_stack[NP == 0 ? BH_WARPS : 1][NP == 0 ? BH_DEPTH : 1][32];
-  unsigned* const stk = &s_stack[NP == 0 ? threadIdx.x >> 5 : 0][0][lane];
   const Xf xf = load_xf(ds);
   const unsigned ntasks = bh_tasks(M, K, PL);
   unsigned long long total = 0;
@@ -227,10 +225,10 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
     }
     unsigned steps = 0;
     if constexpr (NP == 0)
-      bh_task(rec, bodies, front, f, y[0], valid[0], eps2, theta2, stk, h[0][0], h[0][1], h[0][2],
-              lo[0][0], lo[0][1], lo[0][2], cnt[0], steps);
+      bh_task_pre(pre, front, f, y[0], valid[0], eps2, theta2, h[0][0], h[0][1], h[0][2],
+                  lo[0][0], lo[0][1], lo[0][2], cnt[0], steps);
     else
-      bh_walk<NP>(rec, bodies, front, f, y, valid, eps2, theta2, h, lo, cnt, steps);
+      bh_walk<NP>(pre, front, f, y, valid, eps2, theta2, h, lo, cnt, steps);
     if (cost && lane == 0) cost[task] = steps + 1u;
 #pragma unroll
     for (int q = 0; q < PL; ++q) {
@@ -288,12 +286,10 @@ int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, floa
               float theta, ForceBuffers& fb, cudaStream_t s, int kind, const unsigned* order, unsigned* cost) {
   unsigned long long* mask = t->n_front <= 64 ? fb.mask : nullptr;
   if (kind == 2)
-    k_bh<2><<<bh_grid<2>(M, t->n_front), BH_WARPS * 32, 0, s>>>(t->node_rec, t->bodies, Y0, M, t->front,
-                                                               t->n_front, ds, eps * eps, theta * theta,
+    k_bh<2><<<bh_grid<2>(M, t->n_front), BH_WARPS * 32, 0, s>>>(t->node_pre, Y0, M, t->front, t->n_front, ds, eps * eps, theta * theta,
                                                                fb.hi, fb.lo, order, cost, mask);
   else
-    k_bh<0><<<bh_grid<0>(M, t->n_front), BH_WARPS * 32, 0, s>>>(t->node_rec, t->bodies, Y0, M, t->front,
-                                                               t->n_front, ds, eps * eps, theta * theta,
+    k_bh<0><<<bh_grid<0>(M, t->n_front), BH_WARPS * 32, 0, s>>>(t->node_pre, Y0, M, t->front, t->n_front, ds, eps * eps, theta * theta,
                                                                fb.hi, fb.lo, order, cost, mask);
   FGA_LAUNCH_CHECK("bh");
   fb.S = t->n_front;

@@ -84,17 +84,19 @@ constexpr int NRED = 27;
 // ------------------------------------------------------------------ tree
 // A frontier cell of the tree: the cells of the frontier partition the tree
 // (every leaf lies under exactly one of them). BH work for a group of template
-// points is split into one task per frontier cell. path[] lists the cell's
-// ancestors from the root; bit j of first_mask is set when this cell is the
-// first frontier cell (in depth-first order) under path[j], i.e. the task that
-// adds path[j]'s monopole for lanes that accept it.
+// points is split into one task per frontier cell. In the depth-first records
+// (fga_tree::node_pre) the cell is record `node` and its subtree the records
+// [node, end); path[] lists the cell's ancestors from the root (record
+// indices); bit j of first_mask is set when this cell is the first frontier
+// cell (in depth-first order) under path[j], i.e. the task that adds
+// path[j]'s monopole for lanes that accept it.
 constexpr int FRONT_MAX_PATH = 27;
 struct FrontCell {
   int node;
   int npath;
   unsigned first_mask;
   int path[FRONT_MAX_PATH];
-  int pad;
+  int end;
 };
 #ifndef FGA_FRONT_TARGET
 #define FGA_FRONT_TARGET 64
@@ -129,8 +131,12 @@ struct fga_tree {
                                  //  count < 0: leaf, bodies first .. first-count-1
   int2* node_bodies = nullptr;   // n_nodes: body range [x, y) of the cell
   fga::FrontCell* front = nullptr;  // frontier cells (device), depth-first order
-  float4* node_rec = nullptr;    // n_nodes x 2 float4: (CoM, mass), (info as int bits),
-                                 // one 32-byte record per cell for the traversal
+  float4* node_pre = nullptr;    // n_pre x 2 float4, the tree in depth-first pre-order
+                                 // (children in octant order): (CoM, mass), (l^2, subtree
+                                 // size, count as in node_info, first body of a leaf) as
+                                 // int bits; a leaf with nb >= 2 particles is followed by
+                                 // nb single-particle records, one per particle
+  int64_t n_pre = 0;
   int n_front = 0;
   float box_lo[3], box_hi[3];    // root box (tight bounding box of X)
   cudaStream_t stream = nullptr; // stream the buffers were allocated on
@@ -215,7 +221,7 @@ constexpr unsigned TASK_ORDER_SCRATCH = 8192;
 // so that the heaviest tasks (a group's own near field) still spread over
 // every warp.
 #ifndef FGA_BH_COOP_POINTS_PER_WARP
-#define FGA_BH_COOP_POINTS_PER_WARP 48
+#define FGA_BH_COOP_POINTS_PER_WARP 96
 #endif
 int bh_walk_kind(int64_t M, int walk);
 inline int bh_points_per_lane(int kind) { return kind == 0 ? 1 : kind; }

@@ -150,17 +150,22 @@ __global__ void k_build_level(int L, int D, int cap, const unsigned long long* _
 }
 
 // Bottom-up: FP64 sums of mass and mass-weighted position (and plain position
-// sums for massless cells) from bodies (leaves) or children (internal cells).
+// sums for massless cells) from bodies (leaves) or children (internal cells),
+// and the number of pre-order records of each subtree (a leaf with nb >= 2
+// particles takes 1 + nb records, see k_interleave_pre).
 __global__ void k_mass_level(int L, const LevelInfo* __restrict__ lv, const float4* __restrict__ bodies,
                              const int4* __restrict__ node_info, Sum4* __restrict__ sum_m,
-                             Sum4* __restrict__ sum_p, float4* __restrict__ node_cm) {
+                             Sum4* __restrict__ sum_p, float4* __restrict__ node_cm,
+                             int* __restrict__ node_size) {
   if (lv->overflow) return;
   const int start = lv->start[L], cnt = lv->count[L];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
     const int v = start + t;
     const int4 inf = node_info[v];
     Sum4 a = {0, 0, 0, 0}, p = {0, 0, 0, 0};
+    int size = 1;
     if (inf.z < 0) {
+      size = inf.z < -1 ? 1 - inf.z : 1;
       for (int b = inf.y; b < inf.y - inf.z; ++b) {
         const float4 q = bodies[b];
         a.x += (double)q.w * q.x;
@@ -177,8 +182,10 @@ __global__ void k_mass_level(int L, const LevelInfo* __restrict__ lv, const floa
         const Sum4 ca = sum_m[c], cp = sum_p[c];
         a.x += ca.x; a.y += ca.y; a.z += ca.z; a.w += ca.w;
         p.x += cp.x; p.y += cp.y; p.z += cp.z; p.w += cp.w;
+        size += node_size[c];
       }
     }
+    node_size[v] = size;
     sum_m[v] = a;
     sum_p[v] = p;
     node_cm[v] = a.w > 0 ? make_float4((float)(a.x / a.w), (float)(a.y / a.w), (float)(a.z / a.w), (float)a.w)
@@ -186,16 +193,38 @@ __global__ void k_mass_level(int L, const LevelInfo* __restrict__ lv, const floa
   }
 }
 
+// Top-down: depth-first pre-order record index of every cell. A cell's first
+// child follows it directly; each further child follows its previous
+// sibling's subtree. pos[0] = 0 (the root) is set before the first level.
+__global__ void k_preorder_level(int L, const LevelInfo* __restrict__ lv, const int4* __restrict__ node_info,
+                                 const int* __restrict__ node_size, int* __restrict__ node_pos) {
+  if (lv->overflow) return;
+  const int start = lv->start[L], cnt = lv->count[L];
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < cnt; t += gridDim.x * blockDim.x) {
+    const int v = start + t;
+    const int4 inf = node_info[v];
+    if (inf.z <= 0) continue;
+    int run = node_pos[v] + 1;
+    for (int c = inf.y; c < inf.y + inf.z; ++c) {
+      node_pos[c] = run;
+      run += node_size[c];
+    }
+  }
+}
+
 // Frontier for splitting BH work (see FrontCell): starting from the root,
 // repeatedly replace the frontier cell holding the most bodies by its
 // children, until about `target` cells (never more) or only
 // leaves remain. Uses the first levels of the breadth-first node arrays.
-static int build_frontier(fga_tree* T, int target, cudaStream_t s) {
+static int build_frontier(fga_tree* T, int target, const int* d_pos, const int* d_size, cudaStream_t s) {
   const int64_t P = std::min<int64_t>(T->n_nodes, 1 << 16);
   std::vector<int4> info(P);
   std::vector<int2> nb(P);
+  std::vector<int> pos(P), size(P);
   FGA_CUDA_TRY(cudaMemcpyAsync(info.data(), T->node_info, sizeof(int4) * P, cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaMemcpyAsync(nb.data(), T->node_bodies, sizeof(int2) * P, cudaMemcpyDeviceToHost, s));
+  FGA_CUDA_TRY(cudaMemcpyAsync(pos.data(), d_pos, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+  FGA_CUDA_TRY(cudaMemcpyAsync(size.data(), d_size, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaStreamSynchronize(s));
   struct Item {
     int node;
@@ -225,15 +254,20 @@ static int build_frontier(fga_tree* T, int target, cudaStream_t s) {
   }
   std::sort(front.begin(), front.end(),
             [&](const Item& a, const Item& b) { return nb[a.node].x < nb[b.node].x; });
+  // in depth-first record indices (pos, size: pre-order index and record count
+  // of each cell's subtree)
   std::vector<FrontCell> table(front.size());
   for (size_t k = 0; k < front.size(); ++k) {
     FrontCell& fc = table[k];
     std::memset(&fc, 0, sizeof(fc));
-    fc.node = front[k].node;
+    const int v = front[k].node;
+    fc.node = pos[v];
+    fc.end = pos[v] + size[v];
     fc.npath = (int)front[k].path.size();
     for (int j = 0; j < fc.npath; ++j) {
-      fc.path[j] = front[k].path[j];
-      if (nb[fc.node].x == nb[fc.path[j]].x) fc.first_mask |= 1u << j;
+      const int a = front[k].path[j];
+      fc.path[j] = pos[a];
+      if (nb[v].x == nb[a].x) fc.first_mask |= 1u << j;
     }
   }
   int rc = dev_alloc_n(&T->front, table.size(), s);
@@ -245,16 +279,31 @@ static int build_frontier(fga_tree* T, int target, cudaStream_t s) {
   return FGA_OK;
 }
 
-__global__ void k_interleave(const float4* __restrict__ cm, const int4* __restrict__ info,
-                             int64_t n, float4* __restrict__ rec) {
+// The depth-first records: cell v at pre[2 * pos[v]] with (l^2, subtree size,
+// count, first body). A single-particle leaf gets l^2 = -1 (always accepted:
+// its one exact term). A leaf holding nb >= 2 particles keeps its l^2 (its
+// monopole when accepted) and is followed by nb single-particle records, one
+// per particle in order, which the walk enters when the leaf is rejected: the
+// same exact terms as the leaf's particle loop of Algorithm 2.
+__global__ void k_interleave_pre(const float4* __restrict__ cm, const int4* __restrict__ info,
+                                 const int* __restrict__ size, const int* __restrict__ pos,
+                                 const float4* __restrict__ bodies, int64_t n, float4* __restrict__ pre) {
+  const float4 single = make_float4(-1.0f, __int_as_float(1), __int_as_float(-1), __int_as_float(0));
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int4 in = info[i];
-    rec[2 * i] = cm[i];
-    // a single-particle leaf is always added as its one exact term (its
-    // particle), accepted or not; l^2 = -1 makes the opening test accept it
-    const float l2 = in.z == -1 ? -1.0f : __int_as_float(in.x);
-    rec[2 * i + 1] = make_float4(l2, __int_as_float(in.y), __int_as_float(in.z), __int_as_float(in.w));
+    const int64_t p = pos[i];
+    pre[2 * p] = cm[i];
+    if (in.z == -1) {
+      pre[2 * p + 1] = single;
+      continue;
+    }
+    pre[2 * p + 1] = make_float4(__int_as_float(in.x), __int_as_float(size[i]), __int_as_float(in.z),
+                                 __int_as_float(in.z < 0 ? in.y : 0));
+    for (int b = 0; b < -in.z; ++b) {
+      pre[2 * (p + 1 + b)] = bodies[in.y + b];
+      pre[2 * (p + 1 + b) + 1] = single;
+    }
   }
 }
 
@@ -282,6 +331,7 @@ int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out
   int *idx = nullptr, *itmp = nullptr, *ustart = nullptr;
   unsigned *flags = nullptr, *uid = nullptr, *n_u = nullptr;
   int2* node_range = nullptr;
+  int *node_size = nullptr, *node_pos = nullptr;
   Sum4 *sum_m = nullptr, *sum_p = nullptr;
   float* box = nullptr;
   LevelInfo* lv = nullptr;
@@ -294,6 +344,8 @@ int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out
   rc |= dev_alloc_n(&uid, N, s);
   rc |= dev_alloc_n(&n_u, 1, s);
   rc |= dev_alloc_n(&node_range, cap, s);
+  rc |= dev_alloc_n(&node_size, cap, s);
+  rc |= dev_alloc_n(&node_pos, cap, s);
   rc |= dev_alloc_n(&sum_m, cap, s);
   rc |= dev_alloc_n(&sum_p, cap, s);
   rc |= dev_alloc_n(&box, 6, s);
@@ -336,13 +388,20 @@ int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out
     FGA_LAUNCH_CHECK("build_level");
   }
   for (int L = D; L >= 0; --L) {
-    k_mass_level<<<grid, TB, 0, s>>>(L, lv, T->bodies, T->node_info, sum_m, sum_p, T->node_cm);
+    k_mass_level<<<grid, TB, 0, s>>>(L, lv, T->bodies, T->node_info, sum_m, sum_p, T->node_cm, node_size);
     FGA_LAUNCH_CHECK("mass_level");
+  }
+  FGA_CUDA_TRY(cudaMemsetAsync(node_pos, 0, sizeof(int), s));
+  for (int L = 0; L <= D; ++L) {
+    k_preorder_level<<<grid, TB, 0, s>>>(L, lv, T->node_info, node_size, node_pos);
+    FGA_LAUNCH_CHECK("preorder_level");
   }
   LevelInfo h_lv;
   unsigned h_nu = 0;
+  int h_npre = 0;
   FGA_CUDA_TRY(cudaMemcpyAsync(&h_lv, lv, sizeof(h_lv), cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaMemcpyAsync(&h_nu, n_u, sizeof(h_nu), cudaMemcpyDeviceToHost, s));
+  FGA_CUDA_TRY(cudaMemcpyAsync(&h_npre, node_size, sizeof(int), cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaStreamSynchronize(s));
   dev_free(ktmp, s);
   dev_free(ukey, s);
@@ -357,23 +416,26 @@ int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out
   dev_free(sum_p, s);
   dev_free(box, s);
   dev_free(lv, s);
+  auto fail2 = [&](int code) {
+    dev_free(node_size, s);
+    dev_free(node_pos, s);
+    fga_tree_destroy(T);
+    return code;
+  };
   if (h_lv.overflow) {
     set_error("tree_build: node capacity exceeded");
-    fga_tree_destroy(T);
-    return FGA_EINTERNAL;
+    return fail2(FGA_EINTERNAL);
   }
   T->n_nodes = h_lv.start[D + 1];
   T->n_unique = (int)h_nu;
-  if ((rc = build_frontier(T, front_target, s))) {
-    fga_tree_destroy(T);
-    return rc;
-  }
-  if (dev_alloc_n(&T->node_rec, (size_t)2 * T->n_nodes, s)) {
-    fga_tree_destroy(T);
-    return FGA_ENOMEM;
-  }
-  k_interleave<<<grid, TB, 0, s>>>(T->node_cm, T->node_info, T->n_nodes, T->node_rec);
-  FGA_LAUNCH_CHECK("interleave");
+  T->n_pre = h_npre;  // the root's subtree: every record
+  if ((rc = build_frontier(T, front_target, node_pos, node_size, s))) return fail2(rc);
+  if (dev_alloc_n(&T->node_pre, (size_t)2 * T->n_pre, s)) return fail2(FGA_ENOMEM);
+  k_interleave_pre<<<grid, TB, 0, s>>>(T->node_cm, T->node_info, node_size, node_pos, T->bodies, T->n_nodes,
+                                       T->node_pre);
+  FGA_LAUNCH_CHECK("interleave_pre");
+  dev_free(node_size, s);
+  dev_free(node_pos, s);
   *out = T;
   return FGA_OK;
 }
@@ -394,12 +456,29 @@ extern "C" void fga_tree_destroy(fga_tree* t) {
   dev_free(t->node_info, t->stream);
   dev_free(t->node_bodies, t->stream);
   dev_free(t->front, t->stream);
-  dev_free(t->node_rec, t->stream);
+  dev_free(t->node_pre, t->stream);
   if (prev != t->device) cudaSetDevice(prev);
   delete t;
 }
 
 extern "C" int64_t fga_tree_node_count(const fga_tree* t) { return t ? t->n_nodes : 0; }
+
+extern "C" int64_t fga_tree_preorder(const fga_tree* t, int64_t cap, float* out, void* stream) {
+  clear_error();
+  if (!t) {
+    set_error("fga_tree_preorder: null tree");
+    return FGA_EINVAL;
+  }
+  if (cap == 0) return t->n_pre;
+  if (cap < t->n_pre || !out) {
+    set_error("fga_tree_preorder: buffer smaller than the record count");
+    return FGA_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  FGA_CUDA_TRY(cudaMemcpyAsync(out, t->node_pre, sizeof(float4) * 2 * t->n_pre, cudaMemcpyDeviceToHost, s));
+  FGA_CUDA_TRY(cudaStreamSynchronize(s));
+  return t->n_pre;
+}
 
 extern "C" int64_t fga_tree_export(const fga_tree* t, int64_t cap, int64_t* ints, double* dbls,
                                    int64_t* leaf_of, void* stream) {

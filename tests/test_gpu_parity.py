@@ -99,6 +99,41 @@ def test_tree_matches_oracle(fga, orc, name):
     np.testing.assert_allclose(eg["l"], eo["l"], rtol=1e-14)
 
 
+@pytest.mark.parametrize("name", list(_tree_cases().keys()))
+def test_walk_records_are_the_oracle_tree_in_preorder(fga, orc, name):
+    # The per-point walk reads the tree as depth-first records with subtree
+    # sizes; a leaf of several points is followed by one record per point.
+    X, m, depth = _tree_cases()[name]
+    X = _f32(X)
+    m = _f32(m)
+    eo = orc.Tree(X, m, max_depth=depth).export()
+    rec = fga.fga_tree_build(_cuda(X), _cuda(m), fga.params(max_depth=depth)).preorder()
+    n = len(eo["depth"])
+    multi = eo["is_leaf"] & (eo["npts"] >= 2)
+    own = 1 + np.where(multi, eo["npts"], 0)
+    size = own.copy()
+    for k in range(n - 1, 0, -1):  # pre-order: descendants follow their ancestors
+        size[eo["parent"][k]] += size[k]
+    start = np.concatenate([[0], np.cumsum(own)[:-1]])
+    assert len(rec["size"]) == own.sum() == size[0]
+    np.testing.assert_array_equal(rec["size"][start], size)
+    nchild = np.bincount(eo["parent"][1:], minlength=n)
+    count = np.where(eo["is_leaf"], -eo["npts"], nchild)
+    np.testing.assert_array_equal(rec["count"][start], count)
+    np.testing.assert_allclose(rec["mass"][start], eo["mass"], rtol=2e-7)
+    scale = np.abs(X).max() + 1e-30
+    np.testing.assert_allclose(rec["com"][start], eo["com"], rtol=0, atol=4e-7 * scale)
+    single = eo["is_leaf"] & (eo["npts"] == 1)
+    assert np.all(rec["l2"][start][single] == -1.0)
+    np.testing.assert_allclose(rec["l2"][start][~single], eo["l"][~single] ** 2, rtol=1e-6)
+    for k in np.flatnonzero(multi):
+        r = start[k] + 1 + np.arange(eo["npts"][k])
+        assert np.all(rec["l2"][r] == -1.0) and np.all(rec["size"][r] == 1) and np.all(rec["count"][r] == -1)
+        pts = np.c_[X, m][eo["leaf_of"] == k]
+        got = np.c_[rec["com"][r], rec["mass"][r]]
+        np.testing.assert_array_equal(got[np.lexsort(got.T[::-1])], pts[np.lexsort(pts.T[::-1])].astype(np.float32))
+
+
 # --------------------------------------------------------------------------- Eq. 6
 
 @pytest.mark.parametrize("N,M", [(1000, 1000), (3001, 777), (257, 4099), (1, 5), (70000, 300)])
