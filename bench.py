@@ -744,6 +744,9 @@ def run_ours_grid(a):
 def tune_summary(rep):
     return {"direct_max_n": rep["direct_max_n"],
             "direct_tiles": ["%dx%d" % (b, q) for b, q in zip(rep["direct_bs"], rep["direct_qpt"])],
+            "sizes": list(rep["sizes"]),
+            "direct_us_per_point": [round(x, 5) for x in rep["direct_us_per_point"]],
+            "bh_us_per_point": [round(x, 5) for x in rep["bh_us_per_point"]],
             "tune_ms": rep["elapsed_ms"]}
 
 

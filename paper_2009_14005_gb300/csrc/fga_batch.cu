@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch
                                                                      unsigned ntasks, unsigned* ctr,
                                                                      const unsigned* __restrict__ order,
                                                                      unsigned* __restrict__ cost) {
-  __shared__ float4 s_tile[BATCH_WARPS][32];
+  __shared__ float4 s_tile[BATCH_WARPS][64];  // 32 sources as (x, x, y, y), (z, z, m, m)
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (;;) {
     unsigned slot = 0;
@@ -88,8 +88,8 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch
       for (int off = 16; off > 0; off >>= 1) c += __shfl_down_sync(FULL, c, off);
       if (lane == 0 && c) atomicAdd(&ds->interactions, c);
     } else {
-      // 64 template points, two per lane (one shared-memory load serves two
-      // terms), against reference chunk f, staged 32 sources at a time
+      // 64 template points, two per lane (the packed FP32 instructions serve
+      // both), against reference chunk f, staged 32 sources at a time
       const int64_t i0 = (int64_t)grp * 64 + lane, i1 = i0 + 32;
       const bool v0 = i0 < M, v1 = i1 < M;
       const float3 y0 = place(xf, P.Y0[v0 ? i0 : 0]);
@@ -100,26 +100,21 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch
       const int64_t j1 = min(P.N, j0 + BATCH_CHUNK);
       // a 32-source tile for 64 points costs about as much as 16 Barnes-Hut walk steps
       if (cost && lane == 0) cost[task] = 16u * (unsigned)((j1 - j0 + 31) / 32) + 1u;
+      const f2 nyx = f2_pack(-y0.x, -y1.x), nyy = f2_pack(-y0.y, -y1.y), nyz = f2_pack(-y0.z, -y1.z);
+      const f2 e2 = f2_pack(eps2, eps2);
       for (int64_t b = j0; b < j1; b += 32) {
         const int64_t j = b + lane;
-        s_tile[w][lane] = j < j1 ? P.X4[j] : make_float4(0.f, 0.f, 0.f, 0.f);  // m = 0 pads
+        const float4 src = j < j1 ? P.X4[j] : make_float4(0.f, 0.f, 0.f, 0.f);  // m = 0 pads
+        s_tile[w][2 * lane] = make_float4(src.x, src.x, src.y, src.y);
+        s_tile[w][2 * lane + 1] = make_float4(src.z, src.z, src.w, src.w);
         __syncwarp();
-        float p0x = 0.f, p0y = 0.f, p0z = 0.f, p1x = 0.f, p1y = 0.f, p1z = 0.f;
+        f2 ax = f2_pack(0.f, 0.f), ay = ax, az = ax;
 #pragma unroll 8
-        for (int q = 0; q < 32; ++q) {
-          const float4 src = s_tile[w][q];
-          const float ax = src.x - y0.x, ay = src.y - y0.y, az = src.z - y0.z;
-          const float bx = src.x - y1.x, by = src.y - y1.y, bz = src.z - y1.z;
-          const float ia = rsqrt_fast(fmaf(ax, ax, fmaf(ay, ay, fmaf(az, az, eps2))));
-          const float ib = rsqrt_fast(fmaf(bx, bx, fmaf(by, by, fmaf(bz, bz, eps2))));
-          const float wa = src.w * (ia * ia * ia), wb = src.w * (ib * ib * ib);
-          p0x = fmaf(wa, ax, p0x);
-          p0y = fmaf(wa, ay, p0y);
-          p0z = fmaf(wa, az, p0z);
-          p1x = fmaf(wb, bx, p1x);
-          p1y = fmaf(wb, by, p1y);
-          p1z = fmaf(wb, bz, p1z);
-        }
+        for (int q = 0; q < 32; ++q) pair_term2(s_tile[w][2 * q], s_tile[w][2 * q + 1], nyx, nyy, nyz, e2, ax, ay, az);
+        float p0x, p0y, p0z, p1x, p1y, p1z;
+        f2_unpack(ax, p0x, p1x);
+        f2_unpack(ay, p0y, p1y);
+        f2_unpack(az, p0z, p1z);
         comp_add(h0x, l0x, p0x);
         comp_add(h0y, l0y, p0y);
         comp_add(h0z, l0z, p0z);

@@ -50,6 +50,59 @@ __device__ __forceinline__ float rsqrt_fast(float x) {
   return y;
 }
 
+// Two FP32 values in one 64-bit register, and the packed FP32 instructions of
+// sm_100 and later (PTX add/mul/fma .rn.f32x2): each element is computed and
+// rounded exactly as the scalar instruction would, two per issue slot.
+struct f2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f2 f2_pack(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2 r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r.v));
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d.v) : "l"(a.v), "l"(b.v));
+  return d;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return d;
+}
+__device__ __forceinline__ f2 f2_from(float4 v, int hi) {  // (x, y) or (z, w) of a float4
+  return hi ? f2_pack(v.z, v.w) : f2_pack(v.x, v.y);
+}
+
+// Eq. 6 for two template points a, b (packed coordinates nya = -y) and one
+// source s given as sxy = (s.x, s.x, s.y, s.y), szm = (s.z, s.z, s.m, s.m):
+// adds m / (r^2 + eps^2)^(3/2) * (s - y) to (px, py, pz) of both points, with
+// the same operations in the same order as the scalar loop (s.x - y.x is
+// s.x + (-y.x), exactly).
+__device__ __forceinline__ void pair_term2(float4 sxy, float4 szm, f2 nyx, f2 nyy, f2 nyz, f2 eps2,
+                                           f2& px, f2& py, f2& pz) {
+  const f2 dx = f2_add(f2_from(sxy, 0), nyx);
+  const f2 dy = f2_add(f2_from(sxy, 1), nyy);
+  const f2 dz = f2_add(f2_from(szm, 0), nyz);
+  const f2 r2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_fma(dz, dz, eps2)));
+  float ra, rb;
+  f2_unpack(r2, ra, rb);
+  const f2 inv = f2_pack(rsqrt_fast(ra), rsqrt_fast(rb));
+  const f2 w = f2_mul(f2_from(szm, 1), f2_mul(f2_mul(inv, inv), inv));
+  px = f2_fma(w, dx, px);
+  py = f2_fma(w, dy, py);
+  pz = f2_fma(w, dz, pz);
+}
+
 // Knuth's TwoSum: s + e == a + b exactly.
 __device__ __forceinline__ void comp_add(float& hi, float& lo, float x) {
   const float s = hi + x;

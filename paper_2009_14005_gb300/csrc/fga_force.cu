@@ -17,9 +17,11 @@ namespace fga {
 // ------------------------------------------------------------------ Eq. 6, all pairs
 //
 // Block of BS threads, each thread owns QPT template points. Sources are
-// staged through shared memory one tile of BS float4 (x, y, z, m) at a time;
-// every thread reads the same source (a broadcast). Per pair: 3 FADD, 3 FFMA
-// (r^2 + eps^2), one MUFU rsqrt, 3 FMUL (m / r^3), 3 FFMA (accumulate).
+// staged through shared memory one tile of BS sources at a time; every thread
+// reads the same source (a broadcast). Per pair: 3 FADD, 3 FFMA
+// (r^2 + eps^2), one MUFU rsqrt, 3 FMUL (m / r^3), 3 FFMA (accumulate); with
+// an even QPT the thread's points go in pairs through the packed two-wide
+// FP32 instructions (pair_term2), half the issue slots for the same results.
 // Each tile's plain FP32 partial is folded into a TwoSum-compensated
 // accumulator. blockIdx.y splits the sources into `chunk`-sized ranges whose
 // partials the epilogue adds (compensated) in a fixed order.
@@ -30,7 +32,10 @@ __global__ void __launch_bounds__(BS) k_direct(const float4* __restrict__ X, int
                                                float4* __restrict__ hi_out,
                                                float4* __restrict__ lo_out) {
   if (ds->done) return;
-  __shared__ float4 tile[BS];
+  // even QPT: template points in pairs, each source staged as (x, x, y, y),
+  // (z, z, m, m) so that the packed FP32 instructions serve both points
+  constexpr bool PAIRED = QPT % 2 == 0;
+  __shared__ float4 tile[PAIRED ? 2 * BS : BS];
   const Xf xf = load_xf(ds);
   const int split = blockIdx.y;
   const int64_t j0 = (int64_t)split * chunk;
@@ -49,23 +54,54 @@ __global__ void __launch_bounds__(BS) k_direct(const float4* __restrict__ X, int
   }
   for (int64_t b = j0; b < j1; b += BS) {
     const int64_t j = b + threadIdx.x;
-    tile[threadIdx.x] = j < j1 ? X[j] : make_float4(0.f, 0.f, 0.f, 0.f);  // m = 0 pads the tail
+    const float4 src = j < j1 ? X[j] : make_float4(0.f, 0.f, 0.f, 0.f);  // m = 0 pads the tail
+    if constexpr (PAIRED) {
+      tile[2 * threadIdx.x] = make_float4(src.x, src.x, src.y, src.y);
+      tile[2 * threadIdx.x + 1] = make_float4(src.z, src.z, src.w, src.w);
+    } else {
+      tile[threadIdx.x] = src;
+    }
     __syncthreads();
     float px[QPT], py[QPT], pz[QPT];
+    if constexpr (PAIRED) {
+      constexpr int NPR = QPT / 2;
+      f2 ax[NPR], ay[NPR], az[NPR], nyx[NPR], nyy[NPR], nyz[NPR];
+      const f2 e2 = f2_pack(eps2, eps2);
 #pragma unroll
-    for (int q = 0; q < QPT; ++q) px[q] = py[q] = pz[q] = 0.f;
+      for (int r = 0; r < NPR; ++r) {
+        ax[r] = ay[r] = az[r] = f2_pack(0.f, 0.f);
+        nyx[r] = f2_pack(-yx[2 * r], -yx[2 * r + 1]);
+        nyy[r] = f2_pack(-yy[2 * r], -yy[2 * r + 1]);
+        nyz[r] = f2_pack(-yz[2 * r], -yz[2 * r + 1]);
+      }
 #pragma unroll 8
-    for (int k = 0; k < BS; ++k) {
-      const float4 s = tile[k];
+      for (int k = 0; k < BS; ++k) {
+        const float4 sxy = tile[2 * k], szm = tile[2 * k + 1];
 #pragma unroll
-      for (int q = 0; q < QPT; ++q) {
-        const float dx = s.x - yx[q], dy = s.y - yy[q], dz = s.z - yz[q];
-        const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
-        const float inv = rsqrt_fast(r2);
-        const float w = s.w * (inv * inv * inv);
-        px[q] = fmaf(w, dx, px[q]);
-        py[q] = fmaf(w, dy, py[q]);
-        pz[q] = fmaf(w, dz, pz[q]);
+        for (int r = 0; r < NPR; ++r) pair_term2(sxy, szm, nyx[r], nyy[r], nyz[r], e2, ax[r], ay[r], az[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < NPR; ++r) {
+        f2_unpack(ax[r], px[2 * r], px[2 * r + 1]);
+        f2_unpack(ay[r], py[2 * r], py[2 * r + 1]);
+        f2_unpack(az[r], pz[2 * r], pz[2 * r + 1]);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < QPT; ++q) px[q] = py[q] = pz[q] = 0.f;
+#pragma unroll 8
+      for (int k = 0; k < BS; ++k) {
+        const float4 s = tile[k];
+#pragma unroll
+        for (int q = 0; q < QPT; ++q) {
+          const float dx = s.x - yx[q], dy = s.y - yy[q], dz = s.z - yz[q];
+          const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2)));
+          const float inv = rsqrt_fast(r2);
+          const float w = s.w * (inv * inv * inv);
+          px[q] = fmaf(w, dx, px[q]);
+          py[q] = fmaf(w, dy, py[q]);
+          pz[q] = fmaf(w, dz, pz[q]);
+        }
       }
     }
 #pragma unroll
@@ -160,21 +196,21 @@ int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const
 //     cell mass at its CoM);
 //   * otherwise an internal cell's children are visited next, and a leaf
 //     holding several particles adds each of them exactly.
-// The pending work of a lane is one range of unvisited siblings per level,
-// packed as (first cell << 4 | count) into one word; the current range lives
-// in registers and the rest in a per-lane column of shared memory (at most
-// one entry per tree level). A cell record is 32 bytes (CoM + mass, then l^2,
-// first child / body, child count, depth), fetched with two loads from the
-// same sector. Warps hold 32 Morton-neighbouring points, so their walks touch
-// mostly the same cells and the loads are served by L1.
+// The tree is read as depth-first records (fga_tree::node_pre), 32 bytes
+// each (CoM + mass, then l^2, subtree record count, child count, first
+// particle), fetched with two loads from the same sector. A walk needs no
+// stack: after a record whose cell the point accepts it skips the subtree,
+// after a rejected one it continues with the next record (the first child).
+// Warps hold 32 Morton-neighbouring points, so their walks touch mostly the
+// same records and the loads are served by L1.
 //
 // Work is split into tasks (group of template points, frontier cell): a task
 // first judges the frontier cell's ancestors (a point accepting one stops;
 // the monopole is added by the task owning the ancestor's first frontier
 // cell), then walks the frontier cell's subtree. Two walks: per lane (32-point
-// groups, bh_task) or cooperative (64-point groups, one walk for the warp,
-// bh_walk<2>), chosen by bh_walk_kind. Tasks are handed out dynamically
-// from a counter in DevState; the last warp to finish resets it.
+// groups, bh_task_pre) or cooperative (64-point groups, one walk for the
+// warp, bh_walk<2>), chosen by bh_walk_kind. Tasks are handed out
+// dynamically from a counter in DevState; the last warp to finish resets it.
 #ifndef FGA_BH_WARPS
 #define FGA_BH_WARPS 4
 #endif
@@ -184,7 +220,7 @@ static constexpr int BH_WARPS = FGA_BH_WARPS;
 #define FGA_BH_MINBLOCKS 8  // resident blocks per SM the register budget is sized for
 #endif
 // NP = 0: one template point per lane, each lane walking its own point over
-// the depth-first records (bh_task_pre); NP > 0: NP points per lane, one
+// the depth-first records (bh_task_pre); NP = 2: two points per lane, one
 // walk for the warp (bh_walk).
 template <int NP>
 __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const float4* __restrict__ pre,

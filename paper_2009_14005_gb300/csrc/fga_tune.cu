@@ -6,9 +6,10 @@
 //     that class; the fastest shape goes into the tile table of plan_direct.
 //   * The FGA_AUTO crossover between the all-pairs sum and Barnes-Hut in the
 //     batch kernels: for reference sizes N = 1k .. 64k, the force cost per
-//     template point of each method (a 32k-point template, so that one pair
-//     fills the GPU) plus, for Barnes-Hut, the tree build amortised over the
-//     iterations of a registration with M = N. The crossover is the largest
+//     template point of each method (a template of at least 32k points, large
+//     enough that one pair fills the GPU with either method) plus, for
+//     Barnes-Hut, the tree build amortised over the iterations of a
+//     registration with M = N. The crossover is the largest
 //     N up to which the all-pairs sum is not slower.
 //
 // The synthetic clouds are points on a few planar patches with a little
@@ -209,12 +210,17 @@ extern "C" int fga_autotune(const fga_params* p_in, int flags, void* stream, fga
   // ---------------------------------------------------------------- crossover
   if (flags & FGA_TUNE_CROSSOVER) {
     const int iters = p.max_iter > 0 ? p.max_iter : 100;
-    const int64_t Mt = 32768;
     int64_t crossover = 0;
     bool bh_won = false;
+    const int64_t warps = (int64_t)sm_count() * 32;
     for (int k = 0; k < FGA_TUNE_NSIZES; ++k) {
       const int64_t N = (int64_t)1024 << k;
       out->sizes[k] = N;
+      // template size: at least 32768 points and enough 64-point all-pairs
+      // tasks (one per reference chunk) for 4 per resident warp, so that both
+      // methods fill the GPU as in a large batch
+      const int64_t chunks = (N + BATCH_CHUNK - 1) / BATCH_CHUNK;
+      const int64_t Mt = std::max<int64_t>(32768, (4 * warps + chunks - 1) / chunks * 64);
       double per_point[2] = {0, 0};
       for (int m = 0; m < 2; ++m) {
         fga_params q = p;
