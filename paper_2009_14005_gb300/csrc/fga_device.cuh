@@ -555,6 +555,14 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const Fr
   unsigned e = any != 0u ? (((unsigned)front[f].node << 4) | 1u) : 0u;
   unsigned se = 0u;
   int sp = 0;
+  // NP == 2: packed coordinates -y of the two points, and packed partial sums
+  // (which take over the ancestors' terms; p is unpacked from them before
+  // every use)
+  const f2 nyx = f2_pack(-y[0].x, -y[NP - 1].x), nyy = f2_pack(-y[0].y, -y[NP - 1].y);
+  const f2 nyz = f2_pack(-y[0].z, -y[NP - 1].z);
+  const f2 th2 = f2_pack(theta2, theta2), e2 = f2_pack(eps2, eps2);
+  f2 px2 = f2_pack(p[0][0], p[NP - 1][0]), py2 = f2_pack(p[0][1], p[NP - 1][1]);
+  f2 pz2 = f2_pack(p[0][2], p[NP - 1][2]);
   while ((e & 15u) != 0u) {
     ++steps;
     const int v = (int)(e >> 4);
@@ -564,22 +572,51 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const Fr
     e += ((unsigned)__float_as_int(ri.y) << 4) - 1u;  // next sibling
     bool rej[NP];
     unsigned r[NP], rany = 0u;
+    if constexpr (NP == 2) {
+      // both points judge the same cell: the packed FP32 instructions take
+      // them together, each element as the scalar code below computes it
+      const f2 dx = f2_add(f2_pack(cm.x, cm.x), nyx), dy = f2_add(f2_pack(cm.y, cm.y), nyy);
+      const f2 dz = f2_add(f2_pack(cm.z, cm.z), nyz);
+      const f2 d2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+      const f2 od2 = f2_mul(th2, d2);
+      float o0, o1, e0, e1;
+      f2_unpack(od2, o0, o1);
+      f2_unpack(f2_add(d2, e2), e0, e1);
+      const bool act0 = (m[0] & bit) != 0u, act1 = (m[1] & bit) != 0u;
+      const bool acc0 = act0 && ri.x < o0, acc1 = act1 && ri.x < o1;
+      const f2 inv = f2_pack(rsqrt_fast(e0), rsqrt_fast(e1));
+      const f2 w = f2_mul(f2_pack(cm.w, cm.w), f2_mul(f2_mul(inv, inv), inv));
+      float w0, w1;
+      f2_unpack(w, w0, w1);
+      const f2 wsel = f2_pack(acc0 ? w0 : 0.f, acc1 ? w1 : 0.f);
+      px2 = f2_fma(wsel, dx, px2);
+      py2 = f2_fma(wsel, dy, py2);
+      pz2 = f2_fma(wsel, dz, pz2);
+      cnt[0] += acc0;
+      cnt[1] += acc1;
+      rej[0] = act0 && !acc0;
+      rej[1] = act1 && !acc1;
+      r[0] = __ballot_sync(FULL, rej[0]);
+      r[1] = __ballot_sync(FULL, rej[1]);
+      rany = r[0] | r[1];
+    } else {
 #pragma unroll
-    for (int q = 0; q < NP; ++q) {
-      const bool act = (m[q] & bit) != 0u;
-      const float dx = cm.x - y[q].x, dy = cm.y - y[q].y, dz = cm.z - y[q].z;
-      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-      // single-particle records carry l^2 = -1: always accepted (one exact term)
-      const bool accept = act && ri.x < theta2 * d2;
-      const float inv = rsqrt_fast(d2 + eps2);
-      const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
-      p[q][0] = fmaf(wgt, dx, p[q][0]);
-      p[q][1] = fmaf(wgt, dy, p[q][1]);
-      p[q][2] = fmaf(wgt, dz, p[q][2]);
-      cnt[q] += accept;
-      rej[q] = act && !accept;
-      r[q] = __ballot_sync(FULL, rej[q]);
-      rany |= r[q];
+      for (int q = 0; q < NP; ++q) {
+        const bool act = (m[q] & bit) != 0u;
+        const float dx = cm.x - y[q].x, dy = cm.y - y[q].y, dz = cm.z - y[q].z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        // single-particle records carry l^2 = -1: always accepted (one exact term)
+        const bool accept = act && ri.x < theta2 * d2;
+        const float inv = rsqrt_fast(d2 + eps2);
+        const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
+        p[q][0] = fmaf(wgt, dx, p[q][0]);
+        p[q][1] = fmaf(wgt, dy, p[q][1]);
+        p[q][2] = fmaf(wgt, dz, p[q][2]);
+        cnt[q] += accept;
+        rej[q] = act && !accept;
+        r[q] = __ballot_sync(FULL, rej[q]);
+        rany |= r[q];
+      }
     }
     if (rany != 0u) {
       if (nchild > 0) {
@@ -601,6 +638,11 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const Fr
         // leaf holding several particles, rejected by these points: each
         // particle exactly, from the single-particle records that follow it (rare)
         const int nb = -nchild;
+        if constexpr (NP == 2) {
+          f2_unpack(px2, p[0][0], p[1][0]);
+          f2_unpack(py2, p[0][1], p[1][1]);
+          f2_unpack(pz2, p[0][2], p[1][2]);
+        }
         for (int b = 1; b <= nb; ++b) {
           const float4 qb = pre[2 * (v + b)];
 #pragma unroll
@@ -615,6 +657,11 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const Fr
         }
 #pragma unroll
         for (int q = 0; q < NP; ++q) cnt[q] += rej[q] ? (unsigned)nb : 0u;
+        if constexpr (NP == 2) {
+          px2 = f2_pack(p[0][0], p[1][0]);
+          py2 = f2_pack(p[0][1], p[1][1]);
+          pz2 = f2_pack(p[0][2], p[1][2]);
+        }
       }
     }
     // range exhausted: resume the innermost saved range
@@ -625,6 +672,12 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const Fr
       for (int q = 0; q < NP; ++q) m[q] = __shfl_sync(FULL, sm[q], sp);
     }
     if ((steps & 31u) == 0u) {
+      if constexpr (NP == 2) {
+        f2_unpack(px2, p[0][0], p[1][0]);
+        f2_unpack(py2, p[0][1], p[1][1]);
+        f2_unpack(pz2, p[0][2], p[1][2]);
+        px2 = py2 = pz2 = f2_pack(0.f, 0.f);
+      }
 #pragma unroll
       for (int q = 0; q < NP; ++q)
 #pragma unroll
@@ -633,6 +686,11 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const Fr
           p[q][c] = 0.f;
         }
     }
+  }
+  if constexpr (NP == 2) {
+    f2_unpack(px2, p[0][0], p[1][0]);
+    f2_unpack(py2, p[0][1], p[1][1]);
+    f2_unpack(pz2, p[0][2], p[1][2]);
   }
 #pragma unroll
   for (int q = 0; q < NP; ++q)
