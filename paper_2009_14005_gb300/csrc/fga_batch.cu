@@ -27,6 +27,7 @@
 
 #include "fga_batch.cuh"
 #include "fga_device.cuh"
+#include "fga_epi.cuh"
 
 namespace fga {
 

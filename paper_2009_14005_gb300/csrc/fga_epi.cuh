@@ -1,0 +1,472 @@
+// Device code of the epilogue, shared by the single-pair kernels
+// (fga_force.cu) and the batched kernels (fga_batch.cu): the per-point ODE
+// step with its reduction terms (Eqs. 7-10), the block and cross-block FP64
+// reductions, and the FP64 rigid fit of one iteration (Eqs. 14, 16) with the
+// composition of the transform and the stop test.
+#pragma once
+
+#include "fga_device.cuh"
+
+namespace fga {
+
+// Symmetric 3x3 eigen-decomposition by cyclic Jacobi rotations (FP64):
+// A = V diag(w) V^T, eigenvalues sorted descending, eigenvectors in V's columns.
+static __device__ void eig_sym3(const double A_in[9], double w[3], double V[9]) {
+  double A[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    A[k] = A_in[k];
+    V[k] = (k % 4 == 0) ? 1.0 : 0.0;
+  }
+  for (int sweep = 0; sweep < 32; ++sweep) {
+    const double off = A[1] * A[1] + A[2] * A[2] + A[5] * A[5];
+    const double dia = A[0] * A[0] + A[4] * A[4] + A[8] * A[8];
+    if (!(off > 1e-32 * dia)) break;
+    for (int pq = 0; pq < 3; ++pq) {
+      const int p = pq == 2 ? 1 : 0;
+      const int q = pq == 0 ? 1 : 2;
+      const double apq = A[3 * p + q];
+      if (apq == 0.0) continue;
+      const double app = A[3 * p + p], aqq = A[3 * q + q];
+      const double tau = (aqq - app) / (2.0 * apq);
+      const double tn = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+      const double c = 1.0 / sqrt(1.0 + tn * tn), sn = tn * c;
+      // A <- J^T A J with J the rotation in the (p, q) plane
+      for (int k = 0; k < 3; ++k) {
+        const double akp = A[3 * k + p], akq = A[3 * k + q];
+        A[3 * k + p] = c * akp - sn * akq;
+        A[3 * k + q] = sn * akp + c * akq;
+      }
+      for (int k = 0; k < 3; ++k) {
+        const double apk = A[3 * p + k], aqk = A[3 * q + k];
+        A[3 * p + k] = c * apk - sn * aqk;
+        A[3 * q + k] = sn * apk + c * aqk;
+      }
+      for (int k = 0; k < 3; ++k) {
+        const double vkp = V[3 * k + p], vkq = V[3 * k + q];
+        V[3 * k + p] = c * vkp - sn * vkq;
+        V[3 * k + q] = sn * vkp + c * vkq;
+      }
+    }
+  }
+  w[0] = A[0];
+  w[1] = A[4];
+  w[2] = A[8];
+  // sort descending (3 elements)
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2 - a; ++b)
+      if (w[b] < w[b + 1]) {
+        const double tw = w[b];
+        w[b] = w[b + 1];
+        w[b + 1] = tw;
+        for (int k = 0; k < 3; ++k) {
+          const double tv = V[3 * k + b];
+          V[3 * k + b] = V[3 * k + b + 1];
+          V[3 * k + b + 1] = tv;
+        }
+      }
+}
+
+// Proper rotation maximising tr(R^T C): with C = sum_k s_k u_k v_k^T,
+// R = u1 v1^T + u2 v2^T + (u1 x u2)(v1 x v2)^T, i.e. U diag(1, 1, sgn det(U V^T)) V^T
+// of Eq. 14 written with the two leading singular pairs only. The pairs come
+// from the eigenvectors of C^T C (v_k) and u_k = C v_k / |C v_k| (u2 made
+// orthogonal to u1). Returns false when the second singular value is below
+// 1e-7 of the first (rank(C) < 2: no rotation is determined).
+static __device__ bool rigid_rotation(const double C[9], double R[9]) {
+  double B[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      B[3 * r + c] = C[r] * C[c] + C[3 + r] * C[3 + c] + C[6 + r] * C[6 + c];
+  double lam[3], V[9];
+  eig_sym3(B, lam, V);
+  if (!(lam[0] > 0.0) || !(lam[1] > 1e-14 * lam[0])) return false;
+  double v1[3] = {V[0], V[3], V[6]}, v2[3] = {V[1], V[4], V[7]};
+  double u1[3], u2[3];
+  for (int r = 0; r < 3; ++r) {
+    u1[r] = C[3 * r] * v1[0] + C[3 * r + 1] * v1[1] + C[3 * r + 2] * v1[2];
+    u2[r] = C[3 * r] * v2[0] + C[3 * r + 1] * v2[1] + C[3 * r + 2] * v2[2];
+  }
+  const double n1 = sqrt(u1[0] * u1[0] + u1[1] * u1[1] + u1[2] * u1[2]);
+  for (int r = 0; r < 3; ++r) u1[r] /= n1;
+  const double pr = u1[0] * u2[0] + u1[1] * u2[1] + u1[2] * u2[2];
+  for (int r = 0; r < 3; ++r) u2[r] -= pr * u1[r];
+  const double n2 = sqrt(u2[0] * u2[0] + u2[1] * u2[1] + u2[2] * u2[2]);
+  if (!(n2 > 0.0)) return false;
+  for (int r = 0; r < 3; ++r) u2[r] /= n2;
+  const double u3[3] = {u1[1] * u2[2] - u1[2] * u2[1], u1[2] * u2[0] - u1[0] * u2[2],
+                        u1[0] * u2[1] - u1[1] * u2[0]};
+  const double v3[3] = {v1[1] * v2[2] - v1[2] * v2[1], v1[2] * v2[0] - v1[0] * v2[2],
+                        v1[0] * v2[1] - v1[1] * v2[0]};
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) R[3 * r + c] = u1[r] * v1[c] + u2[r] * v2[c] + u3[r] * v3[c];
+  return true;
+}
+
+// FP64 on this GPU has long dependent latencies (about 64 cycles per DFMA and
+// over 600 per division or square root), and the rigid fit is one thread's
+// dependency chain on the iteration's critical path. So the chain avoids FP64
+// division and square root: reciprocals are an FP32 seed refined by two
+// Newton steps in FP64 (r <- r + r (1 - d r), 24 -> 48 -> 53 bits), and sums
+// are pairwise.
+__device__ __forceinline__ double rcp64(double d) {
+  double r = (double)__frcp_rn((float)d);
+  r = fma(r, fma(-d, r, 1.0), r);
+  r = fma(r, fma(-d, r, 1.0), r);
+  return r;
+}
+
+__device__ __forceinline__ double sum9(const double v[9]) {
+  return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
+}
+
+// Orthogonal polar factor of C by Newton's iteration X <- (X + X^{-T}) / 2
+// (Higham), started from a positive multiple of C. For det C > 0 the limit is
+// U V^T of C = U S V^T, i.e. Eq. 14's rotation (sgn det(U V^T) = +1). The
+// iteration runs on one thread and is the tail of every iteration of
+// Algorithm 2, so its dependent chain matters: the first, scaled steps
+// X <- (g X + X^{-T} / g) / 2, g = (|X^{-1}|_F / |X|_F)^{1/2} (any g > 0 keeps
+// the limit), run in FP32 until the iterate is within about 1e-6 of U V^T;
+// unscaled FP64 steps then converge quadratically to the FP64 fixed point.
+// Returns false when C is not safely positive-determinant (the caller then
+// takes the eigen-decomposition route, which also handles rank deficiency).
+template <class T>
+__device__ __forceinline__ T cof3(const T X[9], T cf[9]) {
+  cf[0] = X[4] * X[8] - X[5] * X[7];
+  cf[1] = X[5] * X[6] - X[3] * X[8];
+  cf[2] = X[3] * X[7] - X[4] * X[6];
+  cf[3] = X[2] * X[7] - X[1] * X[8];
+  cf[4] = X[0] * X[8] - X[2] * X[6];
+  cf[5] = X[1] * X[6] - X[0] * X[7];
+  cf[6] = X[1] * X[5] - X[2] * X[4];
+  cf[7] = X[2] * X[3] - X[0] * X[5];
+  cf[8] = X[0] * X[4] - X[1] * X[3];
+  return X[0] * cf[0] + X[1] * cf[1] + X[2] * cf[2];  // det X
+}
+
+static __device__ bool polar_rotation(const double C[9], double R[9]) {
+  double sq[9];
+  for (int k = 0; k < 9; ++k) sq[k] = C[k] * C[k];
+  const double nc2 = sum9(sq);
+  if (!(nc2 > 0.0) || !isfinite(nc2)) return false;
+  const double s0 = (double)rsqrtf((float)nc2);
+  // scaled steps in FP32, |X|_F ~ 1 throughout
+  float Xf[9];
+  for (int k = 0; k < 9; ++k) Xf[k] = (float)(C[k] * s0);
+  for (int it = 0; it < 40; ++it) {
+    float cf[9];
+    const float det = cof3(Xf, cf);
+    if (!(det > 1e-6f)) return false;  // near rank 2 (or det < 0): the eigen route decides
+    const float idet = 1.0f / det;
+    float xx = 0.f, ii = 0.f;
+    for (int k = 0; k < 9; ++k) {
+      cf[k] *= idet;
+      xx = fmaf(Xf[k], Xf[k], xx);
+      ii = fmaf(cf[k], cf[k], ii);
+    }
+    const float g = sqrtf(sqrtf(ii / xx));
+    const float a = 0.5f * g, b = 0.5f / g;
+    float change = 0.f;
+    for (int k = 0; k < 9; ++k) {
+      const float xn = fmaf(a, Xf[k], b * cf[k]);
+      change = fmaf(xn - Xf[k], xn - Xf[k], change);
+      Xf[k] = xn;
+    }
+    if (change < 1e-12f) break;
+  }
+  // unscaled steps in FP64 from the FP32 iterate: the error squares per step
+  double X[9];
+  for (int k = 0; k < 9; ++k) X[k] = (double)Xf[k];
+  for (int it = 0; it < 8; ++it) {
+    double cf[9];
+    const double det = cof3(X, cf);
+    if (!(det > 1e-9)) return false;
+    const double h = 0.5 * rcp64(det);
+    double dd[9];
+    for (int k = 0; k < 9; ++k) {
+      const double xn = fma(h, cf[k], 0.5 * X[k]);
+      dd[k] = (xn - X[k]) * (xn - X[k]);
+      X[k] = xn;
+    }
+    if (sum9(dd) < 1e-28) break;
+  }
+  for (int k = 0; k < 9; ++k) R[k] = X[k];
+  return true;
+}
+
+// Eq. 14 for D = 2 (clouds in a plane z = const): the rotation R' of the
+// plane maximising tr(R'^T C2) over the x, y block C2 of C, i.e. the angle
+// atan2(c21 - c12, c11 + c22), embedded as diag(R', 1). False (no unique
+// optimum: every rotation fits equally) when both arguments vanish.
+__device__ __forceinline__ bool planar_rotation(const double C[9], double R[9]) {
+  const double c11 = C[0], c12 = C[1], c21 = C[3], c22 = C[4];
+  const double p = c11 + c22, q = c21 - c12;
+  const double r = sqrt(p * p + q * q);
+  const double fro = sqrt(c11 * c11 + c12 * c12 + c21 * c21 + c22 * c22);
+  if (!(r > 1e-12 * fro)) return false;
+  const double c = p / r, s = q / r;
+  R[0] = c;
+  R[1] = -s;
+  R[2] = 0.0;
+  R[3] = s;
+  R[4] = c;
+  R[5] = 0.0;
+  R[6] = 0.0;
+  R[7] = 0.0;
+  R[8] = 1.0;
+  return true;
+}
+
+// One thread: reductions -> C -> (R', t') -> compose, convergence, next-iteration constants.
+static __device__ void rigid_step(const double* red, int64_t M, DevState* ds, const EpiParams& ep,
+                           double* traj, unsigned long long inter_add) {
+  const double Md = (double)M;
+  double ybar[3], mud[3];
+  for (int k = 0; k < 3; ++k) {
+    ybar[k] = red[k] * ep.inv_M;     // mean of the centred template (~0)
+    mud[k] = red[3 + k] * ep.inv_M;  // mean displacement
+  }
+  // symmetric S = sum yc yc^T (xx, xy, xz, yy, yz, zz) and Dy = sum d yc^T
+  const double S[9] = {red[6], red[7], red[8], red[7], red[9], red[10], red[8], red[10], red[11]};
+  double C[9];
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c)
+      C[3 * r + c] = S[3 * r + c] + red[12 + 3 * r + c] - Md * (ybar[r] + mud[r]) * ybar[c];
+  double Rp[9];
+  const bool ok = ep.dim == 2 ? planar_rotation(C, Rp) : (polar_rotation(C, Rp) || rigid_rotation(C, Rp));
+  if (!ok) {
+    for (int k = 0; k < 9; ++k) Rp[k] = (k % 4 == 0) ? 1.0 : 0.0;
+    ds->degenerate += 1;
+  }
+  // mu_Y = muf + ybar (muf is the FP32 centre the kernels subtracted)
+  double muy[3];
+  for (int k = 0; k < 3; ++k) muy[k] = (double)ds->muf[k] + ybar[k];
+  double tp[3];
+  for (int r = 0; r < 3; ++r)
+    tp[r] = muy[r] + mud[r] - (Rp[3 * r] * muy[0] + Rp[3 * r + 1] * muy[1] + Rp[3 * r + 2] * muy[2]);
+  double Rn[9], tn[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c)
+      Rn[3 * r + c] = Rp[3 * r] * ds->R[c] + Rp[3 * r + 1] * ds->R[3 + c] + Rp[3 * r + 2] * ds->R[6 + c];
+    tn[r] = Rp[3 * r] * ds->t[0] + Rp[3 * r + 1] * ds->t[1] + Rp[3 * r + 2] * ds->t[2] + tp[r];
+  }
+  double T[12];
+  for (int k = 0; k < 9; ++k) T[k] = Rn[k];
+  for (int k = 0; k < 3; ++k) T[9 + k] = tn[k];
+  const int k_it = ds->iter;
+  if (k_it >= 2) {
+    double d2 = 0;
+    for (int q = 0; q < 12; ++q) d2 += (T[q] - ds->Tm2[q]) * (T[q] - ds->Tm2[q]);
+    ds->last_conv = d2;
+    if (ep.conv_tol > 0 && d2 <= ep.conv_tol) {
+      ds->done = 1;
+      ds->converged = 1;
+    }
+  } else {
+    ds->last_conv = -1.0;
+  }
+  for (int q = 0; q < 12; ++q) {
+    ds->Tm2[q] = ds->Tm1[q];
+    ds->Tm1[q] = T[q];
+  }
+  bool finite = true;
+  for (int q = 0; q < 12; ++q) finite = finite && isfinite(T[q]);
+  if (!finite) {
+    ds->status |= 2;
+    ds->done = 1;
+  }
+  for (int k = 0; k < 9; ++k) {
+    ds->R[k] = Rn[k];
+    ds->Rf[k] = (float)Rn[k];
+  }
+  for (int k = 0; k < 3; ++k) {
+    ds->t[k] = tn[k];
+    ds->tf[k] = (float)tn[k];
+  }
+  for (int r = 0; r < 3; ++r)
+    ds->muf[r] = (float)(Rn[3 * r] * ds->mu0[0] + Rn[3 * r + 1] * ds->mu0[1] +
+                         Rn[3 * r + 2] * ds->mu0[2] + tn[r]);
+  // rigid velocity of the next iteration: v = (y_new - y_old)/dt with
+  // y_old = R'^T (y_new - t'), i.e. v = (I - R'^T)/dt y_new + R'^T t'/dt
+  const double idt = ep.inv_dt;
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c)
+      ds->A[3 * r + c] = (float)(((r == c ? 1.0 : 0.0) - Rp[3 * c + r]) * idt);
+    ds->b[r] = (float)((Rp[r] * tp[0] + Rp[3 + r] * tp[1] + Rp[6 + r] * tp[2]) * idt);
+  }
+  for (int k = 0; k < 3; ++k) {
+    ds->netF[k] = red[21 + k];
+    ds->torque[k] = red[24 + k];
+  }
+  if (traj && k_it < ep.max_traj)
+    for (int q = 0; q < 12; ++q) traj[12 * (int64_t)k_it + q] = T[q];
+  ds->interactions += inter_add;
+  ds->iter = k_it + 1;
+  if (ep.max_iter > 0 && k_it + 1 >= ep.max_iter) ds->done = 1;
+}
+
+
+// ------------------------------------------------------------------ epilogue stages
+constexpr int EPI_BS = 256;  // threads per epilogue block
+
+struct EpiCtx {
+  Xf xf;
+  float mu[3];      // FP32 centre subtracted from the template points
+  float A[9], b[3]; // rigid-velocity coefficients (velocity_mode RIGID)
+};
+
+__device__ __forceinline__ EpiCtx load_epi(const DevState* __restrict__ ds) {
+  EpiCtx c;
+  c.xf = load_xf(ds);
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    c.mu[k] = ds->muf[k];
+    c.b[k] = ds->b[k];
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) c.A[k] = ds->A[k];
+  return c;
+}
+
+// Template point i: a = G * (compensated sum of the S force partials);
+// Eq. 9 with the dissipative force of Eq. 7, v' = v + dt (a - eta v / m_Y);
+// Eq. 10, d = dt v'. Adds the point's 27 reduction terms to r: centred
+// position yc, d, yc yc^T (6), d yc^T (9), force m_Y a, torque yc x m_Y a.
+// `live`: bit s set for the slots to add (all S slots when no mask is kept);
+// the others are exact zeros, and adding a zero never changes a compensated
+// sum, so the result is the same as adding all S slots in order.
+__device__ __forceinline__ void epi_point(int64_t i, const float4* __restrict__ Y0,
+                                          const float4* __restrict__ hi, const float4* __restrict__ lo,
+                                          int S, int64_t M, float4* __restrict__ V,
+                                          const EpiParams& ep, const EpiCtx& c, float (&r)[NRED],
+                                          unsigned long long live = ~0ull) {
+  const float4 y0 = Y0[i];
+  const float3 y = place(c.xf, y0);
+  const float cx = y.x - c.mu[0], cy = y.y - c.mu[1], cz = y.z - c.mu[2];
+  float ahx = 0.f, ahy = 0.f, ahz = 0.f, alx = 0.f, aly = 0.f, alz = 0.f;
+  if (S <= 64 && live != ~0ull) {
+    unsigned long long rest = live & (S == 64 ? ~0ull : ((1ull << S) - 1ull));
+    while (rest) {
+      // up to four slots in flight, then the same in-order compensated sum
+      int sl[4];
+      int nk = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        sl[k] = rest ? __ffsll((long long)rest) - 1 : -1;
+        if (rest) {
+          rest &= rest - 1ull;
+          ++nk;
+        }
+      }
+      float4 h[4], l[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        h[k] = sl[k] >= 0 ? hi[(int64_t)sl[k] * M + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        l[k] = sl[k] >= 0 ? lo[(int64_t)sl[k] * M + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        comp_add(ahx, alx, h[k].x);
+        comp_add(ahy, aly, h[k].y);
+        comp_add(ahz, alz, h[k].z);
+        alx += l[k].x;
+        aly += l[k].y;
+        alz += l[k].z;
+      }
+      (void)nk;
+    }
+  } else {
+    for (int s = 0; s < S; s += 4) {
+      // four independent loads in flight, then the same in-order compensated sum
+      float4 h[4], l[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const bool ok = s + k < S;
+        h[k] = ok ? hi[(int64_t)(s + k) * M + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        l[k] = ok ? lo[(int64_t)(s + k) * M + i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        comp_add(ahx, alx, h[k].x);
+        comp_add(ahy, aly, h[k].y);
+        comp_add(ahz, alz, h[k].z);
+        alx += l[k].x;
+        aly += l[k].y;
+        alz += l[k].z;
+      }
+    }
+  }
+  const float ax = ep.G * (ahx + alx), ay = ep.G * (ahy + aly), az = ep.G * (ahz + alz);
+  float vx, vy, vz;
+  if (ep.vmode == FGA_VEL_RIGID) {
+    vx = fmaf(c.A[0], y.x, fmaf(c.A[1], y.y, fmaf(c.A[2], y.z, c.b[0])));
+    vy = fmaf(c.A[3], y.x, fmaf(c.A[4], y.y, fmaf(c.A[5], y.z, c.b[1])));
+    vz = fmaf(c.A[6], y.x, fmaf(c.A[7], y.y, fmaf(c.A[8], y.z, c.b[2])));
+  } else {
+    const float4 v = V[i];
+    vx = v.x;
+    vy = v.y;
+    vz = v.z;
+  }
+  const float kd = ep.eta / y0.w;
+  vx = vx + ep.dt * (ax - kd * vx);
+  vy = vy + ep.dt * (ay - kd * vy);
+  vz = vz + ep.dt * (az - kd * vz);
+  if (ep.vmode != FGA_VEL_RIGID) V[i] = make_float4(vx, vy, vz, 0.f);
+  const float dx = ep.dt * vx, dy = ep.dt * vy, dz = ep.dt * vz;
+  const float fx = y0.w * ax, fy = y0.w * ay, fz = y0.w * az;
+  r[0] += cx; r[1] += cy; r[2] += cz;
+  r[3] += dx; r[4] += dy; r[5] += dz;
+  r[6] += cx * cx; r[7] += cx * cy; r[8] += cx * cz;
+  r[9] += cy * cy; r[10] += cy * cz; r[11] += cz * cz;
+  r[12] += dx * cx; r[13] += dx * cy; r[14] += dx * cz;
+  r[15] += dy * cx; r[16] += dy * cy; r[17] += dy * cz;
+  r[18] += dz * cx; r[19] += dz * cy; r[20] += dz * cz;
+  r[21] += fx; r[22] += fy; r[23] += fz;
+  r[24] += cy * fz - cz * fy;
+  r[25] += cz * fx - cx * fz;
+  r[26] += cx * fy - cy * fx;
+}
+
+// Block partial of r: FP32 within each warp (a few dozen terms), FP64 across
+// the block's warps in a fixed order; NRED doubles written to out. Every
+// thread of the block must call it.
+__device__ __forceinline__ void epi_block_partial(float (&r)[NRED], double* __restrict__ out) {
+  __shared__ double s_w[EPI_BS / 32][NRED];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NRED; ++k)
+    for (int off = 16; off > 0; off >>= 1) r[k] += __shfl_down_sync(FULL, r[k], off);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < NRED; ++k) s_w[w][k] = (double)r[k];
+  __syncthreads();
+  if (threadIdx.x < NRED) {
+    double acc = 0;
+    for (int ww = 0; ww < EPI_BS / 32; ++ww) acc += s_w[ww][threadIdx.x];
+    out[threadIdx.x] = acc;
+  }
+}
+
+// FP64 sum of nblocks x NRED partials in a fixed order, by the whole block:
+// thread t < 8 NRED adds value t % NRED over blocks t / NRED, + 8, ...;
+// NRED threads then add the 8 strands into s_red (shared, NRED doubles).
+// FP64 adds are scarce on this GPU, so no FP64 warp shuffles are used.
+__device__ __forceinline__ void epi_last_reduce(const double* partials, int nblocks, double* s_red) {
+  __shared__ double s_strand[8][NRED];
+  if (threadIdx.x < 8 * NRED) {
+    const int k = threadIdx.x % NRED, j = threadIdx.x / NRED;
+    double acc = 0.0;
+    for (int b = j; b < nblocks; b += 8) acc += __ldcg(&partials[(int64_t)b * NRED + k]);
+    s_strand[j][k] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x < NRED) {
+    double acc = 0.0;
+    for (int j = 0; j < 8; ++j) acc += s_strand[j][threadIdx.x];
+    s_red[threadIdx.x] = acc;
+  }
+  __syncthreads();
+}
+
+}  // namespace fga

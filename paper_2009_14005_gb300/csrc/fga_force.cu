@@ -11,6 +11,7 @@
 #include <cmath>
 
 #include "fga_device.cuh"
+#include "fga_epi.cuh"
 
 namespace fga {
 
