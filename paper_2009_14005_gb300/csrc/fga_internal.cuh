@@ -71,10 +71,10 @@ struct DevState {
   int iter;               // iterations completed
   int done;               // stop: convergence, non-finite fit or iteration limit
   int converged;          // the convergence test fired
-  int status;             // bit 1: non-finite fit (bit 0 unused: the BH walk's stack is bounded)
+  int status;             // bit 1: non-finite fit (bit 0 unused)
   int degenerate;         // rigid fits with rank(C) < 2
-  unsigned bh_next;       // BH traversal: next 32-point group to hand out
-  unsigned bh_exited;     // BH traversal: warps that found no group left
+  unsigned bh_next;       // BH traversal: next task slot to hand out
+  unsigned bh_exited;     // BH traversal: warps that found no task left
 };
 
 // Number of FP64 reduction values per block: sum y_c (3), sum d (3),
