@@ -323,6 +323,29 @@ def lib_params(fga, a):
                                  "uniform": fga.FGA_MASS_UNIFORM}[w["masses"]], lattice=16, profile=1)
 
 
+def cpu_single_thread(pair, a, iters: int = 20):
+    """The oracle's rate on one core (the all-pairs sphere workload's second
+    CPU figure), on `iters` iterations of the same pair."""
+    import oracle
+    oracle.build()
+    before = oracle.max_threads()
+    oracle.set_threads(1)
+    try:
+        i, t, _ = cpu_sample(pair, a, iters)
+    finally:
+        oracle.set_threads(before)
+    return {"value": i / t, "unit": "interactions/s", "cores": 1,
+            "sample": "%d of %d iterations on one core (%.2f s)" % (iters, workload(a)["iters"], t)}
+
+
+def direct_equivalent(pair_terms: float, t_ms: float):
+    """All-pairs-equivalent rate of a Barnes-Hut run, labelled as such: N * M
+    pairs per iteration, as if every pair were summed exactly, over the same
+    time. The metric itself counts only the terms Barnes-Hut evaluates."""
+    return {"value": pair_terms / (t_ms / 1e3) if t_ms > 0 else None, "unit": "pair-interactions/s",
+            "note": "all-pairs equivalent (N * M per iteration); Barnes-Hut evaluates fewer terms"}
+
+
 def cpu_sample(pair, a, iters):
     """The FP64 oracle on one pair for `iters` iterations (bounded sample).
 
@@ -404,7 +427,7 @@ def run_ours(a):
     torch.cuda.synchronize()
     clocks.start()
     launches0 = fga.fga_launch_count()
-    step_ms, inter, force_ms, force_launches = [], 0, 0.0, 0
+    step_ms, inter, force_ms, force_launches, pair_terms = [], 0, 0.0, 0, 0
     for k in range(a.steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -418,12 +441,14 @@ def run_ours(a):
         inter += st["interactions"]
         force_ms += st["force_ms"]
         force_launches += st["force_launches"]
+        pair_terms += int(Xd.shape[0]) * int(Yd.shape[0]) * st["iterations"]
     torch.cuda.synchronize()
     barrier(world)
     launches = fga.fga_launch_count() - launches0
     clk = clocks.stop()
     t_local = sum(step_ms)
     t_max, inter_all = reduce_max_sum(t_local, float(inter), world)
+    _, pair_terms_all = reduce_max_sum(t_local, float(pair_terms), world)
     value = inter_all / (t_max / 1e3)
 
     # end to end through the same C call with pinned host inputs
@@ -469,6 +494,8 @@ def run_ours(a):
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_tmax / max(a.e2e_steps, 1)},
             "gpu_launches": launches, "roofline": roof, "clocks": clk}
+    if workload(a)["method"] == "bh":
+        line["direct_equivalent"] = direct_equivalent(pair_terms_all, t_max)
     if world == 1 and not a.no_cpu_baseline:
         i, t, cores = cpu_sample(pairs[0], a, a.cpu_iters)
         line["cpu_baseline"] = {"value": i / t, "unit": "interactions/s", "cores": cores,
@@ -477,6 +504,8 @@ def run_ours(a):
                                           "%d of %d iterations on the first %dk x %dk pair (%.1f s)"
                                           % (a.cpu_iters, workload(a)["iters"], workload(a)["n"] // 1000,
                                              workload(a)["n"] // 1000, t)}
+        if a.workload == "sphere-direct":
+            line["cpu_baseline"]["single_thread"] = cpu_single_thread(pairs[0], a)
     print(json.dumps(line), flush=True)
     return 0
 

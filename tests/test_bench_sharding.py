@@ -45,3 +45,21 @@ def test_two_rank_sharding_and_reduction():
     for _, _, t, u in out:
         assert t == pytest.approx(20.0)
         assert u == pytest.approx(201.0)
+
+
+def test_direct_equivalent_is_labelled():
+    import bench
+    d = bench.direct_equivalent(2e12, 500.0)
+    assert d["value"] == pytest.approx(4e12) and "equivalent" in d["note"]
+    assert bench.direct_equivalent(1.0, 0.0)["value"] is None
+
+
+def test_cpu_single_thread_sample_on_the_sphere_workload():
+    import bench
+    import oracle
+    a = bench.parse_args(["--workload", "sphere-direct"])
+    pair = bench.make_pairs([1000], a)[0]
+    before = oracle.max_threads()
+    d = bench.cpu_single_thread(pair, a, iters=2)
+    assert d["cores"] == 1 and d["value"] > 0
+    assert oracle.max_threads() == before
