@@ -338,6 +338,26 @@ def cpu_single_thread(pair, a, iters: int = 20):
             "sample": "%d of %d iterations on one core (%.2f s)" % (iters, workload(a)["iters"], t)}
 
 
+def cpu_direct_sample(pair, a, m_sample: int = 4096):
+    """The oracle's all-pairs force (Eq. 6, FP64) for the first `m_sample`
+    template points against the whole normalised reference, one evaluation:
+    the CPU rate of the all-pairs sum on a Barnes-Hut workload, labelled as a
+    subsample."""
+    import oracle
+    oracle.build()
+    X, Y, _, _ = pair
+    Xn, Yn, _ = oracle.normalize(X, Y)
+    Ys = Yn[:m_sample]
+    w = workload(a)
+    mX = np.full(len(Xn), 1.0 / len(Xn))
+    t0 = time.perf_counter()
+    oracle.direct_acc(Xn, mX, Ys, w["G"], w["eps"])
+    t = time.perf_counter() - t0
+    return {"value": len(Xn) * len(Ys) / t, "unit": "interactions/s", "cores": oracle.max_threads(),
+            "sample": "all-pairs force of %d template points against all %d reference points, one "
+                      "evaluation (%.2f s)" % (len(Ys), len(Xn), t)}
+
+
 def direct_equivalent(pair_terms: float, t_ms: float):
     """All-pairs-equivalent rate of a Barnes-Hut run, labelled as such: N * M
     pairs per iteration, as if every pair were summed exactly, over the same
@@ -506,6 +526,8 @@ def run_ours(a):
                                              workload(a)["n"] // 1000, t)}
         if a.workload == "sphere-direct":
             line["cpu_baseline"]["single_thread"] = cpu_single_thread(pairs[0], a)
+        if workload(a)["method"] == "bh":
+            line["cpu_baseline"]["direct_subsample"] = cpu_direct_sample(pairs[0], a)
     print(json.dumps(line), flush=True)
     return 0
 

@@ -63,3 +63,11 @@ def test_cpu_single_thread_sample_on_the_sphere_workload():
     d = bench.cpu_single_thread(pair, a, iters=2)
     assert d["cores"] == 1 and d["value"] > 0
     assert oracle.max_threads() == before
+
+
+def test_cpu_direct_subsample_on_a_barnes_hut_workload():
+    import bench
+    a = bench.parse_args(["--workload", "lidar-bh", "--n", "3000"])
+    pair = bench.make_pairs([1000], a)[0]
+    d = bench.cpu_direct_sample(pair, a, m_sample=256)
+    assert d["value"] > 0 and "256 template points" in d["sample"]
