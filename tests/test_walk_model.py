@@ -79,3 +79,94 @@ def test_stackless_walk_takes_bhforce_terms(orc, name, theta):
         np.testing.assert_allclose(a, a_o[i], rtol=1e-11, atol=1e-12 * np.abs(a_o[i]).max())
     if theta == 0.0:
         assert np.all(c_o == len(X))
+
+
+def _records_with_counts(eo, X, m):
+    com, mass, l2, skip = _records(eo, X, m)
+    # child count of each record: > 0 for cells, -1 single particle, -nb for a
+    # leaf of nb >= 2 particles (whose particle records follow it)
+    n = len(eo["depth"])
+    nchild = np.bincount(eo["parent"][1:], minlength=n)
+    counts = []
+    for k in range(n):
+        if eo["is_leaf"][k]:
+            counts.append(-int(eo["npts"][k]))
+            if eo["npts"][k] >= 2:
+                counts.extend([-1] * int(eo["npts"][k]))
+        else:
+            counts.append(int(nchild[k]))
+    return com, mass, l2, skip, np.array(counts)
+
+
+def _coop_walk(rec, Y, theta, eps):
+    """One walk for a group of points: a record is judged by the points that
+    rejected all its ancestors (a mask per pending sibling range). A range is
+    (next record, records left); the next sibling is a subtree size further."""
+    com, mass, l2, skip, cnt = rec
+    P = len(Y)
+    acc = np.zeros((P, 3))
+    terms = np.zeros(P, dtype=np.int64)
+    v, left, mask = 0, 1, np.ones(P, bool)
+    saved, most = [], 0
+    while left > 0:
+        d = com[v] - Y
+        r2 = (d * d).sum(1)
+        accept = mask & (l2[v] < theta * theta * r2)
+        acc[accept] += (mass[v] * d[accept]) / ((r2[accept] + eps * eps) ** 1.5)[:, None]
+        terms += accept
+        rej = mask & ~accept
+        nv, nleft = v + skip[v], left - 1
+        if rej.any() and cnt[v] > 0:
+            if nleft > 0:
+                saved.append((nv, nleft, mask))
+                most = max(most, len(saved))
+            v, left, mask = v + 1, int(cnt[v]), rej
+        else:
+            if rej.any() and cnt[v] < -1:
+                for b in range(1, -cnt[v] + 1):
+                    db = com[v + b] - Y[rej]
+                    rb = (db * db).sum(1)
+                    acc[rej] += mass[v + b] * db / ((rb + eps * eps) ** 1.5)[:, None]
+                terms[rej] += -cnt[v]
+            v, left = nv, nleft
+        if left == 0 and saved:
+            v, left, mask = saved.pop()
+    return acc, terms, most
+
+
+@pytest.mark.parametrize("name", ["gauss", "dups", "shallow"])
+@pytest.mark.parametrize("theta", [0.0, 0.5, 0.9])
+def test_cooperative_walk_takes_each_points_bhforce_terms(orc, name, theta):
+    X, m, depth = _clouds()[name]
+    tree = orc.Tree(X, m, max_depth=depth)
+    rec = _records_with_counts(tree.export(), X, m)
+    rng = np.random.default_rng(6)
+    # a group of spatial neighbours plus a few stragglers
+    c = X[rng.integers(len(X))]
+    near = X[np.argsort(((X - c) ** 2).sum(1))[:40]] + rng.normal(scale=0.01, size=(40, 3))
+    Y = np.vstack([near, rng.uniform(X.min(0), X.max(0), size=(24, 3))])
+    a_o, c_o = tree.bh_acc(Y, 1.0, 0.1, theta)
+    a, terms, most = _coop_walk(rec, Y, theta, 0.1)
+    np.testing.assert_array_equal(terms, c_o)
+    np.testing.assert_allclose(a, a_o, rtol=1e-11, atol=1e-12 * np.abs(a_o).max())
+    assert most <= 20  # at most one saved range per tree level below the root
+
+
+def test_saved_ranges_stay_within_the_depth_bound(orc):
+    # a chain of ever-closer pairs drives the tree to its depth limit
+    pts = [[0.0, 0.0, 0.0], [1.0, 1.0, 1.0]]
+    for k in range(1, 24):
+        s = 0.5 ** k
+        pts += [[s, s, s], [s * 0.9, s * 1.1, s * 0.7]]
+    X = np.array(pts)
+    m = np.ones(len(X))
+    tree = orc.Tree(X, m, max_depth=20)
+    eo = tree.export()
+    assert eo["depth"].max() == 20
+    rec = _records_with_counts(eo, X, m)
+    Y = X[:8] + 1e-9
+    a_o, c_o = tree.bh_acc(Y, 1.0, 0.1, 0.0)
+    a, terms, most = _coop_walk(rec, Y, 0.0, 0.1)
+    np.testing.assert_array_equal(terms, c_o)
+    # the GPU walk keeps saved range k in lane k's registers: 32 lanes, 20 levels
+    assert 15 <= most <= 20
