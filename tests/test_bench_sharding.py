@@ -71,3 +71,16 @@ def test_cpu_direct_subsample_on_a_barnes_hut_workload():
     pair = bench.make_pairs([1000], a)[0]
     d = bench.cpu_direct_sample(pair, a, m_sample=256)
     assert d["value"] > 0 and "256 template points" in d["sample"]
+
+
+@pytest.mark.parametrize("name", ["lidar-bh", "sphere-direct", "planar-direct", "planar-bh", "batch",
+                                  "grid", "serve"])
+def test_every_workload_has_a_named_config(name):
+    import json
+    import bench
+    a = bench.parse_args(["--workload", name])
+    cfg = bench.workload_config(a)
+    assert isinstance(cfg.get("workload"), str) and cfg["workload"]
+    json.dumps(cfg)  # serialisable as part of the bench line
+    w = bench.workload(a)
+    assert w["iters"] > 0 and w["n"] > 0
