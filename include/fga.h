@@ -193,7 +193,8 @@ typedef struct fga_tree fga_tree;
  * child's). Only p->max_depth is read from `p`.
  * X: device (N x 3), mX: device (N) or NULL for masses 1/N. The tree keeps its
  * own copy of the bodies; X and mX may be freed once the stream has passed.
- * Errors: FGA_EINVAL (N <= 0, bad depth, non-finite X), FGA_ENOMEM, FGA_ECUDA. */
+ * N <= 2^26 (checked before any device work).
+ * Errors: FGA_EINVAL (N <= 0 or N > 2^26, bad depth, non-finite X), FGA_ENOMEM, FGA_ECUDA. */
 int fga_tree_build(const float* X, const float* mX, int64_t N, const fga_params* p,
                    fga_tree** out, void* stream);
 void fga_tree_destroy(fga_tree* t);
@@ -305,6 +306,8 @@ void fga_state_destroy(fga_state* s);
  * X, Y, mX, mY may be host or device pointers (detected per pointer); host
  * inputs are copied to the device inside the call. Synchronises `stream`.
  * stats (host, optional) receives the counters and the normalised-frame result.
+ * Sizes: 1 <= N, M <= 2^30; with a tree (FGA_BH, or FGA_AUTO above the
+ * crossover) N <= 2^26.
  * Errors: FGA_EINVAL, FGA_ENOMEM, FGA_ECUDA, FGA_EDEGENERATE (R, t still set). */
 int fga_register(const float* X, int64_t N, const float* Y, int64_t M, const float* mX,
                  const float* mY, const fga_params* p, double R_out[9], double t_out[3],

@@ -417,8 +417,8 @@ int fga_tree_build(const float* X, const float* mX, int64_t N, const fga_params*
                    void* stream) {
   clear_error();
   cudaStream_t s = (cudaStream_t)stream;
-  if (!out || !X || N <= 0 || N > (int64_t)1 << 30 || !p || p->max_depth < 1 || p->max_depth > 20) {
-    set_error("fga_tree_build: bad arguments");
+  if (!out || !X || N <= 0 || N > (int64_t)1 << 26 || !p || p->max_depth < 1 || p->max_depth > 20) {
+    set_error("fga_tree_build: bad arguments (1 <= N <= 2^26, max_depth 1..20)");
     return FGA_EINVAL;
   }
   *out = nullptr;

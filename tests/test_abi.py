@@ -79,3 +79,15 @@ def test_bad_walk_is_rejected_without_gpu_work(fga):
                                 None, None)
     assert code == fga.FGA_EINVAL
     assert "bh_walk" in fga.lib.fga_last_error().decode()
+
+
+def test_sizes_above_the_limits_are_rejected_without_gpu_work(fga):
+    X = np.zeros((8, 3), dtype=np.float32)
+    R, t = (ctypes.c_double * 9)(), (ctypes.c_double * 3)()
+    p = fga.params()
+    code = fga.lib.fga_register(X.ctypes.data, (1 << 30) + 1, X.ctypes.data, 8, None, None,
+                                ctypes.byref(p), R, t, None, None)
+    assert code == fga.FGA_EINVAL
+    out = ctypes.c_void_p()
+    code = fga.lib.fga_tree_build(X.ctypes.data, None, (1 << 26) + 1, ctypes.byref(p), ctypes.byref(out), None)
+    assert code == fga.FGA_EINVAL and "2^26" in fga.lib.fga_last_error().decode()
