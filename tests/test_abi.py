@@ -91,3 +91,28 @@ def test_sizes_above_the_limits_are_rejected_without_gpu_work(fga):
     out = ctypes.c_void_p()
     code = fga.lib.fga_tree_build(X.ctypes.data, None, (1 << 26) + 1, ctypes.byref(p), ctypes.byref(out), None)
     assert code == fga.FGA_EINVAL and "2^26" in fga.lib.fga_last_error().decode()
+
+
+def test_batch_masses_and_forces_reject_bad_arguments_without_gpu_work(fga):
+    X = np.zeros((64, 3), dtype=np.float32)
+    res = (fga.fga_pair_result * 2)()
+    good = fga.fga_pair(X.ctypes.data, 64, X.ctypes.data, 64, None, None, None)
+    big = fga.fga_pair(X.ctypes.data, (1 << 26) + 1, X.ctypes.data, 64, None, None, None)
+    bad_p = fga.params(bh_walk=9)
+    per_pair = fga.fga_pair(X.ctypes.data, 64, X.ctypes.data, 64, None, None, ctypes.addressof(bad_p))
+    p = fga.params()
+    for pairs, needle in (([good, big], "pair 1"), ([per_pair, good], "pair 0")):
+        arr = (fga.fga_pair * 2)(*pairs)
+        code = fga.lib.fga_register_batch(arr, 2, ctypes.byref(p), res, None, None)
+        assert code == fga.FGA_EINVAL and needle in fga.lib.fga_last_error().decode()
+    out = np.zeros(64, dtype=np.float32)
+    for mode, lattice, total in ((fga.FGA_MASS_NIV, 0, 1.0), (fga.FGA_MASS_KNN, 12, 1.0),
+                                 (fga.FGA_MASS_UNIFORM, 16, 0.0), (7, 16, 1.0)):
+        code = fga.lib.fga_masses(X.ctypes.data, 64, mode, lattice, -5.0, 5.0, total, out.ctypes.data, None)
+        assert code == fga.FGA_EINVAL
+    acc = np.zeros((64, 3), dtype=np.float32)
+    for kw in (dict(eps=0.0), dict(theta=-1.0)):
+        q = fga.params(**kw)
+        code = fga.lib.fga_forces(None, X.ctypes.data, None, 64, X.ctypes.data, None, 64, ctypes.byref(q),
+                                  acc.ctypes.data, None, None)
+        assert code == fga.FGA_EINVAL
