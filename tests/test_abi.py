@@ -116,3 +116,22 @@ def test_batch_masses_and_forces_reject_bad_arguments_without_gpu_work(fga):
         code = fga.lib.fga_forces(None, X.ctypes.data, None, 64, X.ctypes.data, None, 64, ctypes.byref(q),
                                   acc.ctypes.data, None, None)
         assert code == fga.FGA_EINVAL
+
+
+def test_host_tables_round_trip(fga):
+    # the all-pairs tile table and the FGA_AUTO crossover are host state
+    saved = [fga.get_direct_tile(c) for c in range(3)]
+    old_n = fga.fga_direct_max_n(0)
+    try:
+        for c, (bs, q) in enumerate([(128, 4), (256, 1), (256, 2)]):
+            fga.set_direct_tile(c, bs, q)
+            assert fga.get_direct_tile(c) == (bs, q)
+        for bad in ((3, 128, 2), (0, 64, 2), (1, 256, 3), (-1, 128, 1)):
+            with pytest.raises(fga.FGAError):
+                fga.set_direct_tile(*bad)
+        assert fga.get_direct_tile(0) == (128, 4)  # a rejected call changes nothing
+        assert fga.fga_direct_max_n(12345) == old_n and fga.fga_direct_max_n(0) == 12345
+    finally:
+        for c, (bs, q) in enumerate(saved):
+            fga.set_direct_tile(c, bs, q)
+        fga.fga_direct_max_n(old_n)
