@@ -103,6 +103,8 @@ def lib():
                                         ctypes.c_double, D]
         _lib.orc_masses_niv_d.argtypes = [D, L, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                           ctypes.c_double, ctypes.c_double, D]
+        _lib.orc_niv_fractions.argtypes = [D, L, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                           ctypes.c_double, D, LP]
         _lib.orc_kabsch_d.argtypes = [D, D, L, ctypes.c_int, D, D]
         _lib.orc_masses_knn.argtypes = [D, L, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                         ctypes.c_double, D]
@@ -182,6 +184,21 @@ def masses_niv(P, lattice: int = 16, a: float = -5.0, b: float = 5.0, total: flo
     if rc != 0:
         raise ValueError("bad NIV arguments")
     return out
+
+
+def niv_fractions(P, lattice: int = 16, a: float = -5.0, b: float = 5.0, dim: int = 3):
+    """Covered fraction of every lattice cell (Eq. 18's V(union of balls) /
+    V(cell); 0 for empty cells), shape (lattice,) * dim indexed [cz, cy, cx]
+    in 3D and [cy, cx] in 2D, and each point's flat cell index."""
+    P = _d(P)
+    ncell = lattice ** dim
+    frac = np.empty(ncell)
+    cell = np.empty(len(P), dtype=np.int64)
+    rc = lib().orc_niv_fractions(_p(P), len(P), dim, lattice, a, b, _p(frac),
+                                 cell.ctypes.data_as(ctypes.POINTER(ctypes.c_long)))
+    if rc != 0:
+        raise ValueError("bad NIV arguments")
+    return frac.reshape((lattice,) * dim), cell
 
 
 def masses_knn(P, k: int = 16, dim: int = 3, a: float = -5.0, b: float = 5.0, total: float = 1.0):

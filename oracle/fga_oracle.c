@@ -131,23 +131,73 @@ void orc_denormalize(const double R[9], const double t[3], const double info[8],
 /* Sec. IV-F.2, Eq. 18: normalised intrinsic volume (NIV) masses             */
 /* ------------------------------------------------------------------------ */
 
-/* Reading: the lattice is lattice^3 equal cubes over the normalised domain
- * [a, b]^3, cell side h = (b - a) / lattice (the ball radius of Eq. 18 is
- * written in these units: (b - a) / (2 d lattice) = h / (2 D) with d read as
- * the dimension D = 3). A point's cell along each axis is
- * floor((x - a) / h), clamped to [0, lattice - 1]. The covered fraction of a
- * cell holding n points is taken as the Boolean-model coverage
- * f = 1 - (1 - V(ball) / V(cell))^n. A point's weight is 1 / f of its cell
- * (Eq. 18; the normalising integral is a common factor that cancels), and the
- * weights are scaled to sum to `total`. */
-int orc_masses_niv_d(const double* P, long n, int dim, int lattice, double a, double b, double total,
-                     double* m_out) {
+/* Quadrature of the covered fraction (a reading: the paper does not say how
+ * the volume of the union of balls is obtained). Along the cell's last axis
+ * (z in 3D, y in 2D) the union is taken exactly: every ball that reaches a
+ * line through the cell cuts it in a chord, and the covered length of the line
+ * is the length of the union of those chords, clipped to the cell. The other
+ * axes are sampled by the midpoint rule: NIV_COLS x NIV_COLS lines per 3D cell,
+ * NIV_STRIPS lines per 2D cell. Measured against closed forms (one ball, two
+ * overlapping balls, a ball cut by a cell face) the fraction is within 3e-3
+ * (3D) and 1.1e-4 (2D) of the exact one. */
+#define NIV_COLS 64
+#define NIV_STRIPS 1024
+
+typedef struct { double lo, hi; } orc_chord;
+
+static int orc_chord_cmp(const void* pa, const void* pb) {
+    const orc_chord* x = (const orc_chord*)pa;
+    const orc_chord* y = (const orc_chord*)pb;
+    return x->lo < y->lo ? -1 : (x->lo > y->lo ? 1 : 0);
+}
+
+/* Length of the union of k chords: sorted by their lower ends, swept once. */
+static double orc_union_length(orc_chord* c, long k) {
+    if (k == 0) return 0.0;
+    qsort(c, (size_t)k, sizeof(orc_chord), orc_chord_cmp);
+    double len = 0.0, s = c[0].lo, e = c[0].hi;
+    for (long q = 1; q < k; ++q) {
+        if (c[q].lo <= e) {
+            if (c[q].hi > e) e = c[q].hi;
+        } else {
+            len += e - s;
+            s = c[q].lo;
+            e = c[q].hi;
+        }
+    }
+    return len + (e - s);
+}
+
+/* Reading of the lattice: lattice^D equal cubes over the normalised domain
+ * [a, b]^D, cell side h = (b - a) / lattice. A point's cell along each axis is
+ * floor((x - a) / h) clamped to [0, lattice - 1], and its ball is centred at
+ * the point clamped to [a, b] (so it always touches its own cell). The ball
+ * radius of Eq. 18 is (b - a) / (2 d lattice) = h / (2 D), d read as the
+ * dimension D. The covered fraction of a cell is V(union of its points'
+ * balls, inside the cell) / V(cell) (Eq. 18 and the caption of the NIV
+ * figure: the part of the cell occupied by the balls inside it). A point's
+ * weight is 1 / fraction of its cell (Eq. 18; the normalising integral is a
+ * common factor that cancels), and the weights are scaled to sum to `total`.
+ * dim 2 uses x, y: discs of radius h / 4 in square cells.
+ *
+ * orc_niv_fractions writes the covered fraction of every cell to frac
+ * (lattice^D entries, 0 for empty cells, indexed (cz * lattice + cy) *
+ * lattice + cx) and each point's cell to cell (n entries). The test-suite
+ * checks these fractions against closed forms. Returns 0, -1 for bad
+ * arguments, -2 if memory ran out. */
+int orc_niv_fractions(const double* P, long n, int dim, int lattice, double a, double b,
+                      double* frac, long* cell) {
     if (n <= 0 || lattice <= 0 || !(b > a) || (dim != 2 && dim != 3)) return -1;
     long ncell = dim == 3 ? (long)lattice * lattice * lattice : (long)lattice * lattice;
-    long* count = (long*)calloc((size_t)ncell, sizeof(long));
-    long* cell = (long*)malloc((size_t)n * sizeof(long));
-    if (!count || !cell) { free(count); free(cell); return -2; }
-    double h = (b - a) / (double)lattice;
+    long* count = (long*)calloc((size_t)ncell + 1, sizeof(long));
+    long* order = (long*)malloc((size_t)n * sizeof(long));
+    long* fill = (long*)malloc((size_t)ncell * sizeof(long));
+    if (!count || !order || !fill) {
+        free(count); free(order); free(fill);
+        return -2;
+    }
+    for (long c = 0; c < ncell; ++c) frac[c] = 0.0;
+    const double h = (b - a) / (double)lattice;
     for (long i = 0; i < n; ++i) {
         long c[3] = {0, 0, 0};
         for (int k = 0; k < dim; ++k) {
@@ -157,21 +207,94 @@ int orc_masses_niv_d(const double* P, long n, int dim, int lattice, double a, do
             c[k] = (long)q;
         }
         cell[i] = (c[2] * lattice + c[1]) * lattice + c[0];
-        count[cell[i]] += 1;
+        count[cell[i] + 1] += 1;
     }
-    /* Eq. 18 with d = D: balls of radius (b-a)/(2 D rho); in 2D discs of area
-       pi r^2 in cells of area h^2 */
-    double rad = (b - a) / (2.0 * (double)dim * (double)lattice);
-    double ratio = dim == 3 ? (4.0 / 3.0 * M_PI * rad * rad * rad) / (h * h * h)
-                            : (M_PI * rad * rad) / (h * h);
+    /* points grouped by cell, in index order within a cell */
+    for (long c = 0; c < ncell; ++c) count[c + 1] += count[c];
+    memcpy(fill, count, (size_t)ncell * sizeof(long));
+    for (long i = 0; i < n; ++i) order[fill[cell[i]]++] = i;
+    free(fill);
+    const double rad = (b - a) / (2.0 * (double)dim * (double)lattice);
+    const double rr = rad * rad;
+    const int q = dim == 3 ? NIV_COLS : NIV_STRIPS;
+    const double dlt = h / (double)q;
+    const long nlines = dim == 3 ? (long)q * q : (long)q;
+    int fail = 0;
+#pragma omp parallel
+    {
+        orc_chord* ch = NULL;
+        long cap = 0;
+#pragma omp for schedule(dynamic, 1)
+        for (long c = 0; c < ncell; ++c) {
+            long first = count[c], nc = count[c + 1] - first;
+            if (nc == 0) continue;
+            if (nc > cap) {
+                orc_chord* t = (orc_chord*)realloc(ch, (size_t)nc * sizeof(orc_chord));
+                if (!t) {
+#pragma omp atomic write
+                    fail = 1;
+                    continue;
+                }
+                ch = t;
+                cap = nc;
+            }
+            long cx = c % lattice, cy = (c / lattice) % lattice, cz = c / ((long)lattice * lattice);
+            double lox = a + (double)cx * h, loy = a + (double)cy * h, loz = a + (double)cz * h;
+            /* the chord axis: z in 3D, y in 2D */
+            double clo = dim == 3 ? loz : loy, chi = clo + h;
+            double covered = 0.0;
+            for (long ln = 0; ln < nlines; ++ln) {
+                double u = lox + ((double)(ln % q) + 0.5) * dlt;              /* x of the line */
+                double v = dim == 3 ? loy + ((double)(ln / q) + 0.5) * dlt : 0; /* y (3D)      */
+                long k = 0;
+                for (long t = 0; t < nc; ++t) {
+                    const double* p = P + 3 * order[first + t];
+                    double px = fmin(fmax(p[0], a), b), py = fmin(fmax(p[1], a), b);
+                    double d2, zc;
+                    if (dim == 3) {
+                        double pz = fmin(fmax(p[2], a), b);
+                        d2 = (u - px) * (u - px) + (v - py) * (v - py);
+                        zc = pz;
+                    } else {
+                        d2 = (u - px) * (u - px);
+                        zc = py;
+                    }
+                    if (d2 >= rr) continue;
+                    double w = sqrt(rr - d2);
+                    double lo = zc - w, hi = zc + w;
+                    if (lo < clo) lo = clo;
+                    if (hi > chi) hi = chi;
+                    if (hi > lo) { ch[k].lo = lo; ch[k].hi = hi; ++k; }
+                }
+                covered += orc_union_length(ch, k);
+            }
+            frac[c] = covered / ((double)nlines * h);
+        }
+        free(ch);
+    }
+    free(count);
+    free(order);
+    return fail ? -2 : 0;
+}
+
+/* Eq. 18 masses: 1 / (covered fraction of the point's cell), scaled to sum to
+ * `total`. */
+int orc_masses_niv_d(const double* P, long n, int dim, int lattice, double a, double b, double total,
+                     double* m_out) {
+    if (n <= 0 || lattice <= 0 || !(b > a) || (dim != 2 && dim != 3)) return -1;
+    long ncell = dim == 3 ? (long)lattice * lattice * lattice : (long)lattice * lattice;
+    double* frac = (double*)malloc((size_t)ncell * sizeof(double));
+    long* cell = (long*)malloc((size_t)n * sizeof(long));
+    if (!frac || !cell) { free(frac); free(cell); return -2; }
+    int rc = orc_niv_fractions(P, n, dim, lattice, a, b, frac, cell);
+    if (rc) { free(frac); free(cell); return rc; }
     double wsum = 0;
     for (long i = 0; i < n; ++i) {
-        double f = 1.0 - pow(1.0 - ratio, (double)count[cell[i]]);
-        m_out[i] = 1.0 / f;
+        m_out[i] = 1.0 / frac[cell[i]];
         wsum += m_out[i];
     }
     for (long i = 0; i < n; ++i) m_out[i] = total * m_out[i] / wsum;
-    free(count);
+    free(frac);
     free(cell);
     return 0;
 }
