@@ -827,9 +827,12 @@ static double det3(const double A[9]) {
 /* Given template points Y and displacements D (both M x 3): mu_Y, mu_YD are the
  * means of Y and Y + D; C = Y^_D^T Y^ with both sets centred (Eq. 14 text);
  * C = U S V^T; R = U diag(1, 1, sgn det(U V^T)) V^T (Eq. 14); t = mu_YD - R mu_Y
- * (Eq. 16). Reading: if the second singular value is below 1e-12 of the first
- * (collinear template), no rotation is determined: R = I, t = mu_YD - mu_Y,
- * and the return value is 1 instead of 0. */
+ * (Eq. 16). Reading: if the second singular value is not above 1e-7 of the
+ * first (a collinear or nearly collinear template), no rotation is
+ * determined: R = I, t = mu_YD - mu_Y, and the return value is 1 instead of
+ * 0. The bound is where an FP64 eigen-decomposition of C^T C (eigenvalues
+ * sigma^2) can still tell sigma_2 from rounding: sigma_2^2 / sigma_1^2 =
+ * 1e-14 is a few hundred units of the last place of sigma_1^2. */
 /* Eq. 14 for D = 2 (clouds in the plane z = 0): the 2 x 2 cross-covariance
  * C = sum (y + d - mu_YD)(y - mu_Y)^T of the x, y components, its SVD
  * C = U S V^T by one Jacobi rotation (the textbook 2 x 2 case), and
@@ -903,7 +906,7 @@ int orc_kabsch_d(const double* Y, const double* D, long M, int dim, double R[9],
     }
     if (dim == 2) {
         /* R set by kabsch2 */
-    } else if (!(s[1] > 1e-12 * s[0])) {
+    } else if (!(s[1] > 1e-7 * s[0])) {
         for (int i = 0; i < 9; ++i) R[i] = (i % 4 == 0) ? 1.0 : 0.0;
         status = 1;
     } else {

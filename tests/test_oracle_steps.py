@@ -146,6 +146,18 @@ def test_collinear_template_is_degenerate(orc):
     np.testing.assert_allclose(t, D.mean(0), atol=1e-14)
 
 
+def test_degenerate_bound_is_sigma2_1e7_sigma1(orc):
+    # C = diag(4, 4 e^2, 0) exactly (orthogonal, centred x and y columns, D = 0):
+    # sigma_2 / sigma_1 = e^2. A ratio of 1e-9 is degenerate, 1e-6 is not.
+    x = np.array([1.0, -1.0, 1.0, -1.0])
+    y = np.array([1.0, 1.0, -1.0, -1.0])
+    for ratio, status in [(1e-9, 1), (1e-11, 1), (1e-6, 0), (1e-3, 0)]:
+        Y = np.column_stack([x, np.sqrt(ratio) * y, np.zeros(4)])
+        R, t, st = orc.kabsch(Y, np.zeros_like(Y))
+        assert st == status, ratio
+        np.testing.assert_allclose(R, np.eye(3), atol=1e-12)
+
+
 # --------------------------------------------------------------------------- Appendix A
 
 def test_normalisation_range_and_centres(orc):
