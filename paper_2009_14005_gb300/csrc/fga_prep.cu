@@ -5,6 +5,8 @@
 #include <algorithm>
 #include <cfloat>
 
+#include <math_constants.h>
+
 #include "fga_internal.cuh"
 
 namespace fga {
@@ -226,19 +228,176 @@ __global__ void k_niv_count(const float* __restrict__ p, int64_t n, double a, do
     atomicAdd(&counts[niv_cell(p, i, a, h, L, dim)], 1u);
 }
 
-// Per cell: w = 1 / (1 - (1 - ratio)^count) (0 for empty cells); per-block sums of count * w.
-__global__ void k_niv_cellw(const unsigned* __restrict__ counts, int64_t ncell, double ratio,
-                            double* __restrict__ w, double* __restrict__ part) {
-  double v[1] = {0};
-  for (int64_t c = blockIdx.x * (int64_t)RB + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * RB) {
-    unsigned n = counts[c];
-    double wc = 0;
-    if (n) {
-      wc = 1.0 / (1.0 - pow(1.0 - ratio, (double)n));
-      v[0] += (double)n * wc;
-    }
-    w[c] = wc;
+// Eq. 18's covered fraction of a lattice cell, V(union of the balls of its
+// points, inside the cell) / V(cell). The union is measured exactly along the
+// cell's last axis (z in 3D, y in 2D) on NIV_COLS x NIV_COLS lines per 3D cell
+// (NIV_STRIPS lines per 2D cell) placed at the midpoints of a regular grid
+// across that axis: each ball that reaches a line cuts a chord, and the line
+// contributes the length of the union of its chords inside the cell. The
+// fraction is the mean covered length over the lines, divided by h. Ball
+// centres are the points clamped to [a, b]; the radius is h / (2 D).
+constexpr int NIV_COLS = 64, NIV_STRIPS = 1024, NIV_ZBITS = 10;
+
+template <int DIM>
+struct NivShape {
+  static constexpr int Q = DIM == 3 ? NIV_COLS : NIV_STRIPS;
+  static constexpr int LINES = DIM == 3 ? Q * Q : Q;
+  static constexpr int TILES = LINES / 32;  // one warp task = 32 lines of one cell
+};
+
+// Sort key of point i: its cell above NIV_ZBITS bits of its position along
+// the chord axis inside the cell, so that a cell's points are contiguous and
+// ordered along the chords (the union below is exact in any order; this order
+// lets one pass over the points follow a chain of overlapping chords).
+__global__ void k_niv_key(const float* __restrict__ p, int64_t n, double a, double b, double h, int L,
+                          int dim, unsigned* __restrict__ counts, unsigned long long* __restrict__ keys,
+                          int* __restrict__ vals) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = niv_cell(p, i, a, h, L, dim);
+    atomicAdd(&counts[c], 1u);
+    const int ca = dim == 3 ? c / (L * L) : (c / L) % L;  // cell index along the chord axis
+    const double zc = fmin(fmax((double)p[3 * i + dim - 1], a), b);
+    double q = floor((zc - __dadd_rn(a, __dmul_rn((double)ca, h))) / h * (double)(1 << NIV_ZBITS));
+    q = fmin(fmax(q, 0.0), (double)((1 << NIV_ZBITS) - 1));
+    keys[i] = ((unsigned long long)c << NIV_ZBITS) | (unsigned long long)q;
+    vals[i] = (int)i;
   }
+}
+
+__global__ void k_niv_flag(const unsigned* __restrict__ counts, int64_t ncell, unsigned* __restrict__ flag) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
+       c += (int64_t)gridDim.x * blockDim.x)
+    flag[c] = counts[c] ? 1u : 0u;
+}
+
+// list[rank] = cell for every non-empty cell (rank = exclusive scan of the flags).
+__global__ void k_niv_list(const unsigned* __restrict__ counts, const unsigned* __restrict__ rank,
+                           int64_t ncell, unsigned* __restrict__ list) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < ncell;
+       c += (int64_t)gridDim.x * blockDim.x)
+    if (counts[c]) list[rank[c]] = (unsigned)c;
+}
+
+// Clamped ball centres in sorted order: (x, y, z, 0).
+__global__ void k_niv_gather(const float* __restrict__ p, const int* __restrict__ order, int64_t n,
+                             float a, float b, float4* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = order[i];
+    out[i] = make_float4(fminf(fmaxf(p[3 * j], a), b), fminf(fmaxf(p[3 * j + 1], a), b),
+                         fminf(fmaxf(p[3 * j + 2], a), b), 0.f);
+  }
+}
+
+// One warp per (non-empty cell, 32 lines) for the cells of ranks [r0, r1);
+// each lane measures one line.
+// Covered length of a line: starting from the cell's lower face s, repeated
+// passes over the cell's points extend the reach e over every chord with
+// lo <= e; a pass that extends nothing ends the component [s, e] and yields the
+// lowest chord start above e, where the next component begins. Components are
+// added in increasing order, as a sorted sweep would add them, and every
+// endpoint is a chord end, so the length of the union does not depend on the
+// order of the points. An FP32 distance test with a 1 % margin skips points
+// that cannot reach the line; the chord itself is FP64 with explicitly
+// rounded products (no contraction), the same arithmetic as a plain sweep.
+// part[task] = sum over the warp's 32 lines, task = (rank - r0) * tiles + tile.
+template <int DIM>
+__global__ void __launch_bounds__(256) k_niv_cover(const float4* __restrict__ pts,
+                                                   const unsigned* __restrict__ offs,
+                                                   const unsigned* __restrict__ counts,
+                                                   const unsigned* __restrict__ list,
+                                                   const unsigned* __restrict__ nnz, int64_t r0,
+                                                   int64_t r1, int L, double a, double h, double rr,
+                                                   double* __restrict__ part) {
+  using S = NivShape<DIM>;
+  const int lane = threadIdx.x & 31;
+  const int64_t rend = r1 < (int64_t)(*nnz) ? r1 : (int64_t)(*nnz);
+  const int64_t ntask = rend > r0 ? (rend - r0) * S::TILES : 0;
+  const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const double dlt = h / (double)S::Q;
+  const float rrf = (float)(rr * 1.01);
+  for (int64_t task = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; task < ntask;
+       task += nwarp) {
+    const unsigned c = list[r0 + task / S::TILES];
+    const int ln = (int)(task % S::TILES) * 32 + lane;
+    const unsigned first = offs[c], nc = counts[c];
+    const int cx = (int)(c % (unsigned)L), cy = (int)((c / (unsigned)L) % (unsigned)L);
+    const int cz = DIM == 3 ? (int)(c / ((unsigned)L * (unsigned)L)) : 0;
+    const double lox = __dadd_rn(a, __dmul_rn((double)cx, h));
+    const double loy = __dadd_rn(a, __dmul_rn((double)cy, h));
+    const double u = __dadd_rn(lox, __dmul_rn((double)(ln % S::Q) + 0.5, dlt));
+    const double v = DIM == 3 ? __dadd_rn(loy, __dmul_rn((double)(ln / S::Q) + 0.5, dlt)) : 0.0;
+    const double clo = DIM == 3 ? __dadd_rn(a, __dmul_rn((double)cz, h)) : loy;
+    const double chi = clo + h;
+    const float uf = (float)u, vf = (float)v;
+    double s = clo, total = 0.0;
+    for (;;) {
+      double e = s, nxt;
+      bool grew;
+      do {
+        grew = false;
+        nxt = CUDART_INF;
+        for (unsigned t = 0; t < nc; ++t) {
+          const float4 q = pts[first + t];
+          const float dxf = uf - q.x;
+          float d2f = dxf * dxf;
+          if (DIM == 3) {
+            const float dyf = vf - q.y;
+            d2f = __fadd_rn(d2f, __fmul_rn(dyf, dyf));
+          }
+          if (d2f >= rrf) continue;
+          const double dx = u - (double)q.x;
+          double d2 = __dmul_rn(dx, dx);
+          if (DIM == 3) {
+            const double dy = v - (double)q.y;
+            d2 = __dadd_rn(d2, __dmul_rn(dy, dy));
+          }
+          if (d2 >= rr) continue;
+          const double w = sqrt(rr - d2);
+          const double zc = DIM == 3 ? (double)q.z : (double)q.y;
+          const double lo = fmax(zc - w, clo), hi = fmin(zc + w, chi);
+          if (!(hi > lo)) continue;
+          if (lo <= e) {
+            if (hi > e) {
+              e = hi;
+              grew = true;
+            }
+          } else {
+            nxt = fmin(nxt, lo);
+          }
+        }
+      } while (grew);
+      total += e - s;
+      if (nxt == CUDART_INF) break;
+      s = nxt;
+    }
+    for (int off = 16; off > 0; off >>= 1) total += __shfl_down_sync(FULL, total, off);
+    if (lane == 0) part[task] = total;
+  }
+}
+
+// Non-empty cells of ranks [r0, r1): fraction = (sum of the cell's tiles, in
+// tile order) / (lines * h), weight w = 1 / fraction.
+__global__ void k_niv_cellw(const unsigned* __restrict__ list, const unsigned* __restrict__ nnz,
+                            int64_t r0, int64_t r1, const double* __restrict__ cover, int tiles,
+                            int lines, double h, double* __restrict__ w) {
+  const int64_t rend = r1 < (int64_t)(*nnz) ? r1 : (int64_t)(*nnz);
+  for (int64_t r = r0 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < rend;
+       r += (int64_t)gridDim.x * blockDim.x) {
+    double sum = 0.0;
+    for (int t = 0; t < tiles; ++t) sum += cover[(r - r0) * tiles + t];
+    const double frac = sum / ((double)lines * h);
+    w[list[r]] = frac > 0.0 ? 1.0 / frac : 0.0;
+  }
+}
+
+// Per-block sums of count * w over the non-empty cells.
+__global__ void k_niv_wsum(const unsigned* __restrict__ counts, int64_t ncell,
+                           const double* __restrict__ w, double* __restrict__ part) {
+  double v[1] = {0};
+  for (int64_t c = blockIdx.x * (int64_t)RB + threadIdx.x; c < ncell; c += (int64_t)gridDim.x * RB)
+    if (counts[c]) v[0] += (double)counts[c] * w[c];
   block_sum<1>(v);
   if (threadIdx.x == 0) part[blockIdx.x] = v[0];
 }
@@ -350,29 +509,79 @@ int masses_device(const float* pts, int64_t n, int mode, int lattice, float a, f
   const double h = ((double)b - (double)a) / (double)L;
   // Eq. 18 with d = D: balls of radius (b-a)/(2 D rho); discs for D = 2
   const double rad = ((double)b - (double)a) / (2.0 * (double)dim * (double)L);
-  const double ratio = dim == 2 ? (M_PI * rad * rad) / (h * h)
-                                : (4.0 / 3.0 * M_PI * rad * rad * rad) / (h * h * h);
+  const double rr = rad * rad;
+  const int tiles = dim == 2 ? NivShape<2>::TILES : NivShape<3>::TILES;
+  const int lines = dim == 2 ? NivShape<2>::LINES : NivShape<3>::LINES;
+  int cell_bits = 1;
+  while (cell_bits < 40 && ((int64_t)1 << cell_bits) < ncell) ++cell_bits;
   const int gc = red_grid(ncell);
-  unsigned* counts = nullptr;
-  double* w = nullptr;
-  int rc = dev_alloc_n(&counts, (size_t)ncell, s);
-  if (rc) return rc;
-  rc = dev_alloc_n(&w, (size_t)ncell + gc + 1, s);
-  if (rc) return rc;
-  double* part = w + ncell;
-  double* wsum = part + gc;
+  // non-empty cells are measured in chunks of at most NIV_CHUNK cells, so the
+  // per-task sums stay small whatever the lattice
+  constexpr int64_t NIV_CHUNK = 32768;
+  const int64_t cells_max = std::min<int64_t>(n, ncell);
+  const int64_t chunk = std::min<int64_t>(cells_max, NIV_CHUNK);
+  unsigned* u32 = nullptr;        // counts, offs, flags, ranks, list, nnz
+  unsigned long long* keys = nullptr;
+  int* vals = nullptr;
+  float4* centres = nullptr;
+  double* dbl = nullptr;          // w (ncell), cover (chunk * tiles), part (gc), wsum
+  int rc = dev_alloc_n(&u32, (size_t)5 * ncell + 1, s);
+  if (!rc) rc = dev_alloc_n(&keys, (size_t)2 * n, s);
+  if (!rc) rc = dev_alloc_n(&vals, (size_t)2 * n, s);
+  if (!rc) rc = dev_alloc_n(&centres, (size_t)n, s);
+  if (!rc) rc = dev_alloc_n(&dbl, (size_t)ncell + chunk * tiles + gc + 1, s);
+  if (rc) {
+    dev_free(u32, s);
+    dev_free(keys, s);
+    dev_free(vals, s);
+    dev_free(centres, s);
+    dev_free(dbl, s);
+    return rc;
+  }
+  unsigned *counts = u32, *offs = u32 + ncell, *flag = u32 + 2 * ncell, *rank = u32 + 3 * ncell;
+  unsigned *list = u32 + 4 * ncell, *nnz = u32 + 5 * ncell;
+  double *w = dbl, *cover = dbl + ncell, *part = cover + chunk * tiles, *wsum = part + gc;
   FGA_CUDA_TRY(cudaMemsetAsync(counts, 0, sizeof(unsigned) * ncell, s));
-  k_niv_count<<<red_grid(n), RB, 0, s>>>(pts, n, (double)a, h, L, dim, counts);
-  FGA_LAUNCH_CHECK("niv_count");
-  k_niv_cellw<<<gc, RB, 0, s>>>(counts, ncell, ratio, w, part);
-  FGA_LAUNCH_CHECK("niv_cellw");
-  k_sum_parts<<<1, RB, 0, s>>>(part, gc, wsum);
-  FGA_LAUNCH_CHECK("niv_wsum");
-  k_niv_assign<<<red_grid(n), RB, 0, s>>>(pts, n, (double)a, h, L, dim, w, wsum, total, out);
-  FGA_LAUNCH_CHECK("niv_assign");
-  dev_free(counts, s);
-  dev_free(w, s);
-  return FGA_OK;
+  k_niv_key<<<red_grid(n), RB, 0, s>>>(pts, n, (double)a, (double)b, h, L, dim, counts, keys, vals);
+  FGA_LAUNCH_CHECK("niv_key");
+  rc = radix_sort_pairs(keys, vals, keys + n, vals + n, n, cell_bits + NIV_ZBITS, s);
+  if (!rc) rc = scan_exclusive(counts, offs, ncell, nullptr, s);
+  if (!rc) {
+    k_niv_flag<<<gc, RB, 0, s>>>(counts, ncell, flag);
+    FGA_LAUNCH_CHECK("niv_flag");
+    rc = scan_exclusive(flag, rank, ncell, nnz, s);
+  }
+  if (!rc) {
+    k_niv_list<<<gc, RB, 0, s>>>(counts, rank, ncell, list);
+    FGA_LAUNCH_CHECK("niv_list");
+    k_niv_gather<<<red_grid(n), RB, 0, s>>>(pts, vals, n, a, b, centres);
+    FGA_LAUNCH_CHECK("niv_gather");
+    const unsigned gcov = (unsigned)(8 * sm_count());
+    for (int64_t r0 = 0; r0 < cells_max; r0 += chunk) {
+      const int64_t r1 = std::min<int64_t>(r0 + chunk, cells_max);
+      if (dim == 2)
+        k_niv_cover<2><<<gcov, 256, 0, s>>>(centres, offs, counts, list, nnz, r0, r1, L, (double)a, h,
+                                            rr, cover);
+      else
+        k_niv_cover<3><<<gcov, 256, 0, s>>>(centres, offs, counts, list, nnz, r0, r1, L, (double)a, h,
+                                            rr, cover);
+      FGA_LAUNCH_CHECK("niv_cover");
+      k_niv_cellw<<<red_grid(r1 - r0), RB, 0, s>>>(list, nnz, r0, r1, cover, tiles, lines, h, w);
+      FGA_LAUNCH_CHECK("niv_cellw");
+    }
+    k_niv_wsum<<<gc, RB, 0, s>>>(counts, ncell, w, part);
+    FGA_LAUNCH_CHECK("niv_wsum_blocks");
+    k_sum_parts<<<1, RB, 0, s>>>(part, gc, wsum);
+    FGA_LAUNCH_CHECK("niv_wsum");
+    k_niv_assign<<<red_grid(n), RB, 0, s>>>(pts, n, (double)a, h, L, dim, w, wsum, total, out);
+    FGA_LAUNCH_CHECK("niv_assign");
+  }
+  dev_free(u32, s);
+  dev_free(keys, s);
+  dev_free(vals, s);
+  dev_free(centres, s);
+  dev_free(dbl, s);
+  return rc;
 }
 
 __global__ void k_sum1(const float* __restrict__ m, int64_t n, double* __restrict__ part) {
