@@ -1,12 +1,15 @@
 #!/usr/bin/env python
 """Benchmark of FGA registration on GB300 (one JSON line on stdout).
 
-Workload: two 120k-point LiDAR-like sweeps (64 rings, ground plane + box
-obstacles, 1/r^2 density fall-off, ~50 % overlap, sigma = 0.02 m), NIV masses
-(lattice 16), Barnes-Hut with theta = 0.5, 200 iterations of Algorithm 2,
-FP32 forces with FP64 reductions. One step = one whole registration
-(normalisation, masses, tree build, 200 iterations, de-normalisation) of one
-pair whose inputs are already resident in device memory.
+Default workload: large inhomogeneous clouds, N = M = 1M points sampled
+independently from seeded piecewise-planar scenes (8-16 rectangles, 10x
+density variation, 5 % uniform outliers, sigma = 0.01), uniform masses,
+Barnes-Hut with theta = 0.5, 100 iterations of Algorithm 2, FP32 forces with
+FP64 reductions and rigid fit. One step = one whole registration
+(normalisation, masses, tree build, 100 iterations, de-normalisation) of one
+pair whose inputs are already resident in device memory. The same line
+carries the theta = 0.3 and 0.7 registrations and the tiled all-pairs sum on
+the same pairs (a few steps each), as extra keys.
 
 Metric: pair-interactions/s = force terms evaluated (accepted cells + leaf
 particles, counted on the device) per second of registration time; the line
@@ -14,9 +17,12 @@ also carries registrations/s and p50/p99 latency. ``e2e`` repeats the
 measurement through the same C call with pinned HOST inputs (host->device
 copies and the result read-back inside the timed region).
 
+Other workloads (``--workload``): the 120k LiDAR-like sweeps (Barnes-Hut,
+16-NN masses), the 1k sphere and 262k planar all-pairs cases, the 256-pair
+batch, the parameter grid and the served Poisson trace.
+
 ``--impl reference`` times the FP64 CPU oracle on the same workload (each step
-a bounded sample: one iteration of the loop on the full pair) on the host
-cores.
+a bounded sample of it) on the host cores.
 
 Multi-GPU (torchrun): every rank registers its own pairs (no collective on the
 data path); the timing is the max over ranks, the value the sum over ranks.
@@ -52,19 +58,25 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="lidar-bh")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="planar-bh")
     ap.add_argument("--n", type=int, default=None, help="points per cloud (workload default)")
     ap.add_argument("--iters", type=int, default=None, help="iterations (workload default)")
     ap.add_argument("--theta", type=float, default=None, help="BH opening parameter")
     ap.add_argument("--pairs", type=int, default=2, help="distinct seeded pairs per rank")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--masses", choices=["default", "niv16", "knn16", "uniform"], default="default",
-                    help="reference masses: the workload's default (NIV lattice 16 for LiDAR), the NIV "
-                         "lattice, inverse density from the 16th nearest neighbour, or uniform")
+                    help="reference masses: the workload's default (16-NN for LiDAR, else uniform), the "
+                         "NIV lattice, inverse density from the 16th nearest neighbour, or uniform")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-iters", type=int, default=24,
-                    help="oracle iterations in the CPU baseline's sample (about 10 s on 16 cores for "
-                         "the LiDAR workload)")
+    ap.add_argument("--cpu-iters", type=int, default=None,
+                    help="oracle iterations in the CPU baseline's sample (workload default: about "
+                         "10-30 s on 16 cores)")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="planar-bh: skip the theta 0.3 / 0.7 and all-pairs runs")
+    ap.add_argument("--sweep-steps", type=int, default=2,
+                    help="timed registrations per extra theta (and all-pairs) run")
+    ap.add_argument("--walk", type=int, default=0,
+                    help="Barnes-Hut walk (fga_params.bh_walk; 0 = by template size)")
     return ap.parse_args(argv)
 
 
@@ -193,8 +205,8 @@ WORKLOADS = {
     # the headline configuration: LiDAR-like sweeps, Barnes-Hut
     # (G = 1 from the paper's parameter range: with 66.7 the trajectory on this
     # cloud is chaotic, so no FP32 run can track the FP64 one)
-    "lidar-bh": dict(gen="lidar", n=120_000, iters=200, method="bh", theta=0.5, niv=True,
-                     G=1.0, eps=0.2, eta=0.2),
+    "lidar-bh": dict(gen="lidar", n=120_000, iters=200, method="bh", theta=0.5, niv=False,
+                     masses="knn16", G=1.0, eps=0.2, eta=0.2, cpu_iters=24),
     # 1k x 1k points on the unit sphere, all-pairs sum
     "sphere-direct": dict(gen="sphere", n=1000, iters=100, method="direct", theta=0.5, niv=False,
                           G=66.7, eps=0.05, eta=0.1),
@@ -203,7 +215,7 @@ WORKLOADS = {
                           G=66.7, eps=0.2, eta=0.2),
     # large piecewise-planar scenes, Barnes-Hut
     "planar-bh": dict(gen="planar", n=1_000_000, iters=100, method="bh", theta=0.5, niv=False,
-                      G=66.7, eps=0.2, eta=0.2),
+                      G=66.7, eps=0.2, eta=0.2, cpu_iters=1, ref_template=131_072),
     # many independent pairs (N, M log-uniform in [500, 50k], sphere and planar
     # shapes, rotations <= 60 deg), all-pairs or Barnes-Hut per pair by size,
     # one graph-captured loop per step; n = number of pairs
@@ -228,8 +240,13 @@ def workload(a):
         if v is not None:
             w[k] = v
     masses = getattr(a, "masses", "default")
-    w["masses"] = ("niv16" if w["niv"] else "uniform") if masses == "default" else masses
+    if masses == "default":
+        masses = w.get("masses", "niv16" if w["niv"] else "uniform")
+    w["masses"] = masses
     w["niv"] = w["masses"] == "niv16"
+    if getattr(a, "cpu_iters", None) is not None:
+        w["cpu_iters"] = a.cpu_iters
+    w.setdefault("cpu_iters", 24)
     return w
 
 
@@ -320,7 +337,8 @@ def lib_params(fga, a):
     return fga.params(method={"bh": fga.FGA_BH, "direct": fga.FGA_DIRECT, "auto": fga.FGA_AUTO}[w["method"]],
                       theta=w["theta"], max_iter=w["iters"], G=w["G"], eps=w["eps"], eta=w["eta"],
                       mass_mode={"niv16": fga.FGA_MASS_NIV, "knn16": fga.FGA_MASS_KNN,
-                                 "uniform": fga.FGA_MASS_UNIFORM}[w["masses"]], lattice=16, profile=1)
+                                 "uniform": fga.FGA_MASS_UNIFORM}[w["masses"]], lattice=16, profile=1,
+                      bh_walk=getattr(a, "walk", 0))
 
 
 def cpu_single_thread(pair, a, iters: int = 20):
@@ -395,7 +413,12 @@ def run_reference(a):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
+    w = workload(a)
     pair = make_pairs(shard_seeds(0, 1, 1), a)[0]
+    m_ref = w.get("ref_template")
+    if m_ref and w["gen"] not in ("batch", "serve", "grid"):
+        X, Y, R, t = pair
+        pair = (X, Y[:m_ref], R, t)
     for _ in range(a.warmup):
         cpu_sample(pair, a, 1)
     total_i, total_t, cores = 0, 0.0, 1
@@ -404,9 +427,14 @@ def run_reference(a):
         total_i += i
         total_t += t
     value = total_i / total_t
-    sample = ("FP64 C oracle, Algorithm 2 with BHForce: normalisation, NIV masses, tree and ONE "
-              "iteration of the loop on the full %d x %d pair per step" % (workload(a)["n"],
-                                                                           workload(a)["n"]))
+    if w["gen"] in ("batch", "serve", "grid"):
+        what = "the workload's first pair"
+    else:
+        what = "the %d x %d pair" % (len(pair[0]), len(pair[1])) + (
+            " (the first %d template points of the %d)" % (m_ref, w["n"]) if m_ref else "")
+    sample = ("FP64 C oracle, Algorithm 2 (%s): normalisation, %s masses, %sand ONE iteration of the "
+              "loop on %s per step" % ("BHForce" if w["method"] == "bh" else "all-pairs sum / BHForce by size",
+                                       w["masses"], "tree " if w["method"] != "direct" else "", what))
     line = {"impl": "reference", "metric": "pair-interactions/s", "value": value,
             "unit": "interactions/s", "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1e3 * total_t / a.steps, "higher_is_better": True, "scaling": "weak",
@@ -417,6 +445,63 @@ def run_reference(a):
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def time_registrations(fga, dev, p, steps, flush, stream, offset=0, gts=None):
+    """`steps` whole registrations on device-resident pairs, each bracketed by
+    CUDA events on the launch stream, the L2 flushed before each (outside the
+    events). Returns per-step ms, the summed counters and, with `gts` (ground
+    truth (R, t, bbox diagonal) per pair), each result's error against it."""
+    import torch
+    import oracle
+    out = dict(step_ms=[], inter=0, force_ms=0.0, force_launches=0, pair_terms=0, gt_rot=[], gt_t=[])
+    for k in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        Xd, Yd = dev[(k + offset) % len(dev)]
+        e0.record(stream)
+        R, t, st = fga.fga_register(Xd, Yd, p, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        out["step_ms"].append(e0.elapsed_time(e1))
+        out["inter"] += st["interactions"]
+        out["force_ms"] += st["force_ms"]
+        out["force_launches"] += st["force_launches"]
+        out["pair_terms"] += int(Xd.shape[0]) * int(Yd.shape[0]) * st["iterations"]
+        if gts is not None:
+            Rg, tg, diag = gts[(k + offset) % len(dev)]
+            out["gt_rot"].append(oracle.rotation_error_deg(R, Rg))
+            out["gt_t"].append(float(np.linalg.norm(np.asarray(t) - tg)) / diag)
+    return out
+
+
+def gt_summary(m):
+    """Ground-truth error of the timed registrations (the synthetic pairs carry
+    the motion that generated them)."""
+    if not m["gt_rot"]:
+        return None
+    return {"rot_deg_median": float(np.median(m["gt_rot"])), "rot_deg_max": float(np.max(m["gt_rot"])),
+            "t_rel_median": float(np.median(m["gt_t"])), "t_rel_max": float(np.max(m["gt_t"])),
+            "note": "rotation (deg) and translation (/ bbox diagonal) of each timed result against the "
+                    "motion that generated the synthetic pair"}
+
+
+def roofline_of(kname, inter, force_ms, force_launches, t_local, peaks, peak_src, sms, summary):
+    """FP32-issue roofline of the dominant force kernel from its CUDA-event launch times."""
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_rate = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / FP32_INSTR_PER_INTERACTION
+    launch_inter = inter / max(force_launches, 1)
+    launch_s = force_ms / 1e3 / max(force_launches, 1)
+    achieved = launch_inter / launch_s if launch_s > 0 else 0.0
+    return {"bound": "alu", "kernel": kname, "achieved": achieved / 1e9, "peak": peak_rate / 1e9,
+            "unit": "Ginteractions/s", "frac": achieved / peak_rate,
+            "traffic": recorded_traffic("paper_2009_14005_gb300/csrc/fga_force.cu", summary),
+            "peak_source": "%d SMs x %d FP32 lanes x %.0f MHz (sm_max_mhz, %s) / %d FP32 "
+                           "instructions per interaction" % (sms, FP32_LANES_PER_SM, sm_mhz, peak_src,
+                                                             FP32_INSTR_PER_INTERACTION),
+            "launches": force_launches, "interactions_per_launch": launch_inter,
+            "mean_launch_ms": 1e3 * launch_s, "share_of_step": force_ms / max(t_local, 1e-9)}
 
 
 def run_ours(a):
@@ -430,9 +515,12 @@ def run_ours(a):
     __graft_entry__.build_library()
     import paper_2009_14005_gb300 as fga
 
+    w = workload(a)
     pairs = make_pairs(shard_seeds(rank, world, a.pairs), a)
     dev = [(torch.as_tensor(X, device="cuda"), torch.as_tensor(Y, device="cuda")) for X, Y, _, _ in pairs]
     host = [(torch.from_numpy(X).pin_memory(), torch.from_numpy(Y).pin_memory()) for X, Y, _, _ in pairs]
+    gts = [(np.asarray(Rg), np.asarray(tg), float(np.linalg.norm(X.max(0) - X.min(0))))
+           for X, Y, Rg, tg in pairs]
     p = lib_params(fga, a)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
@@ -447,28 +535,15 @@ def run_ours(a):
     torch.cuda.synchronize()
     clocks.start()
     launches0 = fga.fga_launch_count()
-    step_ms, inter, force_ms, force_launches, pair_terms = [], 0, 0.0, 0, 0
-    for k in range(a.steps):
-        flush.zero_()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        Xd, Yd = dev[k % len(dev)]
-        e0.record(stream)
-        R, t, st = fga.fga_register(Xd, Yd, p, stream=stream)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        inter += st["interactions"]
-        force_ms += st["force_ms"]
-        force_launches += st["force_launches"]
-        pair_terms += int(Xd.shape[0]) * int(Yd.shape[0]) * st["iterations"]
+    m = time_registrations(fga, dev, p, a.steps, flush, stream, gts=gts)
     torch.cuda.synchronize()
     barrier(world)
     launches = fga.fga_launch_count() - launches0
     clk = clocks.stop()
+    step_ms = m["step_ms"]
     t_local = sum(step_ms)
-    t_max, inter_all = reduce_max_sum(t_local, float(inter), world)
-    _, pair_terms_all = reduce_max_sum(t_local, float(pair_terms), world)
+    t_max, inter_all = reduce_max_sum(t_local, float(m["inter"]), world)
+    _, pair_terms_all = reduce_max_sum(t_local, float(m["pair_terms"]), world)
     value = inter_all / (t_max / 1e3)
 
     # end to end through the same C call with pinned host inputs
@@ -484,25 +559,40 @@ def run_ours(a):
         h2d, d2h = st["h2d_bytes"], st["d2h_bytes"]
     e2e_tmax, e2e_iall = reduce_max_sum(1e3 * e2e_t, float(e2e_i), world)
 
+    # planar-bh: theta 0.3 and 0.7, and the tiled all-pairs sum, on the same pairs
+    sweep = {}
+    if a.workload == "planar-bh" and not a.no_sweep:
+        for th in (0.3, 0.7):
+            q = lib_params(fga, a)
+            q.theta = th
+            fga.fga_register(*dev[0], q)
+            s = time_registrations(fga, dev, q, a.sweep_steps, flush, stream)
+            tl = sum(s["step_ms"])
+            tm, ia = reduce_max_sum(tl, float(s["inter"]), world)
+            sweep["theta_%.1f" % th] = {
+                "value": ia / (tm / 1e3), "unit": "interactions/s", "steps": a.sweep_steps,
+                "registrations_per_s": a.sweep_steps * world / (tm / 1e3), "ms_per_step": tm / a.sweep_steps,
+                "k_bh_frac": None, "_s": s, "_tl": tl}
+        q = lib_params(fga, a)
+        q.method = fga.FGA_DIRECT
+        q.max_iter = 5
+        fga.fga_register(*dev[0], q)
+        s = time_registrations(fga, dev, q, a.sweep_steps, flush, stream)
+        tl = sum(s["step_ms"])
+        tm, ia = reduce_max_sum(tl, float(s["inter"]), world)
+        sweep["all_pairs"] = {"value": ia / (tm / 1e3), "unit": "interactions/s", "steps": a.sweep_steps,
+                              "iterations": 5, "ms_per_step": tm / a.sweep_steps,
+                              "note": "tiled all-pairs sum (Eq. 6) on the same pairs; 5 iterations per "
+                                      "registration, N * M terms per iteration",
+                              "_s": s, "_tl": tl}
+
     if rank != 0:
         return 0
     peaks, peak_src = measured_peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_rate = sms * FP32_LANES_PER_SM * sm_mhz * 1e6 / FP32_INSTR_PER_INTERACTION
-    launch_inter = inter / max(force_launches, 1)
-    launch_s = force_ms / 1e3 / max(force_launches, 1)
-    achieved = launch_inter / launch_s if launch_s > 0 else 0.0
-    kname = "k_bh" if workload(a)["method"] == "bh" else "k_direct"
-    roof = {"bound": "alu", "kernel": kname, "achieved": achieved / 1e9, "peak": peak_rate / 1e9,
-            "unit": "Ginteractions/s", "frac": achieved / peak_rate,
-            "traffic": recorded_traffic("paper_2009_14005_gb300/csrc/fga_force.cu",
-                                        "%s_%s.md" % (kname, a.workload)),
-            "peak_source": "%d SMs x %d FP32 lanes x %.0f MHz (sm_max_mhz, %s) / %d FP32 "
-                           "instructions per interaction" % (sms, FP32_LANES_PER_SM, sm_mhz, peak_src,
-                                                             FP32_INSTR_PER_INTERACTION),
-            "launches": force_launches, "interactions_per_launch": launch_inter,
-            "mean_launch_ms": 1e3 * launch_s, "share_of_step": force_ms / max(t_local, 1e-9)}
+    kname = "k_bh" if w["method"] == "bh" else "k_direct"
+    roof = roofline_of(kname, m["inter"], m["force_ms"], m["force_launches"], t_local, peaks, peak_src, sms,
+                       "%s_%s.md" % (kname, a.workload))
     line = {"metric": "pair-interactions/s", "value": value, "unit": "interactions/s",
             "n_gpus": world, "steps": a.steps, "warmup": a.warmup, "ms_per_step": t_max / a.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -513,20 +603,30 @@ def run_ours(a):
                     "unit": "interactions/s",
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "ms_per_step": e2e_tmax / max(a.e2e_steps, 1)},
-            "gpu_launches": launches, "roofline": roof, "clocks": clk}
-    if workload(a)["method"] == "bh":
+            "gpu_launches": launches, "roofline": roof, "clocks": clk,
+            "ground_truth_error": gt_summary(m)}
+    for key, v in sweep.items():
+        s, tl = v.pop("_s"), v.pop("_tl")
+        kn = "k_direct" if key == "all_pairs" else "k_bh"
+        r = roofline_of(kn, s["inter"], s["force_ms"], s["force_launches"], tl, peaks, peak_src, sms,
+                        "%s_%s.md" % (kn, "planar-direct" if key == "all_pairs" else a.workload))
+        v["roofline_frac"] = r["frac"]
+        v["mean_launch_ms"] = r["mean_launch_ms"]
+        v.pop("k_bh_frac", None)
+        line[key] = v
+    if w["method"] == "bh":
         line["direct_equivalent"] = direct_equivalent(pair_terms_all, t_max)
     if world == 1 and not a.no_cpu_baseline:
-        i, t, cores = cpu_sample(pairs[0], a, a.cpu_iters)
+        i, t, cores = cpu_sample(pairs[0], a, w["cpu_iters"])
         line["cpu_baseline"] = {"value": i / t, "unit": "interactions/s", "cores": cores,
                                 "kind": "oracle",
-                                "sample": "FP64 C oracle (OpenMP), normalisation + NIV masses + tree + "
+                                "sample": "FP64 C oracle (OpenMP), normalisation + %s masses + tree + "
                                           "%d of %d iterations on the first %dk x %dk pair (%.1f s)"
-                                          % (a.cpu_iters, workload(a)["iters"], workload(a)["n"] // 1000,
-                                             workload(a)["n"] // 1000, t)}
+                                          % (w["masses"], w["cpu_iters"], w["iters"], w["n"] // 1000,
+                                             w["n"] // 1000, t)}
         if a.workload == "sphere-direct":
             line["cpu_baseline"]["single_thread"] = cpu_single_thread(pairs[0], a)
-        if workload(a)["method"] == "bh":
+        if w["method"] == "bh":
             line["cpu_baseline"]["direct_subsample"] = cpu_direct_sample(pairs[0], a)
     print(json.dumps(line), flush=True)
     return 0
@@ -653,12 +753,12 @@ def run_ours_batch(a):
             "gpu_launches": launches, "roofline": roof, "clocks": clk,
             "autotuned": tune_summary(tuned)}
     if world == 1 and not a.no_cpu_baseline:
-        i, t, cores = cpu_sample(batches[0], a, a.cpu_iters)
+        i, t, cores = cpu_sample(batches[0], a, workload(a)["cpu_iters"])
         line["cpu_baseline"] = {"value": i / t, "unit": "interactions/s", "cores": cores,
                                 "kind": "oracle",
                                 "sample": "FP64 C oracle (OpenMP), normalisation + tree + %d of %d "
                                           "iterations on the first pair of the batch (%d x %d, %.1f s)"
-                                          % (a.cpu_iters, workload(a)["iters"], len(batches[0][0][0]),
+                                          % (workload(a)["cpu_iters"], workload(a)["iters"], len(batches[0][0][0]),
                                              len(batches[0][0][1]), t)}
     print(json.dumps(line), flush=True)
     return 0
@@ -783,11 +883,11 @@ def run_ours_grid(a):
                     "ms_per_step": e2e_tmax / max(a.e2e_steps, 1)},
             "gpu_launches": launches, "roofline": roof, "clocks": clk, "autotuned": tune_summary(tuned)}
     if world == 1 and not a.no_cpu_baseline:
-        i, t, cores = cpu_sample([(X, Y, None, None)], a, a.cpu_iters)
+        i, t, cores = cpu_sample([(X, Y, None, None)], a, w["cpu_iters"])
         line["cpu_baseline"] = {"value": i / t, "unit": "interactions/s", "cores": cores,
                                 "kind": "oracle",
                                 "sample": "FP64 C oracle (OpenMP), %d of %d iterations of one cell "
-                                          "(1000 x 1000, %.1f s)" % (a.cpu_iters, w["iters"], t)}
+                                          "(1000 x 1000, %.1f s)" % (w["cpu_iters"], w["iters"], t)}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -936,12 +1036,12 @@ def run_ours_serve(a):
             "autotuned": tune_summary(tuned)}
     if world == 1 and not a.no_cpu_baseline:
         X, Y = trace[0][1], trace[0][2]
-        i, t, cores = cpu_sample([(X, Y, None, None)], a, a.cpu_iters)
+        i, t, cores = cpu_sample([(X, Y, None, None)], a, w["cpu_iters"])
         line["cpu_baseline"] = {"value": i / t, "unit": "interactions/s", "cores": cores,
                                 "kind": "oracle",
                                 "sample": "FP64 C oracle (OpenMP), normalisation + tree + %d of %d "
                                           "iterations on the trace's first request (%d x %d, %.1f s)"
-                                          % (a.cpu_iters, w["iters"], len(X), len(Y), t)}
+                                          % (w["cpu_iters"], w["iters"], len(X), len(Y), t)}
     print(json.dumps(line), flush=True)
     return 0
 

@@ -47,6 +47,8 @@ extern "C" {
                            64-point groups to keep every resident warp busy */
 #define FGA_WALK_LANE 1
 #define FGA_WALK_COOP 2
+#define FGA_WALK_CURSOR 3   /* one walk per 64 points that follows each point's own walk */
+#define FGA_WALK_CURSOR32 4 /* the same with 32 points per warp                          */
 
 #define FGA_VEL_UNCONSTRAINED 0 /* velocities of Eq. 9 persist between iterations */
 #define FGA_VEL_RIGID 1         /* velocities replaced by the rigid motion        */
@@ -82,12 +84,15 @@ typedef struct fga_params {
                         are registered in the plane (quadtree, 2-D NIV discs,
                         the 2 x 2 rigid fit of Eq. 14), and R_out / t_out keep
                         the 3-D layout: R = diag(R2, 1), t = (t2, ~0)         */
-  int bh_walk;       /* Barnes-Hut traversal of the one-pair path (the result is
+  int bh_walk;       /* Barnes-Hut traversal of the one-pair path (every walk
+                        takes each point's own BHForce terms; the result is
                         the same up to FP32 rounding order): FGA_WALK_AUTO (0),
-                        FGA_WALK_LANE (one walk per template point) or
+                        FGA_WALK_LANE (one walk per template point),
                         FGA_WALK_COOP (one walk per 64 points, each point
-                        judging every node the walk visits); the batch and
-                        server paths always use FGA_WALK_COOP                 */
+                        judging every node the walk visits), FGA_WALK_CURSOR /
+                        FGA_WALK_CURSOR32 (one walk per 64 / 32 points that
+                        visits the union of the points' own walks, record by
+                        record)                                               */
 } fga_params;
 
 /* Fills `p` with the paper's defaults (Sec. V, parameter settings):
@@ -236,10 +241,22 @@ int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N,
                const float* mY, int64_t M, const fga_params* p, float* acc_out,
                int64_t* interactions_out, void* stream);
 
+/* BHForce (Eq. 15) on `tree` as fga_forces computes it, plus the number of
+ * terms each template point added (accepted cells + leaf particles of its
+ * own walk, in Y's order): the per-point counterpart of interactions_out,
+ * for comparing a point's walk with another implementation's. Y: device
+ * (M x 3), mY: device (M) or NULL, acc_out: device (M x 3), terms_out: device
+ * (M int32). Queues its work on `stream` without synchronising.
+ * Errors: FGA_EINVAL (no tree, sizes, eps <= 0, theta < 0), FGA_ENOMEM, FGA_ECUDA. */
+int fga_forces_terms(const fga_tree* tree, const float* Y, const float* mY, int64_t M,
+                     const fga_params* p, float* acc_out, int32_t* terms_out, void* stream);
+
 /* ----------------------------------------------------------------- no allocation */
 /* Size, in float4 (16 bytes), of the device array that fga_forces_direct_static
  * uses for all its intermediate buffers: 524288 float4 = 8 MiB. */
 #define FGA_STATIC_SCRATCH_FLOAT4 524288
+/* float4 slots the call's state block takes at the start of that array */
+#define FGA_STATIC_STATE_FLOAT4 33
 
 /* The all-pairs forces of fga_forces(tree = NULL, ...) without any device
  * allocation. The paper has no counterpart: this entry point exists for
@@ -252,11 +269,13 @@ int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N,
  * Packed inputs, per-split partial sums and the kernel's state block live in
  * one array of FGA_STATIC_SCRATCH_FLOAT4 float4 compiled into the library; it
  * occupies every device that loads the library until the process exits.
- * Limit: 32 + N + M + 2 M <= FGA_STATIC_SCRATCH_FLOAT4 (one source split; the
- * call uses more splits when they fit); larger inputs are rejected with
- * FGA_EINVAL and a message, before any GPU work. The first call on each device
- * looks up the array's address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture. Every call shares
+ * Limit: FGA_STATIC_STATE_FLOAT4 + N + M + 2 M <= FGA_STATIC_SCRATCH_FLOAT4,
+ * i.e. 33 + N + 3 M <= 524288 (one source split; the call uses more splits
+ * when they fit); larger inputs are rejected with FGA_EINVAL and a message,
+ * before any GPU work. Every call looks up the array's address on the current
+ * device (cudaGetSymbolAddress, which allocates nothing); the first call on a
+ * device loads the library's device code there, so make it before any stream
+ * capture. Every call shares
  * the array and overwrites what it reads before reading it, so leftovers of an
  * earlier call do not matter; calls that overlap on the GPU (unordered streams
  * or concurrent host threads) race on the array and must be serialised by the

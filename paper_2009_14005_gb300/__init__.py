@@ -42,6 +42,8 @@ FGA_AUTO = 2
 FGA_WALK_AUTO = 0  # Barnes-Hut walk by template size
 FGA_WALK_LANE = 1  # one walk per template point
 FGA_WALK_COOP = 2  # one walk per 64 template points
+FGA_WALK_CURSOR = 3  # one walk per 64 points following each point's own walk
+FGA_WALK_CURSOR32 = 4  # the same, 32 points per warp
 FGA_VEL_UNCONSTRAINED = 0
 FGA_VEL_RIGID = 1
 FGA_MASS_UNIFORM = 0
@@ -59,9 +61,10 @@ SYMBOLS = [
     "fga_forces_direct_static", "fga_register_batch", "fga_direct_max_n",
     "fga_server_create", "fga_server_submit", "fga_server_poll", "fga_server_stats_get",
     "fga_server_destroy", "fga_autotune", "fga_set_direct_tile", "fga_get_direct_tile",
-    "fga_masses_landmarks",
+    "fga_masses_landmarks", "fga_forces_terms",
 ]
 FGA_STATIC_SCRATCH_FLOAT4 = 524288
+FGA_STATIC_STATE_FLOAT4 = 33
 
 
 class fga_params(ctypes.Structure):
@@ -179,6 +182,7 @@ def _load():
         "fga_tree_export": (I64, [P, I64, P, P, P, VP]),
         "fga_tree_preorder": (I64, [P, I64, P, VP]),
         "fga_forces": (ctypes.c_int, [P, P, P, I64, P, P, I64, PP, P, ctypes.POINTER(I64), VP]),
+        "fga_forces_terms": (ctypes.c_int, [P, P, P, I64, PP, P, P, VP]),
         "fga_state_create": (ctypes.c_int, [P, P, I64, P, P, I64, P, PP,
                                             ctypes.POINTER(ctypes.c_void_p), VP]),
         "fga_step": (ctypes.c_int, [P, ctypes.c_int, VP]),
@@ -409,6 +413,19 @@ def fga_forces(tree, X, mX, Y, mY=None, p: fga_params | None = None, want_count:
                         _ptr(mY), Y.shape[0], ctypes.byref(p), _ptr(out),
                         ctypes.byref(cnt) if want_count else None, _stream(stream)))
     return (out, int(cnt.value)) if want_count else out
+
+
+def fga_forces_terms(tree, Y, mY=None, p: fga_params | None = None, stream=None):
+    """BHForce on ``tree`` and each template point's term count (int32, Y's order)."""
+    torch = _torch()
+    p = p or params()
+    Y = _dev(Y, 3, "Y")
+    mY = _dev(mY) if mY is not None else None
+    out = torch.empty_like(Y)
+    terms = torch.empty(Y.shape[0], dtype=torch.int32, device=Y.device)
+    _err(lib.fga_forces_terms(tree.handle, _ptr(Y), _ptr(mY), Y.shape[0], ctypes.byref(p), _ptr(out),
+                              _ptr(terms), _stream(stream)))
+    return out, terms
 
 
 def fga_forces_direct_static(X, mX, Y, mY=None, p: fga_params | None = None, out=None,

@@ -121,8 +121,8 @@ int check_params(const fga_params* p, bool need_tree) {
     set_error("dim must be 2 or 3");
     return FGA_EINVAL;
   }
-  if (p->bh_walk != FGA_WALK_AUTO && p->bh_walk != FGA_WALK_LANE && p->bh_walk != FGA_WALK_COOP) {
-    set_error("bh_walk must be FGA_WALK_AUTO, FGA_WALK_LANE or FGA_WALK_COOP");
+  if (p->bh_walk < FGA_WALK_AUTO || p->bh_walk > FGA_WALK_CURSOR32) {
+    set_error("bh_walk must be FGA_WALK_AUTO, _LANE, _COOP, _CURSOR or _CURSOR32");
     return FGA_EINVAL;
   }
   if (p->max_iter < 0) {
@@ -459,7 +459,7 @@ int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N,
   if (tree) {
     if (sc.alloc(&perm, M)) return FGA_ENOMEM;
     rc = pack_template(Y, mY, 1.0f, M, true, Y0, perm, s);
-    fb.S = tree->n_front;
+    fb.S = bh_chunks(M, tree->n_front, bh_walk_kind(M, p->bh_walk));
   } else {
     if (sc.alloc(&X4, N)) return FGA_ENOMEM;
     rc = pack_template(Y, mY, 1.0f, M, false, Y0, nullptr, s);
@@ -488,6 +488,44 @@ int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N,
   return FGA_OK;
 }
 
+__global__ void k_terms_out(const unsigned* __restrict__ terms, const int* __restrict__ perm, int64_t M,
+                            int32_t* __restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
+       i += (int64_t)gridDim.x * blockDim.x)
+    out[perm[i]] = (int32_t)terms[i];
+}
+
+int fga_forces_terms(const fga_tree* tree, const float* Y, const float* mY, int64_t M,
+                     const fga_params* p, float* acc_out, int32_t* terms_out, void* stream) {
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  if (!tree || !p || !(p->eps > 0.f) || !(p->theta >= 0.f) || M <= 0 || !Y || !acc_out || !terms_out) {
+    set_error("fga_forces_terms: bad arguments");
+    return FGA_EINVAL;
+  }
+  Scratch sc(s);
+  float4* Y0 = nullptr;
+  int* perm = nullptr;
+  unsigned* terms = nullptr;
+  DevState* ds = nullptr;
+  ForceBuffers fb;
+  if (sc.alloc(&Y0, M) || sc.alloc(&ds, 1) || sc.alloc(&perm, M) || sc.alloc(&terms, M))
+    return FGA_ENOMEM;
+  int rc = pack_template(Y, mY, 1.0f, M, true, Y0, perm, s);
+  if (rc) return rc;
+  fb.S = bh_chunks(M, tree->n_front, bh_walk_kind(M, p->bh_walk));
+  if (sc.alloc(&fb.hi, (size_t)fb.S * M) || sc.alloc(&fb.lo, (size_t)fb.S * M)) return FGA_ENOMEM;
+  FGA_CUDA_TRY(cudaMemsetAsync(terms, 0, sizeof(unsigned) * M, s));
+  if ((rc = launch_state_init(ds, nullptr, s))) return rc;
+  rc = launch_bh(tree, Y0, M, ds, p->eps, p->theta, fb, s, bh_walk_kind(M, p->bh_walk), nullptr, nullptr,
+                 terms);
+  if (rc) return rc;
+  if ((rc = launch_forces_out(fb, M, Y0, mY != nullptr, p->G, perm, acc_out, s))) return rc;
+  k_terms_out<<<grid_for(M), 256, 0, s>>>(terms, perm, M, terms_out);
+  FGA_LAUNCH_CHECK("terms_out");
+  return FGA_OK;
+}
+
 }  // extern "C"
 
 // Build a state from device arrays that are already checked.
@@ -513,7 +551,7 @@ static int state_create_checked(const float* Xn, const float* mX, int64_t N, con
       if ((rc = tree_build(Xn, mX, N, p->max_depth, &st->own_tree, s))) return fail(rc);
       st->tree = st->own_tree;
     }
-    st->fb.S = st->tree->n_front;
+    st->fb.S = bh_chunks(M, st->tree->n_front, bh_walk_kind(M, p->bh_walk));
   } else {
     if (dev_alloc_n(&st->X4, N, s)) return fail(FGA_ENOMEM);
     k_pack4<<<grid_for(N), 256, 0, s>>>(Xn, mX, (float)(1.0 / (double)N), N, st->X4);
@@ -527,7 +565,8 @@ static int state_create_checked(const float* Xn, const float* mX, int64_t N, con
   if (bh && dev_alloc_n(&st->perm, M, s)) return fail(FGA_ENOMEM);
   if (bh) {
     st->bh_kind = bh_walk_kind(M, p->bh_walk);
-    st->bh_ntasks = bh_tasks(M, st->tree->n_front, bh_points_per_lane(st->bh_kind));
+    st->bh_ntasks = bh_tasks(M, bh_chunks(M, st->tree->n_front, st->bh_kind),
+                             bh_points_per_lane(st->bh_kind));
     if (dev_alloc_n(&st->bh_cost, st->bh_ntasks, s) ||
         dev_alloc_n(&st->bh_order, (size_t)st->bh_ntasks + TASK_ORDER_SCRATCH, s))
       return fail(FGA_ENOMEM);

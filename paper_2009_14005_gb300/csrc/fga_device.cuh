@@ -422,4 +422,155 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const Fr
     for (int c = 0; c < 3; ++c) comp_add(h[q][c], l[q][c], p[q][c]);
 }
 
+// The per-point BHForce of Algorithm 2 for the 32 * NP template points of a
+// warp (NP = 1 or 2 per lane), restricted to frontier cell f, as one walk
+// that follows all the points' own walks at once. Each point keeps the
+// position of its own stackless depth-first walk (bh_task_pre): the record
+// it reads next, nx. The warp reads the smallest nx over its points (one
+// broadcast record load); the points whose walk is at that record judge it
+// exactly as their own walk would (accept: add the monopole, skip the
+// subtree; reject: go to the next record), the others wait. Since every walk
+// only moves forward through the pre-order records, the warp visits exactly
+// the union of its points' walks, in order, and each point adds exactly its
+// own terms in its own order. (A point waiting beyond record v accepted an
+// ancestor of v, so the next record is always v + 1 if some point rejected v
+// and v + size(v) otherwise; with FGA_BH_CURSOR_VOTE the warp takes it from a
+// vote instead of the minimum.) Per step: one record, one judgement per point
+// (packed FP32 for NP = 2) and one warp-wide reduction; no stack, no masks.
+// Partial sums are flushed into the compensated accumulators every 32 warp
+// steps. Adds into h[q], l[q], cnt[q]; `steps` gains the records visited.
+#ifndef FGA_BH_CURSOR_VOTE
+#define FGA_BH_CURSOR_VOTE 0
+#endif
+template <int NP>
+__device__ __forceinline__ void bh_walk_cursor(const float4* __restrict__ pre,
+                                               const FrontCell* __restrict__ front, unsigned f,
+                                               const float3 (&y)[NP], const bool (&valid)[NP],
+                                               float eps2, float theta2, float (&h)[NP][3],
+                                               float (&l)[NP][3], unsigned (&cnt)[NP],
+                                               unsigned& steps) {
+  static_assert(NP == 1 || NP == 2, "one or two points per lane");
+  float p[NP][3];
+  bool live[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) {
+    p[q][0] = p[q][1] = p[q][2] = 0.f;
+    live[q] = valid[q];
+  }
+  {
+    const int npath = front[f].npath;
+    const unsigned first_mask = front[f].first_mask;
+    for (int j = 0; j < npath; ++j) {
+      const int a = front[f].path[j];
+      const float4 cm = pre[2 * a];
+      const float l2 = pre[2 * a + 1].x;
+      const bool own = (first_mask >> j) & 1u;
+#pragma unroll
+      for (int q = 0; q < NP; ++q) {
+        const float dx = cm.x - y[q].x, dy = cm.y - y[q].y, dz = cm.z - y[q].z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const bool accept = live[q] && l2 < theta2 * d2;
+        if (own) {
+          const float inv = rsqrt_fast(d2 + eps2);
+          const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
+          p[q][0] = fmaf(wgt, dx, p[q][0]);
+          p[q][1] = fmaf(wgt, dy, p[q][1]);
+          p[q][2] = fmaf(wgt, dz, p[q][2]);
+          cnt[q] += accept;
+        }
+        live[q] = live[q] && !accept;
+      }
+    }
+  }
+  const int end = front[f].end;
+  int nx[NP];
+#pragma unroll
+  for (int q = 0; q < NP; ++q) nx[q] = live[q] ? front[f].node : end;
+  int v = (int)__reduce_min_sync(FULL, (unsigned)(NP == 2 ? min(nx[0], nx[NP - 1]) : nx[0]));
+  unsigned k = 0;
+  if constexpr (NP == 2) {
+    const f2 nyx = f2_pack(-y[0].x, -y[1].x), nyy = f2_pack(-y[0].y, -y[1].y);
+    const f2 nyz = f2_pack(-y[0].z, -y[1].z);
+    const f2 th2 = f2_pack(theta2, theta2), e2 = f2_pack(eps2, eps2);
+    f2 px2 = f2_pack(p[0][0], p[1][0]), py2 = f2_pack(p[0][1], p[1][1]), pz2 = f2_pack(p[0][2], p[1][2]);
+    while (v < end) {
+      const float4 cm = pre[2 * v];
+      const float4 ri = pre[2 * v + 1];
+      const int skip = __float_as_int(ri.y);
+      const f2 dx = f2_add(f2_pack(cm.x, cm.x), nyx), dy = f2_add(f2_pack(cm.y, cm.y), nyy);
+      const f2 dz = f2_add(f2_pack(cm.z, cm.z), nyz);
+      const f2 d2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+      float o0, o1, e0, e1;
+      f2_unpack(f2_mul(th2, d2), o0, o1);
+      f2_unpack(f2_add(d2, e2), e0, e1);
+      const bool act0 = nx[0] == v, act1 = nx[1] == v;
+      const bool acc0 = act0 && ri.x < o0, acc1 = act1 && ri.x < o1;
+      const f2 inv = f2_pack(rsqrt_fast(e0), rsqrt_fast(e1));
+      const f2 w = f2_mul(f2_pack(cm.w, cm.w), f2_mul(f2_mul(inv, inv), inv));
+      float w0, w1;
+      f2_unpack(w, w0, w1);
+      const f2 wsel = f2_pack(acc0 ? w0 : 0.f, acc1 ? w1 : 0.f);
+      px2 = f2_fma(wsel, dx, px2);
+      py2 = f2_fma(wsel, dy, py2);
+      pz2 = f2_fma(wsel, dz, pz2);
+      cnt[0] += acc0;
+      cnt[1] += acc1;
+      nx[0] = act0 ? v + (acc0 ? skip : 1) : nx[0];
+      nx[1] = act1 ? v + (acc1 ? skip : 1) : nx[1];
+#if FGA_BH_CURSOR_VOTE
+      v = __any_sync(FULL, (act0 && !acc0) || (act1 && !acc1)) ? v + 1 : v + skip;
+#else
+      v = (int)__reduce_min_sync(FULL, (unsigned)min(nx[0], nx[1]));
+#endif
+      if ((++k & 31u) == 0u) {
+        f2_unpack(px2, p[0][0], p[1][0]);
+        f2_unpack(py2, p[0][1], p[1][1]);
+        f2_unpack(pz2, p[0][2], p[1][2]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) comp_add(h[q][c], l[q][c], p[q][c]);
+        px2 = py2 = pz2 = f2_pack(0.f, 0.f);
+      }
+    }
+    f2_unpack(px2, p[0][0], p[1][0]);
+    f2_unpack(py2, p[0][1], p[1][1]);
+    f2_unpack(pz2, p[0][2], p[1][2]);
+  } else {
+    while (v < end) {
+      const float4 cm = pre[2 * v];
+      const float4 ri = pre[2 * v + 1];
+      const int skip = __float_as_int(ri.y);
+      const float dx = cm.x - y[0].x, dy = cm.y - y[0].y, dz = cm.z - y[0].z;
+      const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+      const bool act = nx[0] == v;
+      const bool accept = act && ri.x < theta2 * d2;
+      const float inv = rsqrt_fast(d2 + eps2);
+      const float wgt = accept ? cm.w * (inv * inv * inv) : 0.f;
+      p[0][0] = fmaf(wgt, dx, p[0][0]);
+      p[0][1] = fmaf(wgt, dy, p[0][1]);
+      p[0][2] = fmaf(wgt, dz, p[0][2]);
+      cnt[0] += accept;
+      nx[0] = act ? v + (accept ? skip : 1) : nx[0];
+#if FGA_BH_CURSOR_VOTE
+      v = __any_sync(FULL, act && !accept) ? v + 1 : v + skip;
+#else
+      v = (int)__reduce_min_sync(FULL, (unsigned)nx[0]);
+#endif
+      if ((++k & 31u) == 0u) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          comp_add(h[0][c], l[0][c], p[0][c]);
+          p[0][c] = 0.f;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NP; ++q)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) comp_add(h[q][c], l[q][c], p[q][c]);
+  steps += k;
+}
+
 }  // namespace fga

@@ -220,24 +220,28 @@ static constexpr int BH_WARPS = FGA_BH_WARPS;
 #ifndef FGA_BH_MINBLOCKS
 #define FGA_BH_MINBLOCKS 8  // resident blocks per SM the register budget is sized for
 #endif
-// NP = 0: one template point per lane, each lane walking its own point over
-// the depth-first records (bh_task_pre); NP = 2: two points per lane, one
-// walk for the warp (bh_walk).
-template <int NP>
+// KIND (bh_walk_kind): 0 = one template point per lane, each lane walking its
+// own point over the depth-first records (bh_task_pre); 2 = two points per
+// lane, one walk for the warp with saved sibling ranges (bh_walk); 3 / 4 =
+// two / one points per lane, one walk for the warp that follows every
+// point's own walk (bh_walk_cursor).
+template <int KIND>
 __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const float4* __restrict__ pre,
                                                          const float4* __restrict__ Y0, int64_t M,
                                                          const FrontCell* __restrict__ front, int K,
+                                                         int C,
                                                          DevState* __restrict__ ds, float eps2,
                                                          float theta2, float4* __restrict__ hi_out,
                                                          float4* __restrict__ lo_out,
                                                          const unsigned* __restrict__ order,
                                                          unsigned* __restrict__ cost,
-                                                         unsigned long long* __restrict__ mask) {
-  constexpr int PL = NP == 0 ? 1 : NP;  // template points per lane
+                                                         unsigned long long* __restrict__ mask,
+                                                         unsigned* __restrict__ terms) {
+  constexpr int PL = (KIND == 0 || KIND == 4) ? 1 : 2;  // template points per lane
   if (ds->done) return;
   const int lane = threadIdx.x & 31;
   const Xf xf = load_xf(ds);
-  const unsigned ntasks = bh_tasks(M, K, PL);
+  const unsigned ntasks = bh_tasks(M, C, PL);
   unsigned long long total = 0;
   for (;;) {
     unsigned slot = 0;
@@ -246,7 +250,8 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
     if (slot >= ntasks) break;
     unsigned task = order ? order[slot] : slot;
     if (task >= ntasks) task = slot;  // never index past the task range
-    const unsigned g = task / (unsigned)K, f = task % (unsigned)K;
+    const unsigned g = task / (unsigned)C, c = task % (unsigned)C;
+    const unsigned f0 = (unsigned)(((uint64_t)c * K) / C), f1 = (unsigned)(((uint64_t)(c + 1) * K) / C);
     int64_t i[PL];
     bool valid[PL];
     float3 y[PL];
@@ -261,11 +266,15 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
       cnt[q] = 0u;
     }
     unsigned steps = 0;
-    if constexpr (NP == 0)
-      bh_task_pre(pre, front, f, y[0], valid[0], eps2, theta2, h[0][0], h[0][1], h[0][2],
-                  lo[0][0], lo[0][1], lo[0][2], cnt[0], steps);
-    else
-      bh_walk<NP>(pre, front, f, y, valid, eps2, theta2, h, lo, cnt, steps);
+    for (unsigned f = f0; f < f1; ++f) {
+      if constexpr (KIND == 0)
+        bh_task_pre(pre, front, f, y[0], valid[0], eps2, theta2, h[0][0], h[0][1], h[0][2],
+                    lo[0][0], lo[0][1], lo[0][2], cnt[0], steps);
+      else if constexpr (KIND == 2)
+        bh_walk<2>(pre, front, f, y, valid, eps2, theta2, h, lo, cnt, steps);
+      else
+        bh_walk_cursor<PL>(pre, front, f, y, valid, eps2, theta2, h, lo, cnt, steps);
+    }
     if (cost && lane == 0) cost[task] = steps + 1u;
 #pragma unroll
     for (int q = 0; q < PL; ++q) {
@@ -273,10 +282,11 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
       // with a mask its slot is neither written here nor read by the epilogue
       const bool any = !mask || __any_sync(FULL, valid[q] && cnt[q] > 0u);
       if (any && valid[q]) {
-        hi_out[(int64_t)f * M + i[q]] = make_float4(h[q][0], h[q][1], h[q][2], 0.f);
-        lo_out[(int64_t)f * M + i[q]] = make_float4(lo[q][0], lo[q][1], lo[q][2], 0.f);
+        hi_out[(int64_t)c * M + i[q]] = make_float4(h[q][0], h[q][1], h[q][2], 0.f);
+        lo_out[(int64_t)c * M + i[q]] = make_float4(lo[q][0], lo[q][1], lo[q][2], 0.f);
       }
-      if (mask && any && lane == 0) atomicOr(&mask[(size_t)PL * g + q], 1ull << f);
+      if (mask && any && lane == 0) atomicOr(&mask[(size_t)PL * g + q], 1ull << c);
+      if (terms && valid[q] && cnt[q]) atomicAdd(&terms[i[q]], cnt[q]);
       total += valid[q] ? cnt[q] : 0u;
     }
   }
@@ -294,20 +304,20 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
   }
 }
 
-template <int NP>
-static int bh_grid(int64_t M, int K) {
+template <int KIND>
+static int bh_grid(int64_t M, int C) {
   static std::atomic<int> cached{0};
   int per_sm = cached.load();
   if (per_sm == 0) {
     int b = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bh<NP>, BH_WARPS * 32, 0) != cudaSuccess || b < 1) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_bh<KIND>, BH_WARPS * 32, 0) != cudaSuccess || b < 1) {
       cudaGetLastError();
       b = 1;
     }
     per_sm = b;
     cached.store(b);
   }
-  const int64_t tasks = bh_tasks(M, K, NP == 0 ? 1 : NP);
+  const int64_t tasks = bh_tasks(M, C, bh_points_per_lane(KIND));
   const int64_t need = (tasks + BH_WARPS - 1) / BH_WARPS;
   return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)per_sm * sm_count()));
 }
@@ -315,21 +325,41 @@ static int bh_grid(int64_t M, int K) {
 int bh_walk_kind(int64_t M, int walk) {
   if (walk == FGA_WALK_LANE) return 0;
   if (walk == FGA_WALK_COOP) return 2;
+  if (walk == FGA_WALK_CURSOR) return 3;
+  if (walk == FGA_WALK_CURSOR32) return 4;
   const int64_t warps = (int64_t)sm_count() * 32;
   return M >= (int64_t)FGA_BH_COOP_POINTS_PER_WARP * warps ? 2 : 0;
 }
 
+int bh_chunks(int64_t M, int K, int kind) {
+  if (FGA_BH_TASKS_PER_WARP <= 0 || K <= 1) return K < 1 ? 1 : K;
+  const int pl = bh_points_per_lane(kind);
+  const int64_t groups = (M + 32 * pl - 1) / (32 * pl);
+  const int64_t target = (int64_t)FGA_BH_TASKS_PER_WARP * sm_count() * BH_WARPS * FGA_BH_MINBLOCKS;
+  const int64_t c = (target + groups - 1) / groups;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(c, K));
+}
+
 int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, float eps,
-              float theta, ForceBuffers& fb, cudaStream_t s, int kind, const unsigned* order, unsigned* cost) {
+              float theta, ForceBuffers& fb, cudaStream_t s, int kind, const unsigned* order, unsigned* cost,
+              unsigned* terms) {
   unsigned long long* mask = t->n_front <= 64 ? fb.mask : nullptr;
+  const int C = bh_chunks(M, t->n_front, kind);
+#define FGA_BH_CASE(KD)                                                                           \
+  k_bh<KD><<<bh_grid<KD>(M, C), BH_WARPS * 32, 0, s>>>(t->node_pre, Y0, M, t->front, t->n_front, C, \
+                                                       ds, eps * eps, theta * theta, fb.hi, fb.lo,  \
+                                                       order, cost, mask, terms)
   if (kind == 2)
-    k_bh<2><<<bh_grid<2>(M, t->n_front), BH_WARPS * 32, 0, s>>>(t->node_pre, Y0, M, t->front, t->n_front, ds, eps * eps, theta * theta,
-                                                               fb.hi, fb.lo, order, cost, mask);
+    FGA_BH_CASE(2);
+  else if (kind == 3)
+    FGA_BH_CASE(3);
+  else if (kind == 4)
+    FGA_BH_CASE(4);
   else
-    k_bh<0><<<bh_grid<0>(M, t->n_front), BH_WARPS * 32, 0, s>>>(t->node_pre, Y0, M, t->front, t->n_front, ds, eps * eps, theta * theta,
-                                                               fb.hi, fb.lo, order, cost, mask);
+    FGA_BH_CASE(0);
+#undef FGA_BH_CASE
   FGA_LAUNCH_CHECK("bh");
-  fb.S = t->n_front;
+  fb.S = C;
   return FGA_OK;
 }
 

@@ -203,10 +203,11 @@ int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const
                   float eps, const DirectPlan& plan, ForceBuffers& fb, cudaStream_t s);
 // kind: the walk (bh_walk_kind); order: heavy-first
 // task order from launch_task_order, or null (task index order); cost: where
-// each task's step count is recorded, or null.
+// each task's step count is recorded, or null; terms: per template point
+// (sorted order, zeroed by the caller), the number of BHForce terms added, or null.
 int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, float eps,
               float theta, ForceBuffers& fb, cudaStream_t s, int kind, const unsigned* order = nullptr,
-              unsigned* cost = nullptr);
+              unsigned* cost = nullptr, unsigned* terms = nullptr);
 // Heavy-first order of ntasks tasks from their recorded costs. `order` must
 // hold ntasks + TASK_ORDER_SCRATCH entries (the tail is the sort's scratch).
 constexpr unsigned TASK_ORDER_SCRATCH = 8192;
@@ -224,10 +225,20 @@ constexpr unsigned TASK_ORDER_SCRATCH = 8192;
 #define FGA_BH_COOP_POINTS_PER_WARP 96
 #endif
 int bh_walk_kind(int64_t M, int walk);
-inline int bh_points_per_lane(int kind) { return kind == 0 ? 1 : kind; }
-__host__ __device__ inline unsigned bh_tasks(int64_t M, int K, int pl) {
-  return (unsigned)((M + 32 * pl - 1) / (32 * pl)) * (unsigned)K;
+inline int bh_points_per_lane(int kind) { return (kind == 0 || kind == 4) ? 1 : 2; }
+// Tasks of a launch: (group, chunk), C chunks per group.
+__host__ __device__ inline unsigned bh_tasks(int64_t M, int C, int pl) {
+  return (unsigned)((M + 32 * pl - 1) / (32 * pl)) * (unsigned)C;
 }
+// The K frontier cells are cut into C chunks of consecutive cells (chunk c:
+// cells [c K / C, (c + 1) K / C)); a task walks one chunk for its group, so
+// each template point leaves C partial sums for the epilogue instead of K. C
+// is the fewest chunks that still give every resident warp about
+// FGA_BH_TASKS_PER_WARP tasks (0: C = K, one frontier cell per task).
+#ifndef FGA_BH_TASKS_PER_WARP
+#define FGA_BH_TASKS_PER_WARP 16
+#endif
+int bh_chunks(int64_t M, int K, int kind);
 int launch_task_order(const unsigned* cost, unsigned ntasks, unsigned* order, cudaStream_t s);
 // Refreshed after the first two force launches and then every
 // FGA_BH_REORDER_EVERY launches (0: never, tasks run in index order).

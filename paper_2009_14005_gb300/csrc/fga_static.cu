@@ -11,11 +11,13 @@
 // The array is a file-scope __device__ array, so every GPU that loads the
 // library holds it (8 MiB) until the process exits. Host code cannot pass the
 // array's name to a kernel (on the host that name is only a stand-in, not a
-// device address), so the device address is looked up once per device with
-// cudaGetSymbolAddress on the first call made with that device current.
+// device address), so every call looks up the array's device address on the
+// current device with cudaGetSymbolAddress, a host-side query that allocates
+// nothing. Looking it up on every call (rather than caching it per device)
+// keeps the address right when the module is loaded again, after a
+// cudaDeviceReset or under another context. The first call on a device loads
+// the library's device code there; make it before any stream capture.
 #include <algorithm>
-#include <map>
-#include <mutex>
 #include <string>
 
 #include "fga_internal.cuh"
@@ -24,19 +26,8 @@ namespace fga {
 
 static __device__ __align__(256) float4 g_static_scratch[FGA_STATIC_SCRATCH_FLOAT4];
 
-static std::mutex g_static_mu;
-static std::map<int, float4*> g_static_addr;
-
-// Device address of g_static_scratch on the current device (looked up once).
+// Device address of g_static_scratch on the current device.
 static int static_scratch(float4** out) {
-  int dev = 0;
-  FGA_CUDA_TRY(cudaGetDevice(&dev));
-  std::lock_guard<std::mutex> lk(g_static_mu);
-  auto it = g_static_addr.find(dev);
-  if (it != g_static_addr.end()) {
-    *out = it->second;
-    return FGA_OK;
-  }
   void* p = nullptr;
   cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
   if (e != cudaSuccess || p == nullptr) {
@@ -44,7 +35,6 @@ static int static_scratch(float4** out) {
     set_error(std::string("cudaGetSymbolAddress(static scratch): ") + cudaGetErrorString(e));
     return FGA_ECUDA;
   }
-  g_static_addr[dev] = static_cast<float4*>(p);
   *out = static_cast<float4*>(p);
   return FGA_OK;
 }
@@ -58,6 +48,7 @@ __global__ void k_static_pack(const float* __restrict__ xyz, const float* __rest
 
 // float4 slots taken by one DevState at the start of the array
 static constexpr int64_t kStateSlots = (int64_t)((sizeof(DevState) + sizeof(float4) - 1) / sizeof(float4));
+static_assert(kStateSlots == FGA_STATIC_STATE_FLOAT4, "the header's state-block size is out of date");
 
 static int64_t footprint(int64_t N, int64_t M, int S) { return kStateSlots + N + M + 2 * (int64_t)S * M; }
 

@@ -84,15 +84,24 @@ def test_same_alone_and_in_the_mix(fga, mix):
         assert alone[0]["interactions"] == res_mix[k]["interactions"]
 
 
-def test_per_pair_early_exit(fga):
+def test_per_pair_early_exit(fga, orc):
+    # Algorithm 2's stop test decided per pair on the device: every pair of the
+    # batch stops where the FP64 oracle stops (within one iteration: the test
+    # compares |T_k - T_{k-2}|^2 with the tolerance, and FP32 forces can move
+    # that crossing by one step) and ends at the oracle's transform.
     pairs = [synth.box_pair(s, 400, deg) for s, deg in [(0, 5.0), (1, 15.0), (2, 30.0)]]
     p = fga.params(method=fga.FGA_DIRECT, max_iter=300, conv_tol=1e-6)
+    po = orc.Params(method=orc.FGA_DIRECT, max_iter=300, conv_tol=1e-6)
     res, _ = fga.fga_register_batch([(_cuda(X), _cuda(Y)) for X, Y, _, _ in pairs], p)
     for (X, Y, R_gt, t_gt), r in zip(pairs, res):
         R, t, s1 = fga.fga_register(_cuda(X), _cuda(Y), p)
         assert r["converged"] and s1["converged"]
         assert abs(r["iterations"] - s1["iterations"]) <= 1
         assert r["interactions"] == r["iterations"] * len(X) * len(Y)
+        o = orc.register_full(X, Y, po)
+        assert o["iters"] < 300
+        assert abs(r["iterations"] - o["iters"]) <= 1
+        assert _close(r["R"], r["t"], o["R"], o["t"], X)
     assert len({r["iterations"] for r in res}) > 1
 
 

@@ -1,6 +1,6 @@
 """CUDA path vs the FP64 oracle, through the C ABI (needs a GPU).
 
-Tolerances (derived in DESIGN.md, "Parity bars"):
+Tolerances (each follows from the arithmetic of its step):
 * normalisation: 1e-6 absolute (one float32 rounding of values in [-5, 5]);
 * masses: 1e-6 relative (float32 output of FP64 arithmetic);
 * tree: structure bit-exact, mass / CoM to float32 rounding;
@@ -162,7 +162,9 @@ def test_direct_forces_with_template_masses(fga, orc):
 
 # --------------------------------------------------------------------------- BHForce
 
-WALKS = {"lane": 1, "coop": 2}  # fga_params.bh_walk: per-point walks, one walk per 64 points
+# fga_params.bh_walk: per-point walks; one walk per 64 points with saved
+# ranges; one walk per 64 / 32 points following every point's own walk
+WALKS = {"lane": 1, "coop": 2, "cursor": 3, "cursor32": 4}
 
 
 @pytest.mark.parametrize("walk", list(WALKS))
@@ -179,16 +181,23 @@ def test_bh_forces_match_oracle(fga, orc, theta, walk):
     t = fga.fga_tree_build(_cuda(Xn), _cuda(mX), p)
     a, cnt = fga.fga_forces(t, None, None, _cuda(Yn), None, p, want_count=True)
     a = a.cpu().numpy().astype(np.float64)
+    a2, terms = fga.fga_forces_terms(t, _cuda(Yn), None, p)
+    terms = terms.cpu().numpy()
+    np.testing.assert_array_equal(a2.cpu().numpy(), a.astype(np.float32))
+    assert terms.sum() == cnt
     err_gpu = np.linalg.norm(a - a_d) / np.linalg.norm(a_d)
     err_orc = np.linalg.norm(a_bo - a_d) / np.linalg.norm(a_d)
     assert err_gpu <= err_orc + 1e-5, (err_gpu, err_orc)
-    # same walk as the per-point BHForce: term counts agree up to rare
-    # opening-criterion ties decided differently in FP32 and FP64
-    assert abs(cnt - c_o.sum()) <= 1e-3 * c_o.sum()
+    # same walk as the per-point BHForce: a point whose force is not within
+    # 1e-4 of the oracle's took other terms (an opening-criterion tie decided
+    # differently in FP32 and FP64), which shows in its own term count
     close = np.linalg.norm(a - a_bo, axis=1) <= 1e-4 * np.linalg.norm(a_bo, axis=1) + 1e-6
-    assert close.mean() > 0.99
+    assert np.all(close | (terms != c_o)), np.flatnonzero(~close & (terms == c_o))[:10]
+    assert (terms != c_o).mean() < 0.01
+    assert abs(cnt - c_o.sum()) <= 1e-3 * c_o.sum()
     if theta == 0.0:
         assert cnt == len(Xn) * len(Yn)
+        np.testing.assert_array_equal(terms, len(Xn))
 
 
 @pytest.mark.parametrize("m", [1, 31, 33, 64, 65, 1000])
@@ -204,11 +213,25 @@ def test_bh_walks_take_the_same_terms(fga, orc, m):
         p = fga.params(theta=0.5, eps=0.2, bh_walk=code)
         t = fga.fga_tree_build(_cuda(Xn), _cuda(mX), p)
         out[walk] = fga.fga_forces(t, None, None, _cuda(Yn), None, p, want_count=True)
-    (a1, c1), (a2, c2) = out["lane"], out["coop"]
-    assert c1 == c2
-    a1, a2 = a1.cpu().numpy().astype(np.float64), a2.cpu().numpy().astype(np.float64)
+    a1, c1 = out["lane"]
+    a1 = a1.cpu().numpy().astype(np.float64)
     scale = np.linalg.norm(a1, axis=1).max()
-    np.testing.assert_allclose(a2, a1, rtol=0, atol=2e-6 * scale)
+    for walk in WALKS:
+        a2, c2 = out[walk]
+        assert c2 == c1, walk
+        np.testing.assert_allclose(a2.cpu().numpy().astype(np.float64), a1, rtol=0, atol=2e-6 * scale,
+                                   err_msg=walk)
+    # the cursor walk and the per-lane walk take each point's terms in the
+    # same order with the same arithmetic: only the flush points of the
+    # compensated sums differ, so they agree far below the bar above
+    p = fga.params(theta=0.5, eps=0.2)
+    t = fga.fga_tree_build(_cuda(Xn), _cuda(mX), p)
+    for walk in ("lane", "cursor", "cursor32"):
+        _, terms = fga.fga_forces_terms(t, _cuda(Yn), None, fga.params(theta=0.5, eps=0.2,
+                                                                         bh_walk=WALKS[walk]))
+        out[walk + "_terms"] = terms.cpu().numpy()
+    np.testing.assert_array_equal(out["cursor_terms"], out["lane_terms"])
+    np.testing.assert_array_equal(out["cursor32_terms"], out["lane_terms"])
 
 
 # --------------------------------------------------------------------------- Algorithm 2
@@ -248,11 +271,14 @@ def test_register_box_recovers_ground_truth_and_matches(fga, orc, vm):
 
 @pytest.mark.parametrize("walk", list(WALKS))
 def test_register_bh_lidar_matches_oracle(fga, orc, walk):
+    # G = 1, as on the LiDAR benchmark workload: with the paper's 66.7 this
+    # cloud's FP64 trajectory is chaotic (a 1e-7 nudge of the template moves
+    # the oracle's own result by over 100 degrees), so no FP32 run can track it
     X, Y, _, _ = synth.lidar_pair(5, n=6000)
-    po = orc.Params(method=orc.FGA_BH, theta=0.5, max_iter=200, niv_masses=True)
+    po = orc.Params(method=orc.FGA_BH, theta=0.5, max_iter=200, niv_masses=True, G=1.0)
     o = orc.register_full(X, Y, po)
     p = fga.params(method=fga.FGA_BH, theta=0.5, max_iter=200, mass_mode=fga.FGA_MASS_NIV,
-                   bh_walk=WALKS[walk])
+                   bh_walk=WALKS[walk], G=1.0)
     R, t, st = fga.fga_register(_cuda(X), _cuda(Y), p)
     dphi, dt = _gt_errors(R, t, o["R"], o["t"], X)
     assert dphi <= 0.01 and dt <= 1e-4, (dphi, dt)
@@ -324,6 +350,32 @@ def test_single_template_point_is_degenerate(fga):
     R, t, st = fga.fga_register(_cuda(X), _cuda(X[:1]), fga.params(max_iter=3, method=fga.FGA_DIRECT))
     assert st["status"] == fga.FGA_EDEGENERATE
     np.testing.assert_allclose(R, np.eye(3))
+
+
+@pytest.mark.parametrize("offset,degenerate", [(1e-5, True), (3e-6, True), (3e-2, False)])
+def test_near_collinear_template_is_judged_like_the_oracle(fga, orc, offset, degenerate):
+    # A template on a line with perpendicular offsets of relative size
+    # `offset`: sigma_2 / sigma_1 of its scatter is about offset^2 (1e-10 and
+    # 1e-11 lie between 1e-12 and 1e-7). Both sides declare a fit degenerate
+    # when sigma_2 <= 1e-7 sigma_1, so they agree on every iteration and end
+    # at the same transform.
+    rng = np.random.default_rng(21)
+    X = rng.normal(size=(1500, 3)).astype(np.float32)
+    s = np.linspace(-1.5, 1.5, 400)[:, None]
+    u, n1, n2 = np.array([0.6, 0.8, 0.0]), np.array([-0.8, 0.6, 0.0]), np.array([0.0, 0.0, 1.0])
+    Y = (s * u + offset * (rng.normal(size=(400, 1)) * n1 + rng.normal(size=(400, 1)) * n2)
+         + [0.1, -0.2, 0.3]).astype(np.float32)
+    p = fga.params(method=fga.FGA_DIRECT, max_iter=40)
+    R, t, st = fga.fga_register(_cuda(X), _cuda(Y), p)
+    o = orc.register_full(X, Y, orc.Params(method=orc.FGA_DIRECT, max_iter=40))
+    if degenerate:
+        assert o["degenerate"] == 40 and st["degenerate_fits"] == 40
+        assert st["status"] == fga.FGA_EDEGENERATE
+    else:
+        assert o["degenerate"] == 0 and st["degenerate_fits"] == 0
+    diag = np.linalg.norm(X.max(0) - X.min(0))
+    assert orc.rotation_error_deg(R, o["R"]) <= 0.01
+    assert np.linalg.norm(t - o["t"]) <= 1e-4 * diag
 
 
 def test_aligned_identical_sets_stay_put(fga):

@@ -143,17 +143,27 @@ def test_pair_larger_than_budget_is_refused(fga):
     assert "budget" in str(e.value)
 
 
-def test_early_exit_matches_alone(fga):
+def test_early_exit_matches_alone(fga, orc):
+    # Served pairs that stop early stop where they stop alone (bit for bit) and
+    # where the FP64 oracle stops (within one iteration), at its transform.
     p = params(fga, method=fga.FGA_DIRECT, max_iter=300, conv_tol=1e-6)
+    po = orc.Params(method=orc.FGA_DIRECT, max_iter=300, conv_tol=1e-6)
     pairs = [synth.box_pair(20 + k, n=400 + 150 * k)[:2] for k in range(4)]
     alone = [fga.fga_register_batch([pr], p)[0][0] for pr in pairs]
     with fga.Server(p, iters_per_tick=5) as srv:
         tickets = {srv.submit(X, Y): k for k, (X, Y) in enumerate(pairs)}
         got = srv.drain()
     for r in got:
-        b = alone[tickets[r["ticket"]]]
+        k = tickets[r["ticket"]]
+        b = alone[k]
         assert r["converged"] and r["iterations"] == b["iterations"] < 300
         assert np.array_equal(r["R"], b["R"])
+        X, Y = pairs[k]
+        o = orc.register_full(X, Y, po)
+        assert abs(r["iterations"] - o["iters"]) <= 1
+        diag = np.linalg.norm(X.max(0) - X.min(0))
+        assert rot_err_deg(r["R"], o["R"]) <= 0.01
+        assert np.linalg.norm(np.asarray(r["t"]) - o["t"]) <= 1e-4 * diag
 
 
 def test_work_cap_admits_one_at_a_time(fga):

@@ -74,3 +74,25 @@ def test_static_entry_rejects_sizes_beyond_its_array(fga):
     rc = _call_static(fga, X, mX, Y, None, p, out)
     assert rc == fga.FGA_EINVAL
     assert "static scratch" in fga.last_error()
+
+
+def test_static_entry_at_its_exact_limit(fga):
+    # 33 + N + 3 M = capacity: the largest accepted input (one source split),
+    # equal to fga_forces; one float4 more is rejected before any GPU work.
+    import torch
+    p = fga.params(G=66.7, eps=0.05)
+    cap, state = fga.FGA_STATIC_SCRATCH_FLOAT4, fga.FGA_STATIC_STATE_FLOAT4
+    M = 100_000
+    N = cap - state - 3 * M
+    X, mX, Y, _ = _problem(3, N, M)
+    ref = fga.fga_forces(None, X, mX, Y, None, p).cpu().numpy().astype(np.float64)
+    out = torch.full_like(Y, float("nan"))
+    assert _call_static(fga, X, mX, Y, None, p, out) == fga.FGA_OK, fga.last_error()
+    got = out.cpu().numpy().astype(np.float64)
+    np.testing.assert_allclose(got, ref, rtol=1e-5, atol=1e-5 * np.abs(ref).max())
+    X1, mX1, _, _ = _problem(4, N + 1, 4)
+    out[:] = float("nan")
+    assert _call_static(fga, X1, mX1, Y, None, p, out) == fga.FGA_EINVAL
+    assert "static scratch" in fga.last_error()
+    assert torch.isnan(out).all()
+
