@@ -215,7 +215,7 @@ WORKLOADS = {
                           G=66.7, eps=0.2, eta=0.2),
     # large piecewise-planar scenes, Barnes-Hut
     "planar-bh": dict(gen="planar", n=1_000_000, iters=100, method="bh", theta=0.5, niv=False,
-                      G=66.7, eps=0.2, eta=0.2, cpu_iters=1, ref_template=131_072),
+                      G=66.7, eps=0.2, eta=0.2, cpu_iters=1, ref_template=262_144),
     # many independent pairs (N, M log-uniform in [500, 50k], sphere and planar
     # shapes, rotations <= 60 deg), all-pairs or Barnes-Hut per pair by size,
     # one graph-captured loop per step; n = number of pairs

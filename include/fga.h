@@ -44,11 +44,13 @@ extern "C" {
 #define FGA_BH 1     /* Barnes-Hut tree (Algorithm 1) + BHForce (Eq. 15) */
 #define FGA_AUTO 2   /* FGA_DIRECT when N <= fga_direct_max_n(0), else FGA_BH */
 #define FGA_WALK_AUTO 0 /* by template size: per-lane walks while there are too few
-                           64-point groups to keep every resident warp busy */
+                           64-point groups to keep every resident warp busy,
+                           else FGA_WALK_CURSOR */
 #define FGA_WALK_LANE 1
 #define FGA_WALK_COOP 2
 #define FGA_WALK_CURSOR 3   /* one walk per 64 points that follows each point's own walk */
 #define FGA_WALK_CURSOR32 4 /* the same with 32 points per warp                          */
+#define FGA_WALK_CURSOR128 5 /* the same with 128 points per warp                        */
 
 #define FGA_VEL_UNCONSTRAINED 0 /* velocities of Eq. 9 persist between iterations */
 #define FGA_VEL_RIGID 1         /* velocities replaced by the rigid motion        */
@@ -90,7 +92,8 @@ typedef struct fga_params {
                         FGA_WALK_LANE (one walk per template point),
                         FGA_WALK_COOP (one walk per 64 points, each point
                         judging every node the walk visits), FGA_WALK_CURSOR /
-                        FGA_WALK_CURSOR32 (one walk per 64 / 32 points that
+                        FGA_WALK_CURSOR32 / FGA_WALK_CURSOR128 (one walk per
+                        64 / 32 / 128 points that
                         visits the union of the points' own walks, record by
                         record)                                               */
 } fga_params;

@@ -44,6 +44,7 @@ FGA_WALK_LANE = 1  # one walk per template point
 FGA_WALK_COOP = 2  # one walk per 64 template points
 FGA_WALK_CURSOR = 3  # one walk per 64 points following each point's own walk
 FGA_WALK_CURSOR32 = 4  # the same, 32 points per warp
+FGA_WALK_CURSOR128 = 5  # the same, 128 points per warp
 FGA_VEL_UNCONSTRAINED = 0
 FGA_VEL_RIGID = 1
 FGA_MASS_UNIFORM = 0

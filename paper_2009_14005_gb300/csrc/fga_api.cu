@@ -121,8 +121,8 @@ int check_params(const fga_params* p, bool need_tree) {
     set_error("dim must be 2 or 3");
     return FGA_EINVAL;
   }
-  if (p->bh_walk < FGA_WALK_AUTO || p->bh_walk > FGA_WALK_CURSOR32) {
-    set_error("bh_walk must be FGA_WALK_AUTO, _LANE, _COOP, _CURSOR or _CURSOR32");
+  if (p->bh_walk < FGA_WALK_AUTO || p->bh_walk > FGA_WALK_CURSOR128) {
+    set_error("bh_walk must be FGA_WALK_AUTO, _LANE, _COOP, _CURSOR, _CURSOR32 or _CURSOR128");
     return FGA_EINVAL;
   }
   if (p->max_iter < 0) {

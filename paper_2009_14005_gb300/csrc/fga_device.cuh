@@ -423,7 +423,7 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const Fr
 }
 
 // The per-point BHForce of Algorithm 2 for the 32 * NP template points of a
-// warp (NP = 1 or 2 per lane), restricted to frontier cell f, as one walk
+// warp (NP = 1, 2 or 4 per lane), restricted to frontier cell f, as one walk
 // that follows all the points' own walks at once. Each point keeps the
 // position of its own stackless depth-first walk (bh_task_pre): the record
 // it reads next, nx. The warp reads the smallest nx over its points (one
@@ -436,12 +436,14 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const Fr
 // ancestor of v, so the next record is always v + 1 if some point rejected v
 // and v + size(v) otherwise; with FGA_BH_CURSOR_VOTE the warp takes it from a
 // vote instead of the minimum.) Per step: one record, one judgement per point
-// (packed FP32 for NP = 2) and one warp-wide reduction; no stack, no masks.
+// (packed FP32 pairs for NP >= 2) and one warp-wide reduction; no stack, no
+// masks.
 // Partial sums are flushed into the compensated accumulators every 32 warp
 // steps. Adds into h[q], l[q], cnt[q]; `steps` gains the records visited.
 #ifndef FGA_BH_CURSOR_VOTE
 #define FGA_BH_CURSOR_VOTE 0
 #endif
+
 template <int NP>
 __device__ __forceinline__ void bh_walk_cursor(const float4* __restrict__ pre,
                                                const FrontCell* __restrict__ front, unsigned f,
@@ -449,7 +451,7 @@ __device__ __forceinline__ void bh_walk_cursor(const float4* __restrict__ pre,
                                                float eps2, float theta2, float (&h)[NP][3],
                                                float (&l)[NP][3], unsigned (&cnt)[NP],
                                                unsigned& steps) {
-  static_assert(NP == 1 || NP == 2, "one or two points per lane");
+  static_assert(NP == 1 || NP == 2 || NP == 4, "one, two or four points per lane");
   float p[NP][3];
   bool live[NP];
 #pragma unroll
@@ -484,58 +486,90 @@ __device__ __forceinline__ void bh_walk_cursor(const float4* __restrict__ pre,
   }
   const int end = front[f].end;
   int nx[NP];
+  int first = end;
 #pragma unroll
-  for (int q = 0; q < NP; ++q) nx[q] = live[q] ? front[f].node : end;
-  int v = (int)__reduce_min_sync(FULL, (unsigned)(NP == 2 ? min(nx[0], nx[NP - 1]) : nx[0]));
+  for (int q = 0; q < NP; ++q) {
+    nx[q] = live[q] ? front[f].node : end;
+    first = min(first, nx[q]);
+  }
+  int v = (int)__reduce_min_sync(FULL, (unsigned)first);
   unsigned k = 0;
-  if constexpr (NP == 2) {
-    const f2 nyx = f2_pack(-y[0].x, -y[1].x), nyy = f2_pack(-y[0].y, -y[1].y);
-    const f2 nyz = f2_pack(-y[0].z, -y[1].z);
+  if constexpr (NP >= 2) {
+    constexpr int NR = NP / 2;  // packed pairs of points (2r, 2r + 1)
+    f2 nyx[NR], nyy[NR], nyz[NR], px2[NR], py2[NR], pz2[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      nyx[r] = f2_pack(-y[2 * r].x, -y[2 * r + 1].x);
+      nyy[r] = f2_pack(-y[2 * r].y, -y[2 * r + 1].y);
+      nyz[r] = f2_pack(-y[2 * r].z, -y[2 * r + 1].z);
+      px2[r] = f2_pack(p[2 * r][0], p[2 * r + 1][0]);
+      py2[r] = f2_pack(p[2 * r][1], p[2 * r + 1][1]);
+      pz2[r] = f2_pack(p[2 * r][2], p[2 * r + 1][2]);
+    }
     const f2 th2 = f2_pack(theta2, theta2), e2 = f2_pack(eps2, eps2);
-    f2 px2 = f2_pack(p[0][0], p[1][0]), py2 = f2_pack(p[0][1], p[1][1]), pz2 = f2_pack(p[0][2], p[1][2]);
     while (v < end) {
       const float4 cm = pre[2 * v];
       const float4 ri = pre[2 * v + 1];
       const int skip = __float_as_int(ri.y);
-      const f2 dx = f2_add(f2_pack(cm.x, cm.x), nyx), dy = f2_add(f2_pack(cm.y, cm.y), nyy);
-      const f2 dz = f2_add(f2_pack(cm.z, cm.z), nyz);
-      const f2 d2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
-      float o0, o1, e0, e1;
-      f2_unpack(f2_mul(th2, d2), o0, o1);
-      f2_unpack(f2_add(d2, e2), e0, e1);
-      const bool act0 = nx[0] == v, act1 = nx[1] == v;
-      const bool acc0 = act0 && ri.x < o0, acc1 = act1 && ri.x < o1;
-      const f2 inv = f2_pack(rsqrt_fast(e0), rsqrt_fast(e1));
-      const f2 w = f2_mul(f2_pack(cm.w, cm.w), f2_mul(f2_mul(inv, inv), inv));
-      float w0, w1;
-      f2_unpack(w, w0, w1);
-      const f2 wsel = f2_pack(acc0 ? w0 : 0.f, acc1 ? w1 : 0.f);
-      px2 = f2_fma(wsel, dx, px2);
-      py2 = f2_fma(wsel, dy, py2);
-      pz2 = f2_fma(wsel, dz, pz2);
-      cnt[0] += acc0;
-      cnt[1] += acc1;
-      nx[0] = act0 ? v + (acc0 ? skip : 1) : nx[0];
-      nx[1] = act1 ? v + (acc1 ? skip : 1) : nx[1];
+      const f2 cx = f2_pack(cm.x, cm.x), cy = f2_pack(cm.y, cm.y), cz = f2_pack(cm.z, cm.z);
+      const f2 cw = f2_pack(cm.w, cm.w);
+      int lo = end;
+#pragma unroll
+      for (int r = 0; r < NR; ++r) {
+        const f2 dx = f2_add(cx, nyx[r]), dy = f2_add(cy, nyy[r]), dz = f2_add(cz, nyz[r]);
+        const f2 d2 = f2_fma(dx, dx, f2_fma(dy, dy, f2_mul(dz, dz)));
+        float o0, o1, e0, e1;
+        f2_unpack(f2_mul(th2, d2), o0, o1);
+        f2_unpack(f2_add(d2, e2), e0, e1);
+        const bool act0 = nx[2 * r] == v, act1 = nx[2 * r + 1] == v;
+        const bool acc0 = act0 && ri.x < o0, acc1 = act1 && ri.x < o1;
+        const f2 inv = f2_pack(rsqrt_fast(e0), rsqrt_fast(e1));
+        const f2 w = f2_mul(cw, f2_mul(f2_mul(inv, inv), inv));
+        float w0, w1;
+        f2_unpack(w, w0, w1);
+        const f2 wsel = f2_pack(acc0 ? w0 : 0.f, acc1 ? w1 : 0.f);
+        px2[r] = f2_fma(wsel, dx, px2[r]);
+        py2[r] = f2_fma(wsel, dy, py2[r]);
+        pz2[r] = f2_fma(wsel, dz, pz2[r]);
+        cnt[2 * r] += acc0;
+        cnt[2 * r + 1] += acc1;
+        nx[2 * r] = act0 ? v + (acc0 ? skip : 1) : nx[2 * r];
+        nx[2 * r + 1] = act1 ? v + (acc1 ? skip : 1) : nx[2 * r + 1];
+        lo = min(lo, min(nx[2 * r], nx[2 * r + 1]));
+      }
 #if FGA_BH_CURSOR_VOTE
-      v = __any_sync(FULL, (act0 && !acc0) || (act1 && !acc1)) ? v + 1 : v + skip;
+      {
+        bool rej = false;
+#pragma unroll
+        for (int q = 0; q < NP; ++q) rej = rej || nx[q] == v + 1;
+        v = __any_sync(FULL, rej) ? v + 1 : v + skip;
+      }
 #else
-      v = (int)__reduce_min_sync(FULL, (unsigned)min(nx[0], nx[1]));
+      v = (int)__reduce_min_sync(FULL, (unsigned)lo);
 #endif
       if ((++k & 31u) == 0u) {
-        f2_unpack(px2, p[0][0], p[1][0]);
-        f2_unpack(py2, p[0][1], p[1][1]);
-        f2_unpack(pz2, p[0][2], p[1][2]);
 #pragma unroll
-        for (int q = 0; q < 2; ++q)
+        for (int r = 0; r < NR; ++r) {
+          f2_unpack(px2[r], p[2 * r][0], p[2 * r + 1][0]);
+          f2_unpack(py2[r], p[2 * r][1], p[2 * r + 1][1]);
+          f2_unpack(pz2[r], p[2 * r][2], p[2 * r + 1][2]);
+          px2[r] = py2[r] = pz2[r] = f2_pack(0.f, 0.f);
+        }
 #pragma unroll
-          for (int c = 0; c < 3; ++c) comp_add(h[q][c], l[q][c], p[q][c]);
-        px2 = py2 = pz2 = f2_pack(0.f, 0.f);
+        for (int q = 0; q < NP; ++q)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            comp_add(h[q][c], l[q][c], p[q][c]);
+            p[q][c] = 0.f;
+          }
       }
     }
-    f2_unpack(px2, p[0][0], p[1][0]);
-    f2_unpack(py2, p[0][1], p[1][1]);
-    f2_unpack(pz2, p[0][2], p[1][2]);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      f2_unpack(px2[r], p[2 * r][0], p[2 * r + 1][0]);
+      f2_unpack(py2[r], p[2 * r][1], p[2 * r + 1][1]);
+      f2_unpack(pz2[r], p[2 * r][2], p[2 * r + 1][2]);
+    }
   } else {
     while (v < end) {
       const float4 cm = pre[2 * v];

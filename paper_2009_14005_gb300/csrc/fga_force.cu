@@ -212,9 +212,6 @@ int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const
 // groups, bh_task_pre) or cooperative (64-point groups, one walk for the
 // warp, bh_walk<2>), chosen by bh_walk_kind. Tasks are handed out
 // dynamically from a counter in DevState; the last warp to finish resets it.
-#ifndef FGA_BH_WARPS
-#define FGA_BH_WARPS 4
-#endif
 static constexpr int BH_WARPS = FGA_BH_WARPS;
 
 #ifndef FGA_BH_MINBLOCKS
@@ -225,8 +222,12 @@ static constexpr int BH_WARPS = FGA_BH_WARPS;
 // lane, one walk for the warp with saved sibling ranges (bh_walk); 3 / 4 =
 // two / one points per lane, one walk for the warp that follows every
 // point's own walk (bh_walk_cursor).
+// Resident blocks per SM the register budget of each walk is sized for: the
+// walk with four points per lane holds twice the per-point registers.
+constexpr int bh_min_blocks(int kind) { return kind == 5 ? FGA_BH_MINBLOCKS / 2 : FGA_BH_MINBLOCKS; }
+
 template <int KIND>
-__global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const float4* __restrict__ pre,
+__global__ void __launch_bounds__(BH_WARPS * 32, bh_min_blocks(KIND)) k_bh(const float4* __restrict__ pre,
                                                          const float4* __restrict__ Y0, int64_t M,
                                                          const FrontCell* __restrict__ front, int K,
                                                          int C,
@@ -237,20 +238,36 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
                                                          unsigned* __restrict__ cost,
                                                          unsigned long long* __restrict__ mask,
                                                          unsigned* __restrict__ terms) {
-  constexpr int PL = (KIND == 0 || KIND == 4) ? 1 : 2;  // template points per lane
+  constexpr int PL = (KIND == 0 || KIND == 4) ? 1 : (KIND == 5 ? 4 : 2);  // template points per lane
   if (ds->done) return;
   const int lane = threadIdx.x & 31;
   const Xf xf = load_xf(ds);
   const unsigned ntasks = bh_tasks(M, C, PL);
   unsigned long long total = 0;
+#if FGA_BH_BLOCK_TASKS
+  __shared__ unsigned s_slot;
+#endif
   for (;;) {
     unsigned slot = 0;
+#if FGA_BH_BLOCK_TASKS
+    if (threadIdx.x == 0) s_slot = atomicAdd(&ds->bh_next, 1u);
+    __syncthreads();
+    slot = s_slot;
+    __syncthreads();
+#else
     if (lane == 0) slot = atomicAdd(&ds->bh_next, 1u);
     slot = __shfl_sync(FULL, slot, 0);
+#endif
     if (slot >= ntasks) break;
     unsigned task = order ? order[slot] : slot;
     if (task >= ntasks) task = slot;  // never index past the task range
+#if FGA_BH_BLOCK_TASKS
+    // the block's warps take adjacent groups; a group past the template has
+    // no valid point and adds nothing
+    const unsigned g = (task / (unsigned)C) * BH_WARPS + (threadIdx.x >> 5), c = task % (unsigned)C;
+#else
     const unsigned g = task / (unsigned)C, c = task % (unsigned)C;
+#endif
     const unsigned f0 = (unsigned)(((uint64_t)c * K) / C), f1 = (unsigned)(((uint64_t)(c + 1) * K) / C);
     int64_t i[PL];
     bool valid[PL];
@@ -275,7 +292,7 @@ __global__ void __launch_bounds__(BH_WARPS * 32, FGA_BH_MINBLOCKS) k_bh(const fl
       else
         bh_walk_cursor<PL>(pre, front, f, y, valid, eps2, theta2, h, lo, cnt, steps);
     }
-    if (cost && lane == 0) cost[task] = steps + 1u;
+    if (cost && lane == 0 && (!FGA_BH_BLOCK_TASKS || threadIdx.x == 0)) cost[task] = steps + 1u;
 #pragma unroll
     for (int q = 0; q < PL; ++q) {
       // a 32-point slice in which no point added a term leaves exact zeros:
@@ -318,7 +335,7 @@ static int bh_grid(int64_t M, int C) {
     cached.store(b);
   }
   const int64_t tasks = bh_tasks(M, C, bh_points_per_lane(KIND));
-  const int64_t need = (tasks + BH_WARPS - 1) / BH_WARPS;
+  const int64_t need = FGA_BH_BLOCK_TASKS ? tasks : (tasks + BH_WARPS - 1) / BH_WARPS;
   return (int)std::max<int64_t>(1, std::min<int64_t>(need, (int64_t)per_sm * sm_count()));
 }
 
@@ -327,15 +344,16 @@ int bh_walk_kind(int64_t M, int walk) {
   if (walk == FGA_WALK_COOP) return 2;
   if (walk == FGA_WALK_CURSOR) return 3;
   if (walk == FGA_WALK_CURSOR32) return 4;
+  if (walk == FGA_WALK_CURSOR128) return 5;
   const int64_t warps = (int64_t)sm_count() * 32;
-  return M >= (int64_t)FGA_BH_COOP_POINTS_PER_WARP * warps ? 2 : 0;
+  return M >= (int64_t)FGA_BH_COOP_POINTS_PER_WARP * warps ? 3 : 0;
 }
 
 int bh_chunks(int64_t M, int K, int kind) {
   if (FGA_BH_TASKS_PER_WARP <= 0 || K <= 1) return K < 1 ? 1 : K;
   const int pl = bh_points_per_lane(kind);
   const int64_t groups = (M + 32 * pl - 1) / (32 * pl);
-  const int64_t target = (int64_t)FGA_BH_TASKS_PER_WARP * sm_count() * BH_WARPS * FGA_BH_MINBLOCKS;
+  const int64_t target = (int64_t)FGA_BH_TASKS_PER_WARP * sm_count() * BH_WARPS * bh_min_blocks(kind);
   const int64_t c = (target + groups - 1) / groups;
   return (int)std::max<int64_t>(1, std::min<int64_t>(c, K));
 }
@@ -355,6 +373,8 @@ int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, floa
     FGA_BH_CASE(3);
   else if (kind == 4)
     FGA_BH_CASE(4);
+  else if (kind == 5)
+    FGA_BH_CASE(5);
   else
     FGA_BH_CASE(0);
 #undef FGA_BH_CASE

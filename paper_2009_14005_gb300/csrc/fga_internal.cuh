@@ -212,23 +212,37 @@ int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, floa
 // hold ntasks + TASK_ORDER_SCRATCH entries (the tail is the sort's scratch).
 constexpr unsigned TASK_ORDER_SCRATCH = 8192;
 
-// Barnes-Hut tasks are (group of 32 * pl template points, frontier cell),
-// pl points per lane (points g*32*pl + 32*q + lane, q < pl).
-// bh_walk_kind(M, walk): 0 for per-lane walks (pl = 1), 2 for the
-// cooperative walk with two points per lane (pl = 2); `walk` is
-// fga_params.bh_walk. The cooperative walk costs fewer instructions per point
-// but makes half as many tasks, each longer; FGA_WALK_AUTO takes it when the
-// template has at least FGA_BH_COOP_POINTS_PER_WARP points per resident warp,
-// so that the heaviest tasks (a group's own near field) still spread over
-// every warp.
+// Barnes-Hut tasks are (group of 32 * pl template points, chunk of frontier
+// cells), pl points per lane (points g*32*pl + 32*q + lane, q < pl).
+// bh_walk_kind(M, walk) maps fga_params.bh_walk to the kernel's walk: 0 for
+// per-lane walks (pl = 1), 2 for the walk with saved sibling ranges (pl = 2),
+// 3 / 4 for the union walk with two / one points per lane. FGA_WALK_AUTO
+// takes the union walk with two points per lane when the template has at
+// least FGA_BH_COOP_POINTS_PER_WARP points per resident warp, else per-lane
+// walks: a walk for the whole warp costs fewer instructions and loads per
+// point, but makes half as many tasks, each longer, and the heaviest ones (a
+// group's own near field) must still spread over every warp.
 #ifndef FGA_BH_COOP_POINTS_PER_WARP
 #define FGA_BH_COOP_POINTS_PER_WARP 96
 #endif
 int bh_walk_kind(int64_t M, int walk);
-inline int bh_points_per_lane(int kind) { return (kind == 0 || kind == 4) ? 1 : 2; }
-// Tasks of a launch: (group, chunk), C chunks per group.
+inline int bh_points_per_lane(int kind) { return (kind == 0 || kind == 4) ? 1 : (kind == 5 ? 4 : 2); }
+// Warps per Barnes-Hut block.
+#ifndef FGA_BH_WARPS
+#define FGA_BH_WARPS 4
+#endif
+// With FGA_BH_BLOCK_TASKS, a block takes its tasks as a whole: FGA_BH_WARPS
+// adjacent groups on the same chunk, one per warp, so that the block's warps
+// walk nearly the same records at the same time and share them in L1.
+#ifndef FGA_BH_BLOCK_TASKS
+#define FGA_BH_BLOCK_TASKS 0
+#endif
+// Scheduling units of a launch: (group, chunk), C chunks per group, or with
+// FGA_BH_BLOCK_TASKS (block of FGA_BH_WARPS groups, chunk).
 __host__ __device__ inline unsigned bh_tasks(int64_t M, int C, int pl) {
-  return (unsigned)((M + 32 * pl - 1) / (32 * pl)) * (unsigned)C;
+  const int64_t groups = (M + 32 * pl - 1) / (32 * pl);
+  const int64_t units = FGA_BH_BLOCK_TASKS ? (groups + FGA_BH_WARPS - 1) / FGA_BH_WARPS : groups;
+  return (unsigned)units * (unsigned)C;
 }
 // The K frontier cells are cut into C chunks of consecutive cells (chunk c:
 // cells [c K / C, (c + 1) K / C)); a task walks one chunk for its group, so

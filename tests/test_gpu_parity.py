@@ -163,8 +163,8 @@ def test_direct_forces_with_template_masses(fga, orc):
 # --------------------------------------------------------------------------- BHForce
 
 # fga_params.bh_walk: per-point walks; one walk per 64 points with saved
-# ranges; one walk per 64 / 32 points following every point's own walk
-WALKS = {"lane": 1, "coop": 2, "cursor": 3, "cursor32": 4}
+# ranges; one walk per 64 / 32 / 128 points following every point's own walk
+WALKS = {"lane": 1, "coop": 2, "cursor": 3, "cursor32": 4, "cursor128": 5}
 
 
 @pytest.mark.parametrize("walk", list(WALKS))
@@ -200,7 +200,7 @@ def test_bh_forces_match_oracle(fga, orc, theta, walk):
         np.testing.assert_array_equal(terms, len(Xn))
 
 
-@pytest.mark.parametrize("m", [1, 31, 33, 64, 65, 1000])
+@pytest.mark.parametrize("m", [1, 31, 33, 64, 65, 127, 129, 1000])
 def test_bh_walks_take_the_same_terms(fga, orc, m):
     # Both walks judge every (point, node) pair with the same FP32 arithmetic,
     # in the same depth-first order: the term counts agree exactly, the
@@ -226,12 +226,12 @@ def test_bh_walks_take_the_same_terms(fga, orc, m):
     # compensated sums differ, so they agree far below the bar above
     p = fga.params(theta=0.5, eps=0.2)
     t = fga.fga_tree_build(_cuda(Xn), _cuda(mX), p)
-    for walk in ("lane", "cursor", "cursor32"):
+    for walk in ("lane", "cursor", "cursor32", "cursor128"):
         _, terms = fga.fga_forces_terms(t, _cuda(Yn), None, fga.params(theta=0.5, eps=0.2,
                                                                          bh_walk=WALKS[walk]))
         out[walk + "_terms"] = terms.cpu().numpy()
-    np.testing.assert_array_equal(out["cursor_terms"], out["lane_terms"])
-    np.testing.assert_array_equal(out["cursor32_terms"], out["lane_terms"])
+    for walk in ("cursor", "cursor32", "cursor128"):
+        np.testing.assert_array_equal(out[walk + "_terms"], out["lane_terms"], err_msg=walk)
 
 
 # --------------------------------------------------------------------------- Algorithm 2
