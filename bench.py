@@ -609,7 +609,7 @@ def run_ours(a):
         s, tl = v.pop("_s"), v.pop("_tl")
         kn = "k_direct" if key == "all_pairs" else "k_bh"
         r = roofline_of(kn, s["inter"], s["force_ms"], s["force_launches"], tl, peaks, peak_src, sms,
-                        "%s_%s.md" % (kn, "planar-direct" if key == "all_pairs" else a.workload))
+                        "%s_%s.md" % (kn, a.workload))
         v["roofline_frac"] = r["frac"]
         v["mean_launch_ms"] = r["mean_launch_ms"]
         v.pop("k_bh_frac", None)

@@ -250,7 +250,7 @@ __host__ __device__ inline unsigned bh_tasks(int64_t M, int C, int pl) {
 // is the fewest chunks that still give every resident warp about
 // FGA_BH_TASKS_PER_WARP tasks (0: C = K, one frontier cell per task).
 #ifndef FGA_BH_TASKS_PER_WARP
-#define FGA_BH_TASKS_PER_WARP 16
+#define FGA_BH_TASKS_PER_WARP 32
 #endif
 int bh_chunks(int64_t M, int K, int kind);
 int launch_task_order(const unsigned* cost, unsigned ntasks, unsigned* order, cudaStream_t s);
