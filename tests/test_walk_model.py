@@ -170,3 +170,62 @@ def test_saved_ranges_stay_within_the_depth_bound(orc):
     np.testing.assert_array_equal(terms, c_o)
     # the GPU walk keeps saved range k in lane k's registers: 32 lanes, 20 levels
     assert 15 <= most <= 20
+
+
+def _union_walk(rec, Y, theta, eps):
+    """One walk for a group of points that follows every point's own
+    stackless walk: each point keeps the record its walk reads next (nx); the
+    group visits the smallest nx, and the points whose nx it is judge that
+    record as their own walk would. Returns the forces, term counts, the
+    visited records and whether every step went to v + 1 or v + size(v)."""
+    com, mass, l2, skip = rec
+    P, n = len(Y), len(skip)
+    acc = np.zeros((P, 3))
+    terms = np.zeros(P, dtype=np.int64)
+    nx = np.zeros(P, dtype=np.int64)
+    visited, successors_ok = [], True
+    v = 0
+    while v < n:
+        visited.append(v)
+        act = nx == v
+        d = com[v] - Y
+        r2 = (d * d).sum(1)
+        accept = act & (l2[v] < theta * theta * r2)
+        acc[accept] += (mass[v] * d[accept]) / ((r2[accept] + eps * eps) ** 1.5)[:, None]
+        terms += accept
+        nx[accept] = v + skip[v]
+        nx[act & ~accept] = v + 1
+        nv = int(nx.min())
+        successors_ok &= nv in (v + 1, v + skip[v]) or nv >= n
+        v = nv
+    return acc, terms, visited, successors_ok
+
+
+@pytest.mark.parametrize("name", ["gauss", "dups", "shallow"])
+@pytest.mark.parametrize("theta", [0.0, 0.5, 0.9])
+def test_union_walk_takes_each_points_bhforce_terms(orc, name, theta):
+    # The GPU's union walk (k_bh<3>/<4>/<5>) modelled on the CPU: each point
+    # takes exactly the oracle's BHForce terms, the group visits exactly the
+    # union of its points' own walks, and the next record is always v + 1 or
+    # v + size(v) (a waiting point accepted an ancestor of v).
+    X, m, depth = _clouds()[name]
+    tree = orc.Tree(X, m, max_depth=depth)
+    rec = _records(tree.export(), X, m)
+    rng = np.random.default_rng(8)
+    c = X[rng.integers(len(X))]
+    near = X[np.argsort(((X - c) ** 2).sum(1))[:48]] + rng.normal(scale=0.01, size=(48, 3))
+    Y = np.vstack([near, rng.uniform(X.min(0), X.max(0), size=(16, 3))])
+    a_o, c_o = tree.bh_acc(Y, 1.0, 0.1, theta)
+    a, terms, visited, ok = _union_walk(rec, Y, theta, 0.1)
+    np.testing.assert_array_equal(terms, c_o)
+    np.testing.assert_allclose(a, a_o, rtol=1e-11, atol=1e-12 * np.abs(a_o).max())
+    assert ok
+    own = set()
+    for y in Y:
+        com, mass, l2, skip = rec
+        v = 0
+        while v < len(skip):
+            own.add(v)
+            d = com[v] - y
+            v += skip[v] if l2[v] < theta * theta * (d @ d) else 1
+    assert visited == sorted(own)
