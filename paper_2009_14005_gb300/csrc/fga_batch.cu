@@ -170,10 +170,8 @@ __global__ void __launch_bounds__(EPI_BS) k_batch_epilogue(const PairDev* __rest
   if (!s_last) return;
   __threadfence();
   epi_last_reduce(P.partials, P.nblk, s_red);
+  rigid_step_block(s_red, P.M, ds, P.ep, nullptr, P.inter_add);
   if (threadIdx.x == 0) {
-    double red[NRED];
-    for (int k = 0; k < NRED; ++k) red[k] = s_red[k];
-    rigid_step(red, P.M, ds, P.ep, nullptr, P.inter_add);
     *P.counter = 0u;
     __threadfence();
   }

@@ -153,28 +153,40 @@ static __device__ bool polar_rotation(const double C[9], double R[9]) {
   // scaled steps in FP32, |X|_F ~ 1 throughout
   float Xf[9];
   for (int k = 0; k < 9; ++k) Xf[k] = (float)(C[k] * s0);
+  // The scale g only speeds the iteration up (any g > 0 keeps the limit) and
+  // the FP32 steps only have to come within about 1e-6 of U V^T, so the
+  // reciprocal and the fourth root are the SFU's approximations.
   for (int it = 0; it < 40; ++it) {
     float cf[9];
     const float det = cof3(Xf, cf);
     if (!(det > 1e-6f)) return false;  // near rank 2 (or det < 0): the eigen route decides
-    const float idet = 1.0f / det;
-    float xx = 0.f, ii = 0.f;
+    float idet;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(idet) : "f"(det));
+    float x2[9], c2[9];
     for (int k = 0; k < 9; ++k) {
       cf[k] *= idet;
-      xx = fmaf(Xf[k], Xf[k], xx);
-      ii = fmaf(cf[k], cf[k], ii);
+      x2[k] = Xf[k] * Xf[k];
+      c2[k] = cf[k] * cf[k];
     }
-    const float g = sqrtf(sqrtf(ii / xx));
-    const float a = 0.5f * g, b = 0.5f / g;
-    float change = 0.f;
+    const float xx = ((x2[0] + x2[1]) + (x2[2] + x2[3])) + ((x2[4] + x2[5]) + (x2[6] + x2[7])) + x2[8];
+    const float ii = ((c2[0] + c2[1]) + (c2[2] + c2[3])) + ((c2[4] + c2[5]) + (c2[6] + c2[7])) + c2[8];
+    float ixx;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ixx) : "f"(xx));
+    const float r4 = rsqrt_fast(ii * ixx);  // |X|_F / |X^-T|_F
+    const float g = rsqrt_fast(r4);         // (|X^-T|_F / |X|_F)^(1/2)
+    const float a = 0.5f * g, b = 0.5f * r4 * g;  // 1/g = r4 * g
+    float d2[9];
     for (int k = 0; k < 9; ++k) {
       const float xn = fmaf(a, Xf[k], b * cf[k]);
-      change = fmaf(xn - Xf[k], xn - Xf[k], change);
+      d2[k] = (xn - Xf[k]) * (xn - Xf[k]);
       Xf[k] = xn;
     }
+    const float change = ((d2[0] + d2[1]) + (d2[2] + d2[3])) + ((d2[4] + d2[5]) + (d2[6] + d2[7])) + d2[8];
     if (change < 1e-12f) break;
   }
-  // unscaled steps in FP64 from the FP32 iterate: the error squares per step
+  // unscaled steps in FP64 from the FP32 iterate: the error squares per
+  // step, so from about 1e-6 two steps reach the FP64 fixed point; the test
+  // (and further steps, for a poorly converged start) follows them
   double X[9];
   for (int k = 0; k < 9; ++k) X[k] = (double)Xf[k];
   for (int it = 0; it < 8; ++it) {
@@ -182,6 +194,10 @@ static __device__ bool polar_rotation(const double C[9], double R[9]) {
     const double det = cof3(X, cf);
     if (!(det > 1e-9)) return false;
     const double h = 0.5 * rcp64(det);
+    if (it < 1) {
+      for (int k = 0; k < 9; ++k) X[k] = fma(h, cf[k], 0.5 * X[k]);
+      continue;
+    }
     double dd[9];
     for (int k = 0; k < 9; ++k) {
       const double xn = fma(h, cf[k], 0.5 * X[k]);
@@ -218,8 +234,33 @@ __device__ __forceinline__ bool planar_rotation(const double C[9], double R[9]) 
 }
 
 // One thread: reductions -> C -> (R', t') -> compose, convergence, next-iteration constants.
-static __device__ void rigid_step(const double* red, int64_t M, DevState* ds, const EpiParams& ep,
-                           double* traj, unsigned long long inter_add) {
+static __device__ void rigid_step_on(const double* red, int64_t M, DevState* ds, const EpiParams& ep,
+                                     double* traj, unsigned long long inter_add);
+constexpr int EPI_BS_MIN = 128;  // fewest threads of a block that calls rigid_step_block
+
+// Called by every thread of the block that finishes an iteration: the state
+// is copied into shared memory by the block (8 bytes per thread, one round
+// trip), the fit runs on that copy in thread 0, and the block copies it back.
+// A single thread reading the fields in global memory as the fit needs them
+// makes each load wait behind its own earlier stores to the same struct, one
+// L2 round trip after another. red: the NRED reduced values (shared memory).
+static __device__ void rigid_step_block(const double* red, int64_t M, DevState* ds_g, const EpiParams& ep,
+                                        double* traj, unsigned long long inter_add) {
+  static_assert(sizeof(DevState) % sizeof(unsigned long long) == 0, "state copied in 8-byte words");
+  constexpr int NW = (int)(sizeof(DevState) / sizeof(unsigned long long));
+  static_assert(NW <= EPI_BS_MIN, "one word per thread");
+  __shared__ DevState s_state;
+  unsigned long long* sw = reinterpret_cast<unsigned long long*>(&s_state);
+  unsigned long long* gw = reinterpret_cast<unsigned long long*>(ds_g);
+  if (threadIdx.x < NW) sw[threadIdx.x] = __ldcg(gw + threadIdx.x);
+  __syncthreads();
+  if (threadIdx.x == 0) rigid_step_on(red, M, &s_state, ep, traj, inter_add);
+  __syncthreads();
+  if (threadIdx.x < NW) gw[threadIdx.x] = sw[threadIdx.x];
+}
+
+static __device__ void rigid_step_on(const double* red, int64_t M, DevState* ds, const EpiParams& ep,
+                                     double* traj, unsigned long long inter_add) {
   const double Md = (double)M;
   double ybar[3], mud[3];
   for (int k = 0; k < 3; ++k) {

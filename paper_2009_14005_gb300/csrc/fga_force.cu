@@ -518,10 +518,8 @@ __global__ void __launch_bounds__(EPI_BS) k_epilogue(const float4* __restrict__ 
   if (!s_last) return;
   __threadfence();
   epi_last_reduce(partials, (int)gridDim.x, s_red);
+  rigid_step_block(s_red, M, ds, ep, traj, inter_add);
   if (threadIdx.x == 0) {
-    double red[NRED];
-    for (int k = 0; k < NRED; ++k) red[k] = s_red[k];
-    rigid_step(red, M, ds, ep, traj, inter_add);
     *counter = 0u;
     __threadfence();
   }
