@@ -594,7 +594,57 @@ static int state_create_checked(const float* Xn, const float* mX, int64_t N, con
   return FGA_OK;
 }
 
+static int step_launches(fga_state* st, int n_iter, cudaStream_t s);
+
+// Without per-launch timing, n_iter >= FGA_STEP_GRAPH_MIN iterations are
+// captured as one CUDA graph on a private stream ordered after `s` and
+// launched once (no host round trip per launch; the GPU runs the loop's
+// launches back to back). The graph, its stream and events are released by
+// the runtime when the work completes, so the call stays asynchronous.
+#ifndef FGA_STEP_GRAPH_MIN
+#define FGA_STEP_GRAPH_MIN 4
+#endif
 static int step_impl(fga_state* st, int n_iter, cudaStream_t s) {
+  if (st->p.profile || n_iter < FGA_STEP_GRAPH_MIN) return step_launches(st, n_iter, s);
+  cudaStream_t cs = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  struct Release {
+    cudaStream_t& cs;
+    cudaEvent_t& a;
+    cudaEvent_t& b;
+    cudaGraph_t& g;
+    cudaGraphExec_t& e;
+    ~Release() {
+      if (e) cudaGraphExecDestroy(e);
+      if (g) cudaGraphDestroy(g);
+      if (a) cudaEventDestroy(a);
+      if (b) cudaEventDestroy(b);
+      if (cs) cudaStreamDestroy(cs);
+    }
+  } release{cs, ev_in, ev_out, graph, exec};
+  FGA_CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  FGA_CUDA_TRY(cudaEventCreateWithFlags(&ev_in, cudaEventDisableTiming));
+  FGA_CUDA_TRY(cudaEventCreateWithFlags(&ev_out, cudaEventDisableTiming));
+  FGA_CUDA_TRY(cudaEventRecord(ev_in, s));
+  FGA_CUDA_TRY(cudaStreamWaitEvent(cs, ev_in, 0));
+  FGA_CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  const int lrc = step_launches(st, n_iter, cs);
+  const cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+  if (lrc != FGA_OK || ce != cudaSuccess) {
+    if (lrc == FGA_OK)
+      set_error(std::string("fga_step: graph capture failed: ") + cudaGetErrorString(ce));
+    return lrc != FGA_OK ? lrc : FGA_ECUDA;
+  }
+  FGA_CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
+  FGA_CUDA_TRY(cudaGraphLaunch(exec, cs));
+  FGA_CUDA_TRY(cudaEventRecord(ev_out, cs));
+  FGA_CUDA_TRY(cudaStreamWaitEvent(s, ev_out, 0));
+  return FGA_OK;
+}
+
+static int step_launches(fga_state* st, int n_iter, cudaStream_t s) {
   const fga_params& p = st->p;
   EpiParams ep{p.G, p.dt, p.eta, p.velocity_mode, (double)p.conv_tol, st->max_traj,
                1.0 / (double)st->M, 1.0 / (double)p.dt};
