@@ -84,3 +84,30 @@ def test_every_workload_has_a_named_config(name):
     json.dumps(cfg)  # serialisable as part of the bench line
     w = bench.workload(a)
     assert w["iters"] > 0 and w["n"] > 0
+
+
+def test_default_workload_is_the_1m_planar_barnes_hut_registration():
+    import bench
+    a = bench.parse_args([])
+    w = bench.workload(a)
+    assert a.workload == "planar-bh" and w["n"] == 1_000_000 and w["method"] == "bh"
+    assert w["theta"] == 0.5 and w["iters"] == 100 and w["masses"] == "uniform"
+    assert bench.workload(bench.parse_args(["--workload", "lidar-bh"]))["masses"] == "knn16"
+
+
+def test_reference_arm_prints_one_json_line(capsys):
+    import json
+    import bench
+    assert bench.main(["--impl", "reference", "--n", "3000", "--steps", "1", "--warmup", "0"]) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"]
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["config"]["workload"].startswith("planar-scene-")
+
+
+def test_ground_truth_summary():
+    import bench
+    m = {"gt_rot": [0.1, 0.3, 0.2], "gt_t": [1e-5, 3e-5, 2e-5]}
+    g = bench.gt_summary(m)
+    assert g["rot_deg_median"] == 0.2 and g["rot_deg_max"] == 0.3 and g["t_rel_max"] == 3e-5
+    assert bench.gt_summary({"gt_rot": [], "gt_t": []}) is None
