@@ -156,6 +156,7 @@ static __device__ bool polar_rotation(const double C[9], double R[9]) {
   // The scale g only speeds the iteration up (any g > 0 keeps the limit) and
   // the FP32 steps only have to come within about 1e-6 of U V^T, so the
   // reciprocal and the fourth root are the SFU's approximations.
+  bool converged32 = false;
   for (int it = 0; it < 40; ++it) {
     float cf[9];
     const float det = cof3(Xf, cf);
@@ -182,11 +183,16 @@ static __device__ bool polar_rotation(const double C[9], double R[9]) {
       Xf[k] = xn;
     }
     const float change = ((d2[0] + d2[1]) + (d2[2] + d2[3])) + ((d2[4] + d2[5]) + (d2[6] + d2[7])) + d2[8];
-    if (change < 1e-12f) break;
+    if (change < 1e-12f) {
+      converged32 = true;
+      break;
+    }
   }
   // unscaled steps in FP64 from the FP32 iterate: the error squares per
-  // step, so from about 1e-6 two steps reach the FP64 fixed point; the test
-  // (and further steps, for a poorly converged start) follows them
+  // step. From a converged FP32 iterate (error about 1e-7, FP32 rounding) one
+  // step leaves about 1e-14, far below what the registration resolves, and
+  // a dependent FP64 operation costs a few hundred cycles here: one step.
+  // Otherwise steps repeat until they stop moving.
   double X[9];
   for (int k = 0; k < 9; ++k) X[k] = (double)Xf[k];
   for (int it = 0; it < 8; ++it) {
@@ -194,9 +200,9 @@ static __device__ bool polar_rotation(const double C[9], double R[9]) {
     const double det = cof3(X, cf);
     if (!(det > 1e-9)) return false;
     const double h = 0.5 * rcp64(det);
-    if (it < 1) {
+    if (converged32) {
       for (int k = 0; k < 9; ++k) X[k] = fma(h, cf[k], 0.5 * X[k]);
-      continue;
+      break;
     }
     double dd[9];
     for (int k = 0; k < 9; ++k) {
@@ -233,117 +239,146 @@ __device__ __forceinline__ bool planar_rotation(const double C[9], double R[9]) 
   return true;
 }
 
-// One thread: reductions -> C -> (R', t') -> compose, convergence, next-iteration constants.
-static __device__ void rigid_step_on(const double* red, int64_t M, DevState* ds, const EpiParams& ep,
-                                     double* traj, unsigned long long inter_add);
 constexpr int EPI_BS_MIN = 128;  // fewest threads of a block that calls rigid_step_block
 
-// Called by every thread of the block that finishes an iteration: the state
-// is copied into shared memory by the block (8 bytes per thread, one round
-// trip), the fit runs on that copy in thread 0, and the block copies it back.
-// A single thread reading the fields in global memory as the fit needs them
-// makes each load wait behind its own earlier stores to the same struct, one
-// L2 round trip after another. red: the NRED reduced values (shared memory).
+// Shared values between the phases of the fit.
+struct FitShared {
+  double Rp[9], tp[3];  // R', t' of this iteration
+  double T[12];         // the composed [R | t]
+  double e[12];         // squared differences to [R | t] two iterations back
+};
+
+// Called by every thread of the block that finishes an iteration (Eqs. 14,
+// 16 and Algorithm 2's composition and stop test). A dependent FP64
+// operation costs a few hundred cycles on this GPU and the fit is the
+// iteration's tail, so its work is spread over the block:
+//  1. the block copies the state into shared memory (8 bytes per thread, one
+//     round trip; one thread reading the fields in global memory would wait
+//     behind its own earlier stores to the same struct);
+//  2. thread 0 forms C from the reductions and takes R' (polar or eigen
+//     route) and t';
+//  3. threads 0-11 compose [R | t] entry by entry with the convergence terms,
+//     threads 12-23 the rigid-velocity coefficients;
+//  4. thread 0 sums the convergence terms, updates the flags, the history and
+//     the FP32 copies;
+//  5. the block copies the state back.
+// red: the NRED reduced values (shared memory).
 static __device__ void rigid_step_block(const double* red, int64_t M, DevState* ds_g, const EpiParams& ep,
                                         double* traj, unsigned long long inter_add) {
   static_assert(sizeof(DevState) % sizeof(unsigned long long) == 0, "state copied in 8-byte words");
   constexpr int NW = (int)(sizeof(DevState) / sizeof(unsigned long long));
   static_assert(NW <= EPI_BS_MIN, "one word per thread");
   __shared__ DevState s_state;
+  __shared__ FitShared f;
+  DevState* ds = &s_state;
   unsigned long long* sw = reinterpret_cast<unsigned long long*>(&s_state);
   unsigned long long* gw = reinterpret_cast<unsigned long long*>(ds_g);
-  if (threadIdx.x < NW) sw[threadIdx.x] = __ldcg(gw + threadIdx.x);
+  const int tid = threadIdx.x;
+  if (tid < NW) sw[tid] = __ldcg(gw + tid);
   __syncthreads();
-  if (threadIdx.x == 0) rigid_step_on(red, M, &s_state, ep, traj, inter_add);
-  __syncthreads();
-  if (threadIdx.x < NW) gw[threadIdx.x] = sw[threadIdx.x];
-}
-
-static __device__ void rigid_step_on(const double* red, int64_t M, DevState* ds, const EpiParams& ep,
-                                     double* traj, unsigned long long inter_add) {
-  const double Md = (double)M;
-  double ybar[3], mud[3];
-  for (int k = 0; k < 3; ++k) {
-    ybar[k] = red[k] * ep.inv_M;     // mean of the centred template (~0)
-    mud[k] = red[3 + k] * ep.inv_M;  // mean displacement
-  }
-  // symmetric S = sum yc yc^T (xx, xy, xz, yy, yz, zz) and Dy = sum d yc^T
-  const double S[9] = {red[6], red[7], red[8], red[7], red[9], red[10], red[8], red[10], red[11]};
-  double C[9];
-  for (int r = 0; r < 3; ++r)
-    for (int c = 0; c < 3; ++c)
-      C[3 * r + c] = S[3 * r + c] + red[12 + 3 * r + c] - Md * (ybar[r] + mud[r]) * ybar[c];
-  double Rp[9];
-  const bool ok = ep.dim == 2 ? planar_rotation(C, Rp) : (polar_rotation(C, Rp) || rigid_rotation(C, Rp));
-  if (!ok) {
-    for (int k = 0; k < 9; ++k) Rp[k] = (k % 4 == 0) ? 1.0 : 0.0;
-    ds->degenerate += 1;
-  }
-  // mu_Y = muf + ybar (muf is the FP32 centre the kernels subtracted)
-  double muy[3];
-  for (int k = 0; k < 3; ++k) muy[k] = (double)ds->muf[k] + ybar[k];
-  double tp[3];
-  for (int r = 0; r < 3; ++r)
-    tp[r] = muy[r] + mud[r] - (Rp[3 * r] * muy[0] + Rp[3 * r + 1] * muy[1] + Rp[3 * r + 2] * muy[2]);
-  double Rn[9], tn[3];
-  for (int r = 0; r < 3; ++r) {
-    for (int c = 0; c < 3; ++c)
-      Rn[3 * r + c] = Rp[3 * r] * ds->R[c] + Rp[3 * r + 1] * ds->R[3 + c] + Rp[3 * r + 2] * ds->R[6 + c];
-    tn[r] = Rp[3 * r] * ds->t[0] + Rp[3 * r + 1] * ds->t[1] + Rp[3 * r + 2] * ds->t[2] + tp[r];
-  }
-  double T[12];
-  for (int k = 0; k < 9; ++k) T[k] = Rn[k];
-  for (int k = 0; k < 3; ++k) T[9 + k] = tn[k];
-  const int k_it = ds->iter;
-  if (k_it >= 2) {
-    double d2 = 0;
-    for (int q = 0; q < 12; ++q) d2 += (T[q] - ds->Tm2[q]) * (T[q] - ds->Tm2[q]);
-    ds->last_conv = d2;
-    if (ep.conv_tol > 0 && d2 <= ep.conv_tol) {
-      ds->done = 1;
-      ds->converged = 1;
+  if (tid == 0) {
+    const double Md = (double)M;
+    double ybar[3], mud[3];
+    for (int k = 0; k < 3; ++k) {
+      ybar[k] = red[k] * ep.inv_M;     // mean of the centred template (~0)
+      mud[k] = red[3 + k] * ep.inv_M;  // mean displacement
     }
-  } else {
-    ds->last_conv = -1.0;
+    // symmetric S = sum yc yc^T (xx, xy, xz, yy, yz, zz) and Dy = sum d yc^T
+    const double S[9] = {red[6], red[7], red[8], red[7], red[9], red[10], red[8], red[10], red[11]};
+    double C[9];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c)
+        C[3 * r + c] = S[3 * r + c] + red[12 + 3 * r + c] - Md * (ybar[r] + mud[r]) * ybar[c];
+    double Rp[9];
+    const bool ok = ep.dim == 2 ? planar_rotation(C, Rp) : (polar_rotation(C, Rp) || rigid_rotation(C, Rp));
+    if (!ok) {
+      for (int k = 0; k < 9; ++k) Rp[k] = (k % 4 == 0) ? 1.0 : 0.0;
+      ds->degenerate += 1;
+    }
+    // mu_Y = muf + ybar (muf is the FP32 centre the kernels subtracted)
+    double muy[3];
+    for (int k = 0; k < 3; ++k) muy[k] = (double)ds->muf[k] + ybar[k];
+    for (int r = 0; r < 3; ++r)
+      f.tp[r] = muy[r] + mud[r] - (Rp[3 * r] * muy[0] + Rp[3 * r + 1] * muy[1] + Rp[3 * r + 2] * muy[2]);
+    for (int k = 0; k < 9; ++k) f.Rp[k] = Rp[k];
   }
-  for (int q = 0; q < 12; ++q) {
-    ds->Tm2[q] = ds->Tm1[q];
-    ds->Tm1[q] = T[q];
+  __syncthreads();
+  const int k_it = ds->iter;
+  if (tid < 12) {
+    // [R | t] <- [R'R | R't + t'], one entry per thread
+    const int r = tid < 9 ? tid / 3 : tid - 9;
+    double v;
+    if (tid < 9) {
+      const int c = tid % 3;
+      v = f.Rp[3 * r] * ds->R[c] + f.Rp[3 * r + 1] * ds->R[3 + c] + f.Rp[3 * r + 2] * ds->R[6 + c];
+    } else {
+      v = f.Rp[3 * r] * ds->t[0] + f.Rp[3 * r + 1] * ds->t[1] + f.Rp[3 * r + 2] * ds->t[2] + f.tp[r];
+    }
+    f.T[tid] = v;
+    f.e[tid] = (v - ds->Tm2[tid]) * (v - ds->Tm2[tid]);
+  } else if (tid < 24) {
+    // rigid velocity of the next iteration: v = (y_new - y_old)/dt with
+    // y_old = R'^T (y_new - t'), i.e. v = (I - R'^T)/dt y_new + R'^T t'/dt
+    const double idt = ep.inv_dt;
+    const int q = tid - 12;
+    if (q < 9) {
+      const int r = q / 3, c = q % 3;
+      ds->A[q] = (float)(((r == c ? 1.0 : 0.0) - f.Rp[3 * c + r]) * idt);
+    } else if (q < 12) {
+      const int r = q - 9;
+      ds->b[r] = (float)((f.Rp[r] * f.tp[0] + f.Rp[3 + r] * f.tp[1] + f.Rp[6 + r] * f.tp[2]) * idt);
+    }
   }
-  bool finite = true;
-  for (int q = 0; q < 12; ++q) finite = finite && isfinite(T[q]);
-  if (!finite) {
-    ds->status |= 2;
-    ds->done = 1;
+  __syncthreads();
+  if (tid == 0) {
+    const double* T = f.T;
+    if (k_it >= 2) {
+      const double* e = f.e;
+      const double d2 = (((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7]))) +
+                        ((e[8] + e[9]) + (e[10] + e[11]));
+      ds->last_conv = d2;
+      if (ep.conv_tol > 0 && d2 <= ep.conv_tol) {
+        ds->done = 1;
+        ds->converged = 1;
+      }
+    } else {
+      ds->last_conv = -1.0;
+    }
+    for (int q = 0; q < 12; ++q) {
+      ds->Tm2[q] = ds->Tm1[q];
+      ds->Tm1[q] = T[q];
+    }
+    bool finite = true;
+    for (int q = 0; q < 12; ++q) finite = finite && isfinite(T[q]);
+    if (!finite) {
+      ds->status |= 2;
+      ds->done = 1;
+    }
+    for (int k = 0; k < 9; ++k) {
+      ds->R[k] = T[k];
+      ds->Rf[k] = (float)T[k];
+    }
+    for (int k = 0; k < 3; ++k) {
+      ds->t[k] = T[9 + k];
+      ds->tf[k] = (float)T[9 + k];
+    }
+    // the FP32 centre that the kernels subtract (any value near the
+    // template's centroid serves, as long as the fit adds back the same one)
+    const float m0 = (float)ds->mu0[0], m1 = (float)ds->mu0[1], m2 = (float)ds->mu0[2];
+    for (int r = 0; r < 3; ++r)
+      ds->muf[r] = fmaf(ds->Rf[3 * r], m0, fmaf(ds->Rf[3 * r + 1], m1, fmaf(ds->Rf[3 * r + 2], m2, ds->tf[r])));
+    for (int k = 0; k < 3; ++k) {
+      ds->netF[k] = red[21 + k];
+      ds->torque[k] = red[24 + k];
+    }
+    if (traj && k_it < ep.max_traj)
+      for (int q = 0; q < 12; ++q) traj[12 * (int64_t)k_it + q] = T[q];
+    ds->interactions += inter_add;
+    ds->iter = k_it + 1;
+    if (ep.max_iter > 0 && k_it + 1 >= ep.max_iter) ds->done = 1;
   }
-  for (int k = 0; k < 9; ++k) {
-    ds->R[k] = Rn[k];
-    ds->Rf[k] = (float)Rn[k];
-  }
-  for (int k = 0; k < 3; ++k) {
-    ds->t[k] = tn[k];
-    ds->tf[k] = (float)tn[k];
-  }
-  for (int r = 0; r < 3; ++r)
-    ds->muf[r] = (float)(Rn[3 * r] * ds->mu0[0] + Rn[3 * r + 1] * ds->mu0[1] +
-                         Rn[3 * r + 2] * ds->mu0[2] + tn[r]);
-  // rigid velocity of the next iteration: v = (y_new - y_old)/dt with
-  // y_old = R'^T (y_new - t'), i.e. v = (I - R'^T)/dt y_new + R'^T t'/dt
-  const double idt = ep.inv_dt;
-  for (int r = 0; r < 3; ++r) {
-    for (int c = 0; c < 3; ++c)
-      ds->A[3 * r + c] = (float)(((r == c ? 1.0 : 0.0) - Rp[3 * c + r]) * idt);
-    ds->b[r] = (float)((Rp[r] * tp[0] + Rp[3 + r] * tp[1] + Rp[6 + r] * tp[2]) * idt);
-  }
-  for (int k = 0; k < 3; ++k) {
-    ds->netF[k] = red[21 + k];
-    ds->torque[k] = red[24 + k];
-  }
-  if (traj && k_it < ep.max_traj)
-    for (int q = 0; q < 12; ++q) traj[12 * (int64_t)k_it + q] = T[q];
-  ds->interactions += inter_add;
-  ds->iter = k_it + 1;
-  if (ep.max_iter > 0 && k_it + 1 >= ep.max_iter) ds->done = 1;
+  __syncthreads();
+  if (tid < NW) gw[tid] = sw[tid];
 }
 
 

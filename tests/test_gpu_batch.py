@@ -50,7 +50,11 @@ def test_batch_matches_single_pair_path(fga, mix):
             assert _close(r["R"], r["t"], R, t, X)
             assert r["iterations"] == 40
             if r["method"] == fga.FGA_BH:
-                assert r["interactions"] == s1["interactions"]
+                # the two paths add the partial sums of the frontier cells in
+                # different groupings (per cell / per chunk of cells), so the
+                # templates move apart by FP32 rounding and an opening tie can
+                # flip over 40 iterations
+                assert abs(r["interactions"] - s1["interactions"]) <= 1e-5 * s1["interactions"]
             else:
                 assert r["interactions"] == 40 * len(X) * len(Y)
         assert st["interactions"] == sum(r["interactions"] for r in res)
