@@ -604,6 +604,21 @@ static int step_launches(fga_state* st, int n_iter, cudaStream_t s);
 #ifndef FGA_STEP_GRAPH_MIN
 #define FGA_STEP_GRAPH_MIN 4
 #endif
+// The executable graph of the calling thread's last capture, kept so that the
+// next registration of the same shape (the same launches with other
+// pointers) updates it in place instead of instantiating a new one. It is
+// reused only once its last launch has completed (`done` has fired) and on
+// the device it was made on.
+struct StepGraphCache {
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  int device = -1;
+  ~StepGraphCache() {
+    // the process may be ending with the runtime torn down: no CUDA calls here
+  }
+};
+static thread_local StepGraphCache t_step_graph;
+
 static int step_impl(fga_state* st, int n_iter, cudaStream_t s) {
   if (st->p.profile || n_iter < FGA_STEP_GRAPH_MIN) return step_launches(st, n_iter, s);
   cudaStream_t cs = nullptr;
@@ -637,10 +652,37 @@ static int step_impl(fga_state* st, int n_iter, cudaStream_t s) {
       set_error(std::string("fga_step: graph capture failed: ") + cudaGetErrorString(ce));
     return lrc != FGA_OK ? lrc : FGA_ECUDA;
   }
-  FGA_CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
+  StepGraphCache& cache = t_step_graph;
+  if (cache.exec && (cache.device != st->device || cudaEventQuery(cache.done) != cudaSuccess)) {
+    // still running (or on another device): leave it to the runtime
+    cudaGetLastError();
+    cudaGraphExecDestroy(cache.exec);
+    cudaEventDestroy(cache.done);
+    cache.exec = nullptr;
+    cache.done = nullptr;
+  }
+  if (cache.exec) {
+    cudaGraphExecUpdateResultInfo info;
+    if (cudaGraphExecUpdate(cache.exec, graph, &info) == cudaSuccess) {
+      exec = cache.exec;  // updated in place
+    } else {
+      cudaGetLastError();
+      cudaGraphExecDestroy(cache.exec);
+      cudaEventDestroy(cache.done);
+    }
+    cache.exec = nullptr;
+    cache.done = nullptr;
+  }
+  if (!exec) FGA_CUDA_TRY(cudaGraphInstantiate(&exec, graph, 0));
   FGA_CUDA_TRY(cudaGraphLaunch(exec, cs));
   FGA_CUDA_TRY(cudaEventRecord(ev_out, cs));
   FGA_CUDA_TRY(cudaStreamWaitEvent(s, ev_out, 0));
+  // keep the executable graph for the next call of this thread
+  cache.exec = exec;
+  cache.done = ev_out;
+  cache.device = st->device;
+  exec = nullptr;
+  ev_out = nullptr;
   return FGA_OK;
 }
 

@@ -313,6 +313,26 @@ def test_convergence_stop_matches_oracle(fga, orc):
     assert abs(st["iterations"] - o["iters"]) <= 1
 
 
+def test_graph_and_plain_launches_agree_bitwise(fga):
+    # fga_step captures its iteration loop as one CUDA graph (and updates the
+    # thread's last graph in place when the shape repeats); with profile = 1 it
+    # launches the same kernels one by one. Shapes alternate so that both the
+    # update and the fresh capture are taken.
+    cases = [(synth.sphere_pair(11)[:2], fga.params(method=fga.FGA_DIRECT, max_iter=30, eps=0.05)),
+             (synth.box_pair(12, 3000)[:2], fga.params(method=fga.FGA_BH, theta=0.5, max_iter=25)),
+             (synth.sphere_pair(13)[:2], fga.params(method=fga.FGA_DIRECT, max_iter=30, eps=0.05)),
+             (synth.sphere_pair(14)[:2], fga.params(method=fga.FGA_DIRECT, max_iter=30, eps=0.05, conv_tol=1e-3))]
+    for (X, Y), p in cases:
+        R1, t1, s1 = fga.fga_register(_cuda(X), _cuda(Y), p)
+        q = fga.params(**{k: getattr(p, k) for k, _ in p._fields_})
+        q.profile = 1
+        R2, t2, s2 = fga.fga_register(_cuda(X), _cuda(Y), q)
+        np.testing.assert_array_equal(R1, R2)
+        np.testing.assert_array_equal(t1, t2)
+        assert s1["iterations"] == s2["iterations"] and s1["interactions"] == s2["interactions"]
+        assert s2["force_launches"] > 0 and s1["force_launches"] == 0
+
+
 def test_host_and_device_inputs_agree_and_runs_are_deterministic(fga):
     X, Y, _, _ = synth.lidar_pair(6, n=5000)
     p = fga.params(method=fga.FGA_BH, theta=0.5, max_iter=20)
