@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch
       const float3 y = place(xf, P.Y0[valid ? i : 0]);
       float hx = 0.f, hy = 0.f, hz = 0.f, lx = 0.f, ly = 0.f, lz = 0.f;
       unsigned count = 0, steps = 0;
-      bh_task_pre(P.pre, P.front, f, y, valid, eps2, theta2, hx, hy, hz, lx, ly, lz, count, steps);
+      bh_task_pre(P.pcm, P.pls, P.front, f, y, valid, eps2, theta2, hx, hy, hz, lx, ly, lz, count, steps);
       if (cost && lane == 0) cost[task] = steps + 1u;
       if (valid) {
         P.hi[(int64_t)f * M + i] = make_float4(hx, hy, hz, 0.f);
@@ -276,7 +276,8 @@ int build_inputs(const fga_pair& q, const Prepared& pr, const fga_params* p, Scr
     int* perm = nullptr;
     if (sc.alloc(&perm, q.M)) return FGA_ENOMEM;
     if ((rc = pack_template(pr.Yn, pr.mYn, p->dt, q.M, true, Y0, perm, s))) return rc;
-    P.pre = t->node_pre;
+    P.pcm = pre_cm(t);
+    P.pls = pre_ls(t);
     P.front = t->front;
     P.K = t->n_front;
   } else {

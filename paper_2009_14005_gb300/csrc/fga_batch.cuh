@@ -17,7 +17,8 @@ constexpr int BATCH_WARPS = 4;
 struct PairDev {
   int method;                 // FGA_DIRECT or FGA_BH
   int K;                      // BH: frontier cells; direct: source chunks
-  const float4* pre;          // BH: depth-first cell records
+  const float4* pcm;          // BH: depth-first cell records (CoM, mass)
+  const float2* pls;          // BH: depth-first cell records (l^2, subtree size)
   const FrontCell* front;     // BH: frontier (record indices)
   const float4* X4;           // direct: reference points and masses
   int64_t N, M;

@@ -154,7 +154,8 @@ static_assert(BH_DEPTH > 20, "the BH walk must hold one saved range per tree lev
 // Adds into the compensated accumulators (hx, lx), ... and the term count;
 // `steps` is the warp's longest walk (the task's cost). A lane with
 // valid == false adds nothing.
-__device__ __forceinline__ void bh_task_pre(const float4* __restrict__ pre, const FrontCell* __restrict__ front,
+__device__ __forceinline__ void bh_task_pre(const float4* __restrict__ pcm, const float2* __restrict__ pls,
+                                            const FrontCell* __restrict__ front,
                                             unsigned f, float3 y, bool valid, float eps2, float theta2,
                                             float& hx, float& hy, float& hz, float& lx, float& ly,
                                             float& lz, unsigned& count, unsigned& steps) {
@@ -165,8 +166,8 @@ __device__ __forceinline__ void bh_task_pre(const float4* __restrict__ pre, cons
     const unsigned first_mask = front[f].first_mask;
     for (int j = 0; j < npath; ++j) {
       const int a = front[f].path[j];
-      const float4 cm = pre[2 * a];
-      const float l2 = pre[2 * a + 1].x;
+      const float4 cm = pcm[a];
+      const float l2 = pls[a].x;
       const float dx = cm.x - y.x, dy = cm.y - y.y, dz = cm.z - y.z;
       const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
       const bool accept = live && l2 < theta2 * d2;
@@ -185,8 +186,8 @@ __device__ __forceinline__ void bh_task_pre(const float4* __restrict__ pre, cons
   int v = live ? front[f].node : end;
   unsigned n = 0;
   while (v < end) {
-    const float4 cm = pre[2 * v];
-    const float4 ri = pre[2 * v + 1];
+    const float4 cm = pcm[v];
+    const float2 ri = pls[v];
     const float dx = cm.x - y.x, dy = cm.y - y.y, dz = cm.z - y.z;
     const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
     const bool accept = ri.x < theta2 * d2;
@@ -229,7 +230,8 @@ static_assert(BH_DEPTH <= 32, "one saved range per lane");
 // term counts cnt[q]; `steps` gains the number of nodes visited (the task's
 // cost).
 template <int NP>
-__device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const FrontCell* __restrict__ front,
+__device__ __forceinline__ void bh_walk(const float4* __restrict__ pcm, const float2* __restrict__ pls,
+                                        const int2* __restrict__ pcf, const FrontCell* __restrict__ front,
                                         unsigned f, const float3 (&y)[NP], const bool (&valid)[NP], float eps2,
                                         float theta2, float (&h)[NP][3], float (&l)[NP][3],
                                         unsigned (&cnt)[NP], unsigned& steps) {
@@ -247,8 +249,8 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const Fr
     const unsigned first_mask = front[f].first_mask;
     for (int j = 0; j < npath; ++j) {
       const int a = front[f].path[j];
-      const float4 cm = pre[2 * a];
-      const float l2 = pre[2 * a + 1].x;
+      const float4 cm = pcm[a];
+      const float l2 = pls[a].x;
       const bool own = (first_mask >> j) & 1u;
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
@@ -290,9 +292,9 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const Fr
   while ((e & 15u) != 0u) {
     ++steps;
     const int v = (int)(e >> 4);
-    const float4 cm = pre[2 * v];
-    const float4 ri = pre[2 * v + 1];
-    const int nchild = __float_as_int(ri.z);
+    const float4 cm = pcm[v];
+    const float2 ri = pls[v];
+    const int nchild = pcf[v].x;
     e += ((unsigned)__float_as_int(ri.y) << 4) - 1u;  // next sibling
     bool rej[NP];
     unsigned r[NP], rany = 0u;
@@ -368,7 +370,7 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const Fr
           f2_unpack(pz2, p[0][2], p[1][2]);
         }
         for (int b = 1; b <= nb; ++b) {
-          const float4 qb = pre[2 * (v + b)];
+          const float4 qb = pcm[v + b];
 #pragma unroll
           for (int q = 0; q < NP; ++q) {
             const float ex = qb.x - y[q].x, ey = qb.y - y[q].y, ez = qb.z - y[q].z;
@@ -445,7 +447,8 @@ __device__ __forceinline__ void bh_walk(const float4* __restrict__ pre, const Fr
 #endif
 
 template <int NP>
-__device__ __forceinline__ void bh_walk_cursor(const float4* __restrict__ pre,
+__device__ __forceinline__ void bh_walk_cursor(const float4* __restrict__ pcm,
+                                               const float2* __restrict__ pls,
                                                const FrontCell* __restrict__ front, unsigned f,
                                                const float3 (&y)[NP], const bool (&valid)[NP],
                                                float eps2, float theta2, float (&h)[NP][3],
@@ -464,8 +467,8 @@ __device__ __forceinline__ void bh_walk_cursor(const float4* __restrict__ pre,
     const unsigned first_mask = front[f].first_mask;
     for (int j = 0; j < npath; ++j) {
       const int a = front[f].path[j];
-      const float4 cm = pre[2 * a];
-      const float l2 = pre[2 * a + 1].x;
+      const float4 cm = pcm[a];
+      const float l2 = pls[a].x;
       const bool own = (first_mask >> j) & 1u;
 #pragma unroll
       for (int q = 0; q < NP; ++q) {
@@ -508,8 +511,8 @@ __device__ __forceinline__ void bh_walk_cursor(const float4* __restrict__ pre,
     }
     const f2 th2 = f2_pack(theta2, theta2), e2 = f2_pack(eps2, eps2);
     while (v < end) {
-      const float4 cm = pre[2 * v];
-      const float4 ri = pre[2 * v + 1];
+      const float4 cm = pcm[v];
+      const float2 ri = pls[v];
       const int skip = __float_as_int(ri.y);
       const f2 cx = f2_pack(cm.x, cm.x), cy = f2_pack(cm.y, cm.y), cz = f2_pack(cm.z, cm.z);
       const f2 cw = f2_pack(cm.w, cm.w);
@@ -572,8 +575,8 @@ __device__ __forceinline__ void bh_walk_cursor(const float4* __restrict__ pre,
     }
   } else {
     while (v < end) {
-      const float4 cm = pre[2 * v];
-      const float4 ri = pre[2 * v + 1];
+      const float4 cm = pcm[v];
+      const float2 ri = pls[v];
       const int skip = __float_as_int(ri.y);
       const float dx = cm.x - y[0].x, dy = cm.y - y[0].y, dz = cm.z - y[0].z;
       const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));

@@ -197,9 +197,9 @@ int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const
 //     cell mass at its CoM);
 //   * otherwise an internal cell's children are visited next, and a leaf
 //     holding several particles adds each of them exactly.
-// The tree is read as depth-first records (fga_tree::node_pre), 32 bytes
-// each (CoM + mass, then l^2, subtree record count, child count, first
-// particle), fetched with two loads from the same sector. A walk needs no
+// The tree is read as depth-first records (fga_tree::node_pre): CoM + mass
+// (16 bytes) and l^2 + subtree record count (8 bytes) in separate arrays, so
+// a 128-byte line holds 8 and 16 consecutive records. A walk needs no
 // stack: after a record whose cell the point accepts it skips the subtree,
 // after a rejected one it continues with the next record (the first child).
 // Warps hold 32 Morton-neighbouring points, so their walks touch mostly the
@@ -227,7 +227,9 @@ static constexpr int BH_WARPS = FGA_BH_WARPS;
 constexpr int bh_min_blocks(int kind) { return kind == 5 ? FGA_BH_MINBLOCKS / 2 : FGA_BH_MINBLOCKS; }
 
 template <int KIND>
-__global__ void __launch_bounds__(BH_WARPS * 32, bh_min_blocks(KIND)) k_bh(const float4* __restrict__ pre,
+__global__ void __launch_bounds__(BH_WARPS * 32, bh_min_blocks(KIND)) k_bh(const float4* __restrict__ pcm,
+                                                         const float2* __restrict__ pls,
+                                                         const int2* __restrict__ pcf,
                                                          const float4* __restrict__ Y0, int64_t M,
                                                          const FrontCell* __restrict__ front, int K,
                                                          int C,
@@ -285,12 +287,12 @@ __global__ void __launch_bounds__(BH_WARPS * 32, bh_min_blocks(KIND)) k_bh(const
     unsigned steps = 0;
     for (unsigned f = f0; f < f1; ++f) {
       if constexpr (KIND == 0)
-        bh_task_pre(pre, front, f, y[0], valid[0], eps2, theta2, h[0][0], h[0][1], h[0][2],
+        bh_task_pre(pcm, pls, front, f, y[0], valid[0], eps2, theta2, h[0][0], h[0][1], h[0][2],
                     lo[0][0], lo[0][1], lo[0][2], cnt[0], steps);
       else if constexpr (KIND == 2)
-        bh_walk<2>(pre, front, f, y, valid, eps2, theta2, h, lo, cnt, steps);
+        bh_walk<2>(pcm, pls, pcf, front, f, y, valid, eps2, theta2, h, lo, cnt, steps);
       else
-        bh_walk_cursor<PL>(pre, front, f, y, valid, eps2, theta2, h, lo, cnt, steps);
+        bh_walk_cursor<PL>(pcm, pls, front, f, y, valid, eps2, theta2, h, lo, cnt, steps);
     }
     if (cost && lane == 0 && (!FGA_BH_BLOCK_TASKS || threadIdx.x == 0)) cost[task] = steps + 1u;
 #pragma unroll
@@ -364,7 +366,8 @@ int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, floa
   unsigned long long* mask = t->n_front <= 64 ? fb.mask : nullptr;
   const int C = bh_chunks(M, t->n_front, kind);
 #define FGA_BH_CASE(KD)                                                                           \
-  k_bh<KD><<<bh_grid<KD>(M, C), BH_WARPS * 32, 0, s>>>(t->node_pre, Y0, M, t->front, t->n_front, C, \
+  k_bh<KD><<<bh_grid<KD>(M, C), BH_WARPS * 32, 0, s>>>(pre_cm(t), pre_ls(t), pre_cf(t), Y0, M,      \
+                                                       t->front, t->n_front, C,                     \
                                                        ds, eps * eps, theta * theta, fb.hi, fb.lo,  \
                                                        order, cost, mask, terms)
   if (kind == 2)

@@ -131,11 +131,11 @@ struct fga_tree {
                                  //  count < 0: leaf, bodies first .. first-count-1
   int2* node_bodies = nullptr;   // n_nodes: body range [x, y) of the cell
   fga::FrontCell* front = nullptr;  // frontier cells (device), depth-first order
-  float4* node_pre = nullptr;    // n_pre x 2 float4, the tree in depth-first pre-order
-                                 // (children in octant order): (CoM, mass), (l^2, subtree
-                                 // size, count as in node_info, first body of a leaf) as
-                                 // int bits; a leaf with nb >= 2 particles is followed by
-                                 // nb single-particle records, one per particle
+  float4* node_pre = nullptr;    // the tree in depth-first pre-order (children in octant
+                                 // order), 32 bytes per record in three arrays of n_pre
+                                 // entries each (pre_cm, pre_ls, pre_cf below); a leaf with
+                                 // nb >= 2 particles is followed by nb single-particle
+                                 // records, one per particle
   int64_t n_pre = 0;
   int n_front = 0;
   float box_lo[3], box_hi[3];    // root box (tight bounding box of X)
@@ -143,6 +143,20 @@ struct fga_tree {
 };
 
 namespace fga {
+
+// The depth-first records of a tree, one entry per record in each of three
+// arrays (in this order in fga_tree::node_pre): CoM and mass; l^2 and the
+// record count of the subtree (int bits: the walk's skip); the child count as
+// in node_info and the first body of a leaf. The walks read the first two
+// only: separate arrays put 8 and 16 records in a 128-byte line, so a walk's
+// consecutive records share lines more often than 32-byte records would.
+inline const float4* pre_cm(const fga_tree* t) { return t->node_pre; }
+inline const float2* pre_ls(const fga_tree* t) {
+  return reinterpret_cast<const float2*>(t->node_pre + t->n_pre);
+}
+inline const int2* pre_cf(const fga_tree* t) {
+  return reinterpret_cast<const int2*>(pre_ls(t) + t->n_pre);
+}
 
 // ------------------------------------------------------------------ prep kernels (fga_prep.cu)
 int check_finite(const float* p, int64_t n, int* d_flag, cudaStream_t s);

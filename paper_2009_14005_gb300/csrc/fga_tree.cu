@@ -279,30 +279,35 @@ static int build_frontier(fga_tree* T, int target, const int* d_pos, const int* 
   return FGA_OK;
 }
 
-// The depth-first records: cell v at pre[2 * pos[v]] with (l^2, subtree size,
-// count, first body). A single-particle leaf gets l^2 = -1 (always accepted:
-// its one exact term). A leaf holding nb >= 2 particles keeps its l^2 (its
-// monopole when accepted) and is followed by nb single-particle records, one
-// per particle in order, which the walk enters when the leaf is rejected: the
-// same exact terms as the leaf's particle loop of Algorithm 2.
+// The depth-first records: cell v is record pos[v], with CoM and mass in
+// pcm, (l^2, subtree size) in pls and (count, first body) in pcf. A
+// single-particle leaf gets l^2 = -1 (always accepted: its one exact term). A
+// leaf holding nb >= 2 particles keeps its l^2 (its monopole when accepted)
+// and is followed by nb single-particle records, one per particle in order,
+// which the walk enters when the leaf is rejected: the same exact terms as
+// the leaf's particle loop of Algorithm 2.
 __global__ void k_interleave_pre(const float4* __restrict__ cm, const int4* __restrict__ info,
                                  const int* __restrict__ size, const int* __restrict__ pos,
-                                 const float4* __restrict__ bodies, int64_t n, float4* __restrict__ pre) {
-  const float4 single = make_float4(-1.0f, __int_as_float(1), __int_as_float(-1), __int_as_float(0));
+                                 const float4* __restrict__ bodies, int64_t n, float4* __restrict__ pcm,
+                                 float2* __restrict__ pls, int2* __restrict__ pcf) {
+  const float2 single_ls = make_float2(-1.0f, __int_as_float(1));
+  const int2 single_cf = make_int2(-1, 0);
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int4 in = info[i];
     const int64_t p = pos[i];
-    pre[2 * p] = cm[i];
+    pcm[p] = cm[i];
     if (in.z == -1) {
-      pre[2 * p + 1] = single;
+      pls[p] = single_ls;
+      pcf[p] = single_cf;
       continue;
     }
-    pre[2 * p + 1] = make_float4(__int_as_float(in.x), __int_as_float(size[i]), __int_as_float(in.z),
-                                 __int_as_float(in.z < 0 ? in.y : 0));
+    pls[p] = make_float2(__int_as_float(in.x), __int_as_float(size[i]));
+    pcf[p] = make_int2(in.z, in.z < 0 ? in.y : 0);
     for (int b = 0; b < -in.z; ++b) {
-      pre[2 * (p + 1 + b)] = bodies[in.y + b];
-      pre[2 * (p + 1 + b) + 1] = single;
+      pcm[p + 1 + b] = bodies[in.y + b];
+      pls[p + 1 + b] = single_ls;
+      pcf[p + 1 + b] = single_cf;
     }
   }
 }
@@ -432,7 +437,8 @@ int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out
   if ((rc = build_frontier(T, front_target, node_pos, node_size, s))) return fail2(rc);
   if (dev_alloc_n(&T->node_pre, (size_t)2 * T->n_pre, s)) return fail2(FGA_ENOMEM);
   k_interleave_pre<<<grid, TB, 0, s>>>(T->node_cm, T->node_info, node_size, node_pos, T->bodies, T->n_nodes,
-                                       T->node_pre);
+                                       T->node_pre, const_cast<float2*>(pre_ls(T)),
+                                       const_cast<int2*>(pre_cf(T)));
   FGA_LAUNCH_CHECK("interleave_pre");
   dev_free(node_size, s);
   dev_free(node_pos, s);
@@ -475,7 +481,14 @@ extern "C" int64_t fga_tree_preorder(const fga_tree* t, int64_t cap, float* out,
     return FGA_EINVAL;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  FGA_CUDA_TRY(cudaMemcpyAsync(out, t->node_pre, sizeof(float4) * 2 * t->n_pre, cudaMemcpyDeviceToHost, s));
+  // the three record arrays, interleaved into 32-byte host records
+  const size_t rec = 8 * sizeof(float);
+  FGA_CUDA_TRY(cudaMemcpy2DAsync(out, rec, pre_cm(t), sizeof(float4), sizeof(float4), (size_t)t->n_pre,
+                                 cudaMemcpyDeviceToHost, s));
+  FGA_CUDA_TRY(cudaMemcpy2DAsync(out + 4, rec, pre_ls(t), sizeof(float2), sizeof(float2), (size_t)t->n_pre,
+                                 cudaMemcpyDeviceToHost, s));
+  FGA_CUDA_TRY(cudaMemcpy2DAsync(out + 6, rec, pre_cf(t), sizeof(int2), sizeof(int2), (size_t)t->n_pre,
+                                 cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaStreamSynchronize(s));
   return t->n_pre;
 }
