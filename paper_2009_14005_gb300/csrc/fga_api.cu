@@ -457,9 +457,9 @@ int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N,
   int rc = sc.alloc(&Y0, M) | sc.alloc(&ds, 1);
   if (rc) return FGA_ENOMEM;
   if (tree) {
-    if (sc.alloc(&perm, M)) return FGA_ENOMEM;
+    if (sc.alloc(&perm, M) || sc.alloc(&fb.acc, (size_t)3 * M)) return FGA_ENOMEM;
+    FGA_CUDA_TRY(cudaMemsetAsync(fb.acc, 0, sizeof(long long) * 3 * M, s));
     rc = pack_template(Y, mY, 1.0f, M, true, Y0, perm, s);
-    fb.S = bh_chunks(M, tree->n_front, bh_walk_kind(M, p->bh_walk));
   } else {
     if (sc.alloc(&X4, N)) return FGA_ENOMEM;
     rc = pack_template(Y, mY, 1.0f, M, false, Y0, nullptr, s);
@@ -471,7 +471,7 @@ int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N,
     fb.S = plan.S;
   }
   if (rc) return rc;
-  if (sc.alloc(&fb.hi, (size_t)fb.S * M) || sc.alloc(&fb.lo, (size_t)fb.S * M)) return FGA_ENOMEM;
+  if (!tree && (sc.alloc(&fb.hi, (size_t)fb.S * M) || sc.alloc(&fb.lo, (size_t)fb.S * M))) return FGA_ENOMEM;
   if ((rc = launch_state_init(ds, nullptr, s))) return rc;
   if (tree)
     rc = launch_bh(tree, Y0, M, ds, p->eps, p->theta, fb, s, bh_walk_kind(M, p->bh_walk));
@@ -513,8 +513,8 @@ int fga_forces_terms(const fga_tree* tree, const float* Y, const float* mY, int6
     return FGA_ENOMEM;
   int rc = pack_template(Y, mY, 1.0f, M, true, Y0, perm, s);
   if (rc) return rc;
-  fb.S = bh_chunks(M, tree->n_front, bh_walk_kind(M, p->bh_walk));
-  if (sc.alloc(&fb.hi, (size_t)fb.S * M) || sc.alloc(&fb.lo, (size_t)fb.S * M)) return FGA_ENOMEM;
+  if (sc.alloc(&fb.acc, (size_t)3 * M)) return FGA_ENOMEM;
+  FGA_CUDA_TRY(cudaMemsetAsync(fb.acc, 0, sizeof(long long) * 3 * M, s));
   FGA_CUDA_TRY(cudaMemsetAsync(terms, 0, sizeof(unsigned) * M, s));
   if ((rc = launch_state_init(ds, nullptr, s))) return rc;
   rc = launch_bh(tree, Y0, M, ds, p->eps, p->theta, fb, s, bh_walk_kind(M, p->bh_walk), nullptr, nullptr,
@@ -551,7 +551,6 @@ static int state_create_checked(const float* Xn, const float* mX, int64_t N, con
       if ((rc = tree_build(Xn, mX, N, p->max_depth, &st->own_tree, s))) return fail(rc);
       st->tree = st->own_tree;
     }
-    st->fb.S = bh_chunks(M, st->tree->n_front, bh_walk_kind(M, p->bh_walk));
   } else {
     if (dev_alloc_n(&st->X4, N, s)) return fail(FGA_ENOMEM);
     k_pack4<<<grid_for(N), 256, 0, s>>>(Xn, mX, (float)(1.0 / (double)N), N, st->X4);
@@ -570,16 +569,14 @@ static int state_create_checked(const float* Xn, const float* mX, int64_t N, con
     if (dev_alloc_n(&st->bh_cost, st->bh_ntasks, s) ||
         dev_alloc_n(&st->bh_order, (size_t)st->bh_ntasks + TASK_ORDER_SCRATCH, s))
       return fail(FGA_ENOMEM);
-    if (st->tree->n_front <= 64) {
-      // which partial-sum slots each 32-point group wrote (cleared by the epilogue)
-      const int64_t groups = (M + 31) / 32;
-      if (dev_alloc_n(&st->fb.mask, groups, s)) return fail(FGA_ENOMEM);
-      FGA_CUDA_TRY(cudaMemsetAsync(st->fb.mask, 0, sizeof(unsigned long long) * groups, s));
-    }
+    // the exact fixed-point force sums (zero; the epilogue leaves them zero)
+    if (dev_alloc_n(&st->fb.acc, (size_t)3 * M, s)) return fail(FGA_ENOMEM);
+    FGA_CUDA_TRY(cudaMemsetAsync(st->fb.acc, 0, sizeof(long long) * 3 * M, s));
+  } else if (dev_alloc_n(&st->fb.hi, (size_t)st->fb.S * M, s) ||
+             dev_alloc_n(&st->fb.lo, (size_t)st->fb.S * M, s)) {
+    return fail(FGA_ENOMEM);
   }
   if ((rc = pack_template(Yn, mY, p->dt, M, bh, st->Y0, st->perm, s))) return fail(rc);
-  if (dev_alloc_n(&st->fb.hi, (size_t)st->fb.S * M, s) || dev_alloc_n(&st->fb.lo, (size_t)st->fb.S * M, s))
-    return fail(FGA_ENOMEM);
   if (dev_alloc_n(&st->partials, (size_t)epilogue_blocks(M) * NRED, s)) return fail(FGA_ENOMEM);
   st->max_traj = std::max(p->max_iter, 1);
   if (dev_alloc_n(&st->traj, (size_t)12 * st->max_traj, s)) return fail(FGA_ENOMEM);
@@ -855,7 +852,7 @@ void fga_state_destroy(fga_state* st) {
   dev_free(st->traj, s);
   dev_free(st->bh_cost, s);
   dev_free(st->bh_order, s);
-  dev_free(st->fb.mask, s);
+  dev_free(st->fb.acc, s);
   if (st->own_tree) fga_tree_destroy(st->own_tree);
   for (cudaEvent_t e : st->events) cudaEventDestroy(e);
   if (prev != st->device) cudaSetDevice(prev);

@@ -113,6 +113,10 @@ __device__ __forceinline__ void comp_add(float& hi, float& lo, float x) {
   lo += e;
 }
 
+// x * scale rounded to the nearest integer: a value on the grid of the
+// Barnes-Hut fixed-point sums (scale = 2^F, so the product is exact).
+__device__ __forceinline__ long long fixed_point(float x, float scale) { return __float2ll_rn(x * scale); }
+
 struct Xf {
   float R[9], t[3];
 };

@@ -404,10 +404,16 @@ __device__ __forceinline__ EpiCtx load_epi(const DevState* __restrict__ ds) {
   return c;
 }
 
-// Template point i: a = G * (compensated sum of the S force partials);
-// Eq. 9 with the dissipative force of Eq. 7, v' = v + dt (a - eta v / m_Y);
-// Eq. 10, d = dt v'. Adds the point's 27 reduction terms to r: centred
-// position yc, d, yc yc^T (6), d yc^T (9), force m_Y a, torque yc x m_Y a.
+// Eq. 9 with the dissipative force of Eq. 7, v' = v + dt (a - eta v / m_Y),
+// and Eq. 10, d = dt v', for template point i with acceleration a = G * sum
+// (sx, sy, sz). Adds the point's 27 reduction terms to r: centred position
+// yc, d, yc yc^T (6), d yc^T (9), force m_Y a, torque yc x m_Y a.
+__device__ __forceinline__ void epi_ode(int64_t i, float4 y0, float sx, float sy, float sz,
+                                        float4* __restrict__ V, const EpiParams& ep, const EpiCtx& c,
+                                        float (&r)[NRED]);
+
+// Template point i with the force given as the compensated sum of S partial
+// sums (the all-pairs source splits, or the batch kernels' frontier cells).
 // `live`: bit s set for the slots to add (all S slots when no mask is kept);
 // the others are exact zeros, and adding a zero never changes a compensated
 // sum, so the result is the same as adding all S slots in order.
@@ -417,8 +423,6 @@ __device__ __forceinline__ void epi_point(int64_t i, const float4* __restrict__ 
                                           const EpiParams& ep, const EpiCtx& c, float (&r)[NRED],
                                           unsigned long long live = ~0ull) {
   const float4 y0 = Y0[i];
-  const float3 y = place(c.xf, y0);
-  const float cx = y.x - c.mu[0], cy = y.y - c.mu[1], cz = y.z - c.mu[2];
   float ahx = 0.f, ahy = 0.f, ahz = 0.f, alx = 0.f, aly = 0.f, alz = 0.f;
   if (S <= 64 && live != ~0ull) {
     unsigned long long rest = live & (S == 64 ? ~0ull : ((1ull << S) - 1ull));
@@ -472,7 +476,31 @@ __device__ __forceinline__ void epi_point(int64_t i, const float4* __restrict__ 
       }
     }
   }
-  const float ax = ep.G * (ahx + alx), ay = ep.G * (ahy + aly), az = ep.G * (ahz + alz);
+  epi_ode(i, y0, ahx + alx, ahy + aly, ahz + alz, V, ep, c, r);
+}
+
+// Template point i with the force given as exact fixed-point sums (three
+// planes of M, value = integer * unscale): read, rounded once to FP32, and
+// cleared for the next launch.
+__device__ __forceinline__ void epi_point_fixed(int64_t i, const float4* __restrict__ Y0,
+                                                long long* __restrict__ acc, float unscale, int64_t M,
+                                                float4* __restrict__ V, const EpiParams& ep,
+                                                const EpiCtx& c, float (&r)[NRED]) {
+  const float4 y0 = Y0[i];
+  const long long ix = acc[i], iy = acc[M + i], iz = acc[2 * M + i];
+  acc[i] = 0;
+  acc[M + i] = 0;
+  acc[2 * M + i] = 0;
+  epi_ode(i, y0, __ll2float_rn(ix) * unscale, __ll2float_rn(iy) * unscale, __ll2float_rn(iz) * unscale, V,
+          ep, c, r);
+}
+
+__device__ __forceinline__ void epi_ode(int64_t i, float4 y0, float sx, float sy, float sz,
+                                        float4* __restrict__ V, const EpiParams& ep, const EpiCtx& c,
+                                        float (&r)[NRED]) {
+  const float3 y = place(c.xf, y0);
+  const float cx = y.x - c.mu[0], cy = y.y - c.mu[1], cz = y.z - c.mu[2];
+  const float ax = ep.G * sx, ay = ep.G * sy, az = ep.G * sz;
   float vx, vy, vz;
   if (ep.vmode == FGA_VEL_RIGID) {
     vx = fmaf(c.A[0], y.x, fmaf(c.A[1], y.y, fmaf(c.A[2], y.z, c.b[0])));

@@ -234,11 +234,10 @@ __global__ void __launch_bounds__(BH_WARPS * 32, bh_min_blocks(KIND)) k_bh(const
                                                          const FrontCell* __restrict__ front, int K,
                                                          int C,
                                                          DevState* __restrict__ ds, float eps2,
-                                                         float theta2, float4* __restrict__ hi_out,
-                                                         float4* __restrict__ lo_out,
+                                                         float theta2, long long* __restrict__ acc,
+                                                         float acc_scale,
                                                          const unsigned* __restrict__ order,
                                                          unsigned* __restrict__ cost,
-                                                         unsigned long long* __restrict__ mask,
                                                          unsigned* __restrict__ terms) {
   constexpr int PL = (KIND == 0 || KIND == 4) ? 1 : (KIND == 5 ? 4 : 2);  // template points per lane
   if (ds->done) return;
@@ -297,15 +296,17 @@ __global__ void __launch_bounds__(BH_WARPS * 32, bh_min_blocks(KIND)) k_bh(const
     if (cost && lane == 0 && (!FGA_BH_BLOCK_TASKS || threadIdx.x == 0)) cost[task] = steps + 1u;
 #pragma unroll
     for (int q = 0; q < PL; ++q) {
-      // a 32-point slice in which no point added a term leaves exact zeros:
-      // with a mask its slot is neither written here nor read by the epilogue
-      const bool any = !mask || __any_sync(FULL, valid[q] && cnt[q] > 0u);
-      if (any && valid[q]) {
-        hi_out[(int64_t)c * M + i[q]] = make_float4(h[q][0], h[q][1], h[q][2], 0.f);
-        lo_out[(int64_t)c * M + i[q]] = make_float4(lo[q][0], lo[q][1], lo[q][2], 0.f);
+      // the task's compensated sums join the point's exact fixed-point sums
+      // (a point that added no term adds nothing)
+      if (valid[q] && cnt[q]) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const long long v = fixed_point(h[q][k], acc_scale) + fixed_point(lo[q][k], acc_scale);
+          atomicAdd(reinterpret_cast<unsigned long long*>(&acc[(int64_t)k * M + i[q]]),
+                    (unsigned long long)v);
+        }
+        if (terms) atomicAdd(&terms[i[q]], cnt[q]);
       }
-      if (mask && any && lane == 0) atomicOr(&mask[(size_t)PL * g + q], 1ull << c);
-      if (terms && valid[q] && cnt[q]) atomicAdd(&terms[i[q]], cnt[q]);
       total += valid[q] ? cnt[q] : 0u;
     }
   }
@@ -363,13 +364,18 @@ int bh_chunks(int64_t M, int K, int kind) {
 int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, float eps,
               float theta, ForceBuffers& fb, cudaStream_t s, int kind, const unsigned* order, unsigned* cost,
               unsigned* terms) {
-  unsigned long long* mask = t->n_front <= 64 ? fb.mask : nullptr;
+  if (!fb.acc) {
+    set_error("launch_bh: no fixed-point sums");
+    return FGA_EINTERNAL;
+  }
   const int C = bh_chunks(M, t->n_front, kind);
+  fb.acc_exp = fixed_point_exponent(t->mass_total, eps);
+  const float scale = ldexpf(1.0f, fb.acc_exp);
 #define FGA_BH_CASE(KD)                                                                           \
   k_bh<KD><<<bh_grid<KD>(M, C), BH_WARPS * 32, 0, s>>>(pre_cm(t), pre_ls(t), pre_cf(t), Y0, M,      \
                                                        t->front, t->n_front, C,                     \
-                                                       ds, eps * eps, theta * theta, fb.hi, fb.lo,  \
-                                                       order, cost, mask, terms)
+                                                       ds, eps * eps, theta * theta, fb.acc, scale, \
+                                                       order, cost, terms)
   if (kind == 2)
     FGA_BH_CASE(2);
   else if (kind == 3)
@@ -382,8 +388,15 @@ int launch_bh(const fga_tree* t, const float4* Y0, int64_t M, DevState* ds, floa
     FGA_BH_CASE(0);
 #undef FGA_BH_CASE
   FGA_LAUNCH_CHECK("bh");
-  fb.S = C;
   return FGA_OK;
+}
+
+int fixed_point_exponent(double mass_total, float eps) {
+  const double bound = mass_total / (2.598 * (double)eps * (double)eps);
+  if (!(bound > 0.0) || !std::isfinite(bound)) return 100;
+  int e = 0;
+  std::frexp(bound, &e);  // bound < 2^e
+  return std::max(-100, std::min(100, 61 - e));
 }
 
 // ------------------------------------------------------------------ heavy-first task order
@@ -494,7 +507,7 @@ __global__ void __launch_bounds__(EPI_BS) k_epilogue(const float4* __restrict__ 
                                                      unsigned* __restrict__ counter,
                                                      double* __restrict__ traj, EpiParams ep,
                                                      unsigned long long inter_add,
-                                                     unsigned long long* __restrict__ mask) {
+                                                     long long* __restrict__ acc, float acc_unscale) {
   if (ds->done) return;
   __shared__ bool s_last;
   __shared__ double s_red[NRED];
@@ -502,16 +515,11 @@ __global__ void __launch_bounds__(EPI_BS) k_epilogue(const float4* __restrict__ 
   float r[NRED];
 #pragma unroll
   for (int k = 0; k < NRED; ++k) r[k] = 0.f;
-  // one warp per 32-point group (so that it can clear the group's mask word
-  // once every lane has read it)
-  const int lane = threadIdx.x & 31;
-  for (int64_t base = blockIdx.x * (int64_t)EPI_BS + (threadIdx.x & ~31); base < M;
-       base += (int64_t)gridDim.x * EPI_BS) {
-    const int64_t i = base + lane;
-    const unsigned long long live = mask ? mask[base >> 5] : ~0ull;
-    if (i < M) epi_point(i, Y0, hi, lo, S, M, V, ep, c, r, live);
-    __syncwarp();
-    if (mask && lane == 0) mask[base >> 5] = 0ull;
+  for (int64_t i = blockIdx.x * (int64_t)EPI_BS + threadIdx.x; i < M; i += (int64_t)gridDim.x * EPI_BS) {
+    if (acc)
+      epi_point_fixed(i, Y0, acc, acc_unscale, M, V, ep, c, r);
+    else
+      epi_point(i, Y0, hi, lo, S, M, V, ep, c, r);
   }
   epi_block_partial(r, partials + (int64_t)blockIdx.x * NRED);
   __threadfence();
@@ -532,42 +540,58 @@ int launch_epilogue(const float4* Y0, int64_t M, const ForceBuffers& fb, float4*
                     double* d_partials, unsigned* d_counter, double* d_traj, const EpiParams& ep,
                     cudaStream_t s, unsigned long long inter_add) {
   k_epilogue<<<epilogue_blocks(M), EPI_BS, 0, s>>>(Y0, M, fb.hi, fb.lo, fb.S, V, ds, d_partials,
-                                                   d_counter, d_traj, ep, inter_add,
-                                                   fb.S <= 64 ? fb.mask : nullptr);
+                                                   d_counter, d_traj, ep, inter_add, fb.acc,
+                                                   ldexpf(1.0f, -fb.acc_exp));
   FGA_LAUNCH_CHECK("epilogue");
   return FGA_OK;
 }
 
 // ------------------------------------------------------------------ helpers for fga_forces
 
+// The force on each template point, G (m_Y) times its sum: the compensated
+// sum of the S partial sums, or (acc != null) the exact fixed-point sums,
+// which are cleared.
 __global__ void k_forces_out(const float4* __restrict__ hi, const float4* __restrict__ lo, int S,
+                             long long* __restrict__ acc, float acc_unscale,
                              int64_t M, const float4* __restrict__ Y0, int use_mass, float G,
                              const int* __restrict__ perm, float* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M;
        i += (int64_t)gridDim.x * blockDim.x) {
-    float ahx = 0.f, ahy = 0.f, ahz = 0.f, alx = 0.f, aly = 0.f, alz = 0.f;
-    for (int s = 0; s < S; ++s) {
-      const float4 h = hi[(int64_t)s * M + i];
-      const float4 l = lo[(int64_t)s * M + i];
-      comp_add(ahx, alx, h.x);
-      comp_add(ahy, aly, h.y);
-      comp_add(ahz, alz, h.z);
-      alx += l.x;
-      aly += l.y;
-      alz += l.z;
+    float sx, sy, sz;
+    if (acc) {
+      sx = __ll2float_rn(acc[i]) * acc_unscale;
+      sy = __ll2float_rn(acc[M + i]) * acc_unscale;
+      sz = __ll2float_rn(acc[2 * M + i]) * acc_unscale;
+      acc[i] = acc[M + i] = acc[2 * M + i] = 0;
+    } else {
+      float ahx = 0.f, ahy = 0.f, ahz = 0.f, alx = 0.f, aly = 0.f, alz = 0.f;
+      for (int s = 0; s < S; ++s) {
+        const float4 h = hi[(int64_t)s * M + i];
+        const float4 l = lo[(int64_t)s * M + i];
+        comp_add(ahx, alx, h.x);
+        comp_add(ahy, aly, h.y);
+        comp_add(ahz, alz, h.z);
+        alx += l.x;
+        aly += l.y;
+        alz += l.z;
+      }
+      sx = ahx + alx;
+      sy = ahy + aly;
+      sz = ahz + alz;
     }
     const float f = use_mass ? G * Y0[i].w : G;
     const int64_t j = perm ? (int64_t)perm[i] : i;
-    out[3 * j] = f * (ahx + alx);
-    out[3 * j + 1] = f * (ahy + aly);
-    out[3 * j + 2] = f * (ahz + alz);
+    out[3 * j] = f * sx;
+    out[3 * j + 1] = f * sy;
+    out[3 * j + 2] = f * sz;
   }
 }
 
 int launch_forces_out(const ForceBuffers& fb, int64_t M, const float4* Y0, int use_mass, float G,
                       const int* perm, float* acc_out, cudaStream_t s) {
   const int64_t g = std::max<int64_t>(1, std::min<int64_t>((M + 255) / 256, 8 * (int64_t)sm_count()));
-  k_forces_out<<<(unsigned)g, 256, 0, s>>>(fb.hi, fb.lo, fb.S, M, Y0, use_mass, G, perm, acc_out);
+  k_forces_out<<<(unsigned)g, 256, 0, s>>>(fb.hi, fb.lo, fb.S, fb.acc, ldexpf(1.0f, -fb.acc_exp), M, Y0,
+                                           use_mass, G, perm, acc_out);
   FGA_LAUNCH_CHECK("forces_out");
   return FGA_OK;
 }

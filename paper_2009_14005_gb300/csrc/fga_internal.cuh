@@ -139,6 +139,7 @@ struct fga_tree {
   int64_t n_pre = 0;
   int n_front = 0;
   float box_lo[3], box_hi[3];    // root box (tight bounding box of X)
+  double mass_total = 0.0;       // the root cell's mass (sum of the masses of X)
   cudaStream_t stream = nullptr; // stream the buffers were allocated on
 };
 
@@ -192,14 +193,29 @@ int tree_build(const float* X, const float* mX, int64_t N, int max_depth, fga_tr
 
 // ------------------------------------------------------------------ forces (fga_force.cu)
 struct ForceBuffers {
-  float4* hi = nullptr;   // S x M compensated partial sums (value)
+  // All-pairs: S x M compensated partial sums, one slot per source split.
+  float4* hi = nullptr;   // S x M (value)
   float4* lo = nullptr;   // S x M (compensation)
   int S = 1;              // number of source splits
-  // Optional (Barnes-Hut, S <= 64): bit s of mask[g] is set when slot s of
-  // the 32-point group g was written in this launch; unset slots are exact
-  // zeros, neither written nor read. The epilogue clears the mask.
-  unsigned long long* mask = nullptr;
+  // Barnes-Hut: one exact fixed-point sum per point and axis, three planes of
+  // M int64 (x, y, z). Every task adds its compensated FP32 sums (value and
+  // compensation, each rounded to a multiple of 2^-acc_exp) with integer
+  // atomics, so the result does not depend on the order of the tasks; the
+  // reader (epilogue or force output) takes the value and leaves zeros for
+  // the next launch. acc_exp (fixed_point_exponent) leaves every possible sum
+  // of a point's terms below 2^61 units.
+  long long* acc = nullptr;
+  int acc_exp = 0;
 };
+
+// The binary exponent F of the Barnes-Hut fixed-point sums (value = integer
+// * 2^-F). Each of a point's BHForce terms is m (s - y) / (|s - y|^2 +
+// eps^2)^(3/2) for a particle or cell of mass m, whose size is at most
+// m / (2.598 eps^2) (the maximum over r of r / (r^2 + eps^2)^(3/2), at r =
+// eps / sqrt 2), and the terms of one point cover the reference's total mass
+// once, so any partial sum is below mass_total / (2.598 eps^2) <= 2^e; F =
+// 61 - e keeps it below 2^61. Clamped to [-100, 100].
+int fixed_point_exponent(double mass_total, float eps);
 
 // Plan for the all-pairs kernel: block size, queries per thread, source split.
 struct DirectPlan {

@@ -225,7 +225,10 @@ static int build_frontier(fga_tree* T, int target, const int* d_pos, const int* 
   FGA_CUDA_TRY(cudaMemcpyAsync(nb.data(), T->node_bodies, sizeof(int2) * P, cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaMemcpyAsync(pos.data(), d_pos, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaMemcpyAsync(size.data(), d_size, sizeof(int) * P, cudaMemcpyDeviceToHost, s));
+  float4 root;
+  FGA_CUDA_TRY(cudaMemcpyAsync(&root, T->node_cm, sizeof(float4), cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaStreamSynchronize(s));
+  T->mass_total = (double)root.w;
   struct Item {
     int node;
     std::vector<int> path;
