@@ -514,12 +514,14 @@ __device__ __forceinline__ void bh_walk_cursor(const float4* __restrict__ pcm,
       pz2[r] = f2_pack(p[2 * r][2], p[2 * r + 1][2]);
     }
     const f2 th2 = f2_pack(theta2, theta2), e2 = f2_pack(eps2, eps2);
-    while (v < end) {
+    // one record of the union walk: every point at record v judges it
+    auto step = [&]() {
       const float4 cm = pcm[v];
       const float2 ri = pls[v];
       const int skip = __float_as_int(ri.y);
       const f2 cx = f2_pack(cm.x, cm.x), cy = f2_pack(cm.y, cm.y), cz = f2_pack(cm.z, cm.z);
       const f2 cw = f2_pack(cm.w, cm.w);
+      const int v_acc = v + skip, v_rej = v + 1;
       int lo = end;
 #pragma unroll
       for (int r = 0; r < NR; ++r) {
@@ -540,21 +542,36 @@ __device__ __forceinline__ void bh_walk_cursor(const float4* __restrict__ pcm,
         pz2[r] = f2_fma(wsel, dz, pz2[r]);
         cnt[2 * r] += acc0;
         cnt[2 * r + 1] += acc1;
-        nx[2 * r] = act0 ? v + (acc0 ? skip : 1) : nx[2 * r];
-        nx[2 * r + 1] = act1 ? v + (acc1 ? skip : 1) : nx[2 * r + 1];
+        nx[2 * r] = act0 ? (acc0 ? v_acc : v_rej) : nx[2 * r];
+        nx[2 * r + 1] = act1 ? (acc1 ? v_acc : v_rej) : nx[2 * r + 1];
         lo = min(lo, min(nx[2 * r], nx[2 * r + 1]));
       }
 #if FGA_BH_CURSOR_VOTE
       {
         bool rej = false;
 #pragma unroll
-        for (int q = 0; q < NP; ++q) rej = rej || nx[q] == v + 1;
-        v = __any_sync(FULL, rej) ? v + 1 : v + skip;
+        for (int q = 0; q < NP; ++q) rej = rej || nx[q] == v_rej;
+        v = __any_sync(FULL, rej) ? v_rej : v_acc;
       }
 #else
       v = (int)__reduce_min_sync(FULL, (unsigned)lo);
 #endif
-      if ((++k & 31u) == 0u) {
+    };
+    // four records per pass (v is the same in every lane, so the exits are
+    // uniform), the FP32 sums flushed every 32 records
+    while (v < end) {
+      step();
+      ++k;
+      if (v >= end) break;
+      step();
+      ++k;
+      if (v >= end) break;
+      step();
+      ++k;
+      if (v >= end) break;
+      step();
+      ++k;
+      if ((k & 31u) == 0u) {
 #pragma unroll
         for (int r = 0; r < NR; ++r) {
           f2_unpack(px2[r], p[2 * r][0], p[2 * r + 1][0]);
