@@ -45,7 +45,7 @@ __device__ __forceinline__ int owner_of(const unsigned* __restrict__ start, int 
 }
 
 #ifndef FGA_BATCH_MINBLOCKS
-#define FGA_BATCH_MINBLOCKS 8  // resident blocks per SM the register budget is sized for
+#define FGA_BATCH_MINBLOCKS 9  // resident blocks per SM the register budget is sized for (36 warps)
 #endif
 __global__ void __launch_bounds__(BATCH_WARPS * 32, FGA_BATCH_MINBLOCKS) k_batch_force(const PairDev* __restrict__ pairs,
                                                                      int npairs,

@@ -215,14 +215,17 @@ int launch_direct(const float4* X, int64_t N, const float4* Y0, int64_t M, const
 static constexpr int BH_WARPS = FGA_BH_WARPS;
 
 #ifndef FGA_BH_MINBLOCKS
-#define FGA_BH_MINBLOCKS 8  // resident blocks per SM the register budget is sized for
+#define FGA_BH_MINBLOCKS 9  // resident blocks per SM the register budget is sized for
 #endif
 // KIND (bh_walk_kind): 0 = one template point per lane, each lane walking its
 // own point over the depth-first records (bh_task_pre); 2 = two points per
 // lane, one walk for the warp with saved sibling ranges (bh_walk); 3 / 4 =
 // two / one points per lane, one walk for the warp that follows every
 // point's own walk (bh_walk_cursor).
-// Resident blocks per SM the register budget of each walk is sized for: the
+// Resident blocks per SM the register budget of each walk is sized for: 36
+// warps per SM at 56 registers (the union walk on planar 1M: 4.88 ms per
+// launch, against 5.39 ms with 32 warps at 64 registers and 5.45 ms with 40
+// warps at 48; the per-lane walk on LiDAR 120k: 0.658 against 0.667 ms); the
 // walk with four points per lane holds twice the per-point registers.
 constexpr int bh_min_blocks(int kind) { return kind == 5 ? FGA_BH_MINBLOCKS / 2 : FGA_BH_MINBLOCKS; }
 
