@@ -276,8 +276,9 @@ __host__ __device__ inline unsigned bh_tasks(int64_t M, int C, int pl) {
 }
 // The K frontier cells are cut into C chunks of consecutive cells (chunk c:
 // cells [c K / C, (c + 1) K / C)); a task walks one chunk for its group, so
-// each template point leaves C partial sums for the epilogue instead of K. C
-// is the fewest chunks that still give every resident warp about
+// its fixed costs (the ancestor path, the conversion and atomic addition of
+// its sums) are paid C times per group instead of K. C is the fewest chunks
+// that still give every resident warp about
 // FGA_BH_TASKS_PER_WARP tasks (0: C = K, one frontier cell per task).
 #ifndef FGA_BH_TASKS_PER_WARP
 #define FGA_BH_TASKS_PER_WARP 32

@@ -234,6 +234,30 @@ def test_bh_walks_take_the_same_terms(fga, orc, m):
         np.testing.assert_array_equal(out[walk + "_terms"], out["lane_terms"], err_msg=walk)
 
 
+@pytest.mark.parametrize("walk", ["lane", "cursor"])
+def test_bh_fixed_point_sums_scale_exactly_with_the_masses(fga, orc, walk):
+    # Barnes-Hut forces are summed as integers on a grid of 2^-F with F set
+    # from the reference's total mass and eps. Scaling every mass by a power
+    # of two scales each FP32 term exactly and moves F by the same power, so
+    # the forces scale exactly too; a grid that overflowed, or one fixed
+    # without regard to the masses, would not. The unscaled forces still
+    # match the oracle's BHForce.
+    X, Y, _, _ = synth.planar_scene_pair(3, n=40000, m=6000)
+    Xn, Yn, _ = _norm_pair(orc, X, Y)
+    mX = _f32(orc.masses_niv(Xn))
+    p = fga.params(theta=0.5, eps=0.2, bh_walk=WALKS[walk])
+    out = {}
+    for k in (0, 40, -40):
+        t = fga.fga_tree_build(_cuda(Xn), _cuda(np.ldexp(mX, k)), p)
+        out[k] = fga.fga_forces(t, None, None, _cuda(Yn), None, p).cpu().numpy()
+    assert np.all(np.isfinite(out[0])) and np.abs(out[0]).max() > 0
+    for k in (40, -40):
+        np.testing.assert_array_equal(out[k], np.ldexp(out[0], k), err_msg=str(k))
+    a_bo, _ = orc.Tree(Xn, mX).bh_acc(Yn, p.G, 0.2, 0.5)
+    err = np.linalg.norm(out[0] - a_bo) / np.linalg.norm(a_bo)
+    assert err < 1e-4, err
+
+
 # --------------------------------------------------------------------------- Algorithm 2
 
 def _gt_errors(R, t, R_ref, t_ref, X):
