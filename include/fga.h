@@ -235,11 +235,15 @@ int64_t fga_tree_preorder(const fga_tree* t, int64_t cap, float* out, void* stre
  * summed over all X (tree == NULL: X, mX, N are used) or approximated by
  * BHForce on `tree` with opening parameter p->theta (Eq. 15; X, mX, N are then
  * ignored and may be NULL). mY NULL means m_Yi = 1, i.e. the output is the
- * acceleration. FP32 arithmetic with compensated per-point accumulation.
+ * acceleration. FP32 arithmetic with compensated per-point accumulation;
+ * with a tree, the walks' compensated sums are added exactly as 64-bit
+ * fixed-point integers on a grid set by the tree's total mass and eps.
  * Y: device (M x 3); acc_out: device (M x 3), same order as Y.
  * interactions_out (host, optional): number of force terms evaluated; when
  * given, the call synchronises `stream`.
- * Errors: FGA_EINVAL (sizes, eps <= 0, theta < 0), FGA_ENOMEM, FGA_ECUDA. */
+ * Errors: FGA_EINVAL (sizes, eps <= 0, theta < 0; with a tree, eps below
+ * 1e-5 of the diagonal of the tree's bounding box, where that grid would no
+ * longer resolve the far field to FP32 accuracy), FGA_ENOMEM, FGA_ECUDA. */
 int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N, const float* Y,
                const float* mY, int64_t M, const fga_params* p, float* acc_out,
                int64_t* interactions_out, void* stream);
@@ -250,7 +254,8 @@ int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N,
  * for comparing a point's walk with another implementation's. Y: device
  * (M x 3), mY: device (M) or NULL, acc_out: device (M x 3), terms_out: device
  * (M int32). Queues its work on `stream` without synchronising.
- * Errors: FGA_EINVAL (no tree, sizes, eps <= 0, theta < 0), FGA_ENOMEM, FGA_ECUDA. */
+ * Errors: FGA_EINVAL (no tree, sizes, eps <= 0, theta < 0, eps below 1e-5 of
+ * the diagonal of the tree's bounding box), FGA_ENOMEM, FGA_ECUDA. */
 int fga_forces_terms(const fga_tree* tree, const float* Y, const float* mY, int64_t M,
                      const fga_params* p, float* acc_out, int32_t* terms_out, void* stream);
 
@@ -297,7 +302,8 @@ typedef struct fga_state fga_state;
  * p->method == FGA_BH the tree is built from Xn/mX unless `tree` is given
  * (borrowed, must outlive the state). The state keeps the template sorted
  * along a Morton curve so that neighbouring threads follow similar tree paths.
- * Errors: FGA_EINVAL, FGA_ENOMEM, FGA_ECUDA. */
+ * Errors: FGA_EINVAL (including, for FGA_BH, eps below 1e-5 of the diagonal
+ * of the tree's bounding box, as in fga_forces), FGA_ENOMEM, FGA_ECUDA. */
 int fga_state_create(const float* Xn, const float* mX, int64_t N, const float* Yn,
                      const float* mY, int64_t M, const fga_tree* tree, const fga_params* p,
                      fga_state** out, void* stream);

@@ -88,6 +88,25 @@ int sm_count() {
   return n;
 }
 
+// Barnes-Hut forces are summed as 64-bit fixed-point integers whose grid is
+// set by the largest possible sum, mass_total / (2.598 eps^2). The smallest
+// force of a point is about mass_total / diag^2 (diag: the diagonal of the
+// tree's box), so the grid's rounding, at most 2^-54 mass_total / (2.598
+// eps^2) per point, stays below 2 % of the force tolerance (1e-5 of the sum of
+// the term magnitudes) while diag <= 1e5 eps. Smaller eps are rejected.
+static int check_bh_eps(const fga_tree* t, float eps) {
+  double d2 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    const double e = (double)t->box_hi[k] - (double)t->box_lo[k];
+    d2 += e * e;
+  }
+  if (std::sqrt(d2) > 1e5 * (double)eps) {
+    set_error("Barnes-Hut: eps must be at least 1e-5 of the reference's bounding-box diagonal");
+    return FGA_EINVAL;
+  }
+  return FGA_OK;
+}
+
 int check_params(const fga_params* p, bool need_tree) {
   if (!p) {
     set_error("null fga_params");
@@ -448,6 +467,7 @@ int fga_forces(const fga_tree* tree, const float* X, const float* mX, int64_t N,
     set_error("fga_forces: bad arguments");
     return FGA_EINVAL;
   }
+  if (tree && check_bh_eps(tree, p->eps)) return FGA_EINVAL;
   Scratch sc(s);
   float4 *Y0 = nullptr, *X4 = nullptr;
   int* perm = nullptr;
@@ -503,6 +523,7 @@ int fga_forces_terms(const fga_tree* tree, const float* Y, const float* mY, int6
     set_error("fga_forces_terms: bad arguments");
     return FGA_EINVAL;
   }
+  if (check_bh_eps(tree, p->eps)) return FGA_EINVAL;
   Scratch sc(s);
   float4* Y0 = nullptr;
   int* perm = nullptr;
@@ -551,6 +572,7 @@ static int state_create_checked(const float* Xn, const float* mX, int64_t N, con
       if ((rc = tree_build(Xn, mX, N, p->max_depth, &st->own_tree, s))) return fail(rc);
       st->tree = st->own_tree;
     }
+    if ((rc = check_bh_eps(st->tree, p->eps))) return fail(rc);
   } else {
     if (dev_alloc_n(&st->X4, N, s)) return fail(FGA_ENOMEM);
     k_pack4<<<grid_for(N), 256, 0, s>>>(Xn, mX, (float)(1.0 / (double)N), N, st->X4);

@@ -315,6 +315,26 @@ __global__ void k_interleave_pre(const float4* __restrict__ cm, const int4* __re
   }
 }
 
+// On every way out of tree_build: frees the build's scratch (stream-ordered)
+// and, unless the build succeeded, the tree itself.
+struct BuildGuard {
+  cudaStream_t s;
+  fga_tree* tree;
+  std::vector<void*> bufs;
+  void add(void* p) { bufs.push_back(p); }
+  void release(void* p) {
+    for (void*& b : bufs)
+      if (b == p) {
+        dev_free(b, s);
+        b = nullptr;
+      }
+  }
+  ~BuildGuard() {
+    for (void* b : bufs) dev_free(b, s);
+    if (tree) fga_tree_destroy(tree);
+  }
+};
+
 int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out, cudaStream_t s,
                int front_target) {
   if (N > ((int64_t)1 << 26)) {
@@ -326,6 +346,7 @@ int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out
   T->max_depth = D;
   T->stream = s;
   cudaGetDevice(&T->device);
+  BuildGuard guard{s, T, {}};
   const int64_t cap = 2 * N;
   int rc = 0;
   rc |= dev_alloc_n(&T->bodies, N, s);
@@ -358,23 +379,20 @@ int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out
   rc |= dev_alloc_n(&sum_p, cap, s);
   rc |= dev_alloc_n(&box, 6, s);
   rc |= dev_alloc_n(&lv, 1, s);
-  if (rc) {
-    fga_tree_destroy(T);
-    return FGA_ENOMEM;
-  }
+  for (void* b : {(void*)ktmp, (void*)ukey, (void*)idx, (void*)itmp, (void*)ustart, (void*)flags, (void*)uid,
+                  (void*)n_u, (void*)node_range, (void*)node_size, (void*)node_pos, (void*)sum_m, (void*)sum_p,
+                  (void*)box, (void*)lv})
+    guard.add(b);
+  if (rc) return FGA_ENOMEM;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((N + TB - 1) / TB, 8 * sm_count()));
-  auto fail = [&](int code) {
-    fga_tree_destroy(T);
-    return code;
-  };
-  if ((rc = bbox_xyz(X, N, box, box + 3, s))) return fail(rc);
-  if ((rc = morton_keys(X, N, box, box + 3, D, T->keys, idx, s))) return fail(rc);
-  if ((rc = radix_sort_pairs(T->keys, idx, ktmp, itmp, N, 3 * D, s))) return fail(rc);
+  if ((rc = bbox_xyz(X, N, box, box + 3, s))) return rc;
+  if ((rc = morton_keys(X, N, box, box + 3, D, T->keys, idx, s))) return rc;
+  if ((rc = radix_sort_pairs(T->keys, idx, ktmp, itmp, N, 3 * D, s))) return rc;
   k_gather_bodies<<<grid, TB, 0, s>>>(X, mX, N, idx, T->bodies, T->body_index);
   FGA_LAUNCH_CHECK("gather_bodies");
   k_head_flags<<<grid, TB, 0, s>>>(T->keys, N, flags);
   FGA_LAUNCH_CHECK("head_flags");
-  if ((rc = scan_exclusive(flags, uid, N, n_u, s))) return fail(rc);
+  if ((rc = scan_exclusive(flags, uid, N, n_u, s))) return rc;
   k_unique<<<grid, TB, 0, s>>>(T->keys, N, flags, uid, n_u, ukey, ustart);
   FGA_LAUNCH_CHECK("unique");
   k_tree_init<<<1, 1, 0, s>>>(n_u, lv, node_range, T->node_info);
@@ -411,40 +429,24 @@ int tree_build(const float* X, const float* mX, int64_t N, int D, fga_tree** out
   FGA_CUDA_TRY(cudaMemcpyAsync(&h_nu, n_u, sizeof(h_nu), cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaMemcpyAsync(&h_npre, node_size, sizeof(int), cudaMemcpyDeviceToHost, s));
   FGA_CUDA_TRY(cudaStreamSynchronize(s));
-  dev_free(ktmp, s);
-  dev_free(ukey, s);
-  dev_free(idx, s);
-  dev_free(itmp, s);
-  dev_free(ustart, s);
-  dev_free(flags, s);
-  dev_free(uid, s);
-  dev_free(n_u, s);
-  dev_free(node_range, s);
-  dev_free(sum_m, s);
-  dev_free(sum_p, s);
-  dev_free(box, s);
-  dev_free(lv, s);
-  auto fail2 = [&](int code) {
-    dev_free(node_size, s);
-    dev_free(node_pos, s);
-    fga_tree_destroy(T);
-    return code;
-  };
+  // the scratch the remaining steps do not read (node_size, node_pos: below)
+  for (void* b : {(void*)ktmp, (void*)ukey, (void*)idx, (void*)itmp, (void*)ustart, (void*)flags, (void*)uid,
+                  (void*)n_u, (void*)node_range, (void*)sum_m, (void*)sum_p, (void*)box, (void*)lv})
+    guard.release(b);
   if (h_lv.overflow) {
     set_error("tree_build: node capacity exceeded");
-    return fail2(FGA_EINTERNAL);
+    return FGA_EINTERNAL;
   }
   T->n_nodes = h_lv.start[D + 1];
   T->n_unique = (int)h_nu;
   T->n_pre = h_npre;  // the root's subtree: every record
-  if ((rc = build_frontier(T, front_target, node_pos, node_size, s))) return fail2(rc);
-  if (dev_alloc_n(&T->node_pre, (size_t)2 * T->n_pre, s)) return fail2(FGA_ENOMEM);
+  if ((rc = build_frontier(T, front_target, node_pos, node_size, s))) return rc;
+  if (dev_alloc_n(&T->node_pre, (size_t)2 * T->n_pre, s)) return FGA_ENOMEM;
   k_interleave_pre<<<grid, TB, 0, s>>>(T->node_cm, T->node_info, node_size, node_pos, T->bodies, T->n_nodes,
                                        T->node_pre, const_cast<float2*>(pre_ls(T)),
                                        const_cast<int2*>(pre_cf(T)));
   FGA_LAUNCH_CHECK("interleave_pre");
-  dev_free(node_size, s);
-  dev_free(node_pos, s);
+  guard.tree = nullptr;  // built: the caller owns it
   *out = T;
   return FGA_OK;
 }

@@ -369,6 +369,26 @@ def test_host_and_device_inputs_agree_and_runs_are_deterministic(fga):
 
 # --------------------------------------------------------------------------- edge cases
 
+def test_barnes_hut_rejects_eps_below_its_fixed_point_range(fga):
+    # the fixed-point force sums resolve forces down to the far field only
+    # while the reference's box diagonal is at most 1e5 eps
+    X = np.random.default_rng(1).uniform(-5, 5, size=(2000, 3)).astype(np.float32)
+    diag = float(np.linalg.norm(X.max(0) - X.min(0)))
+    t = fga.fga_tree_build(_cuda(X), None, fga.params())
+    for eps, ok in [(diag * 1.2e-5, True), (diag * 0.8e-5, False)]:
+        p = fga.params(eps=eps, theta=0.5)
+        if ok:
+            a = fga.fga_forces(t, None, None, _cuda(X[:100]), None, p).cpu().numpy()
+            assert np.all(np.isfinite(a))
+        else:
+            with pytest.raises(fga.FGAError) as e:
+                fga.fga_forces(t, None, None, _cuda(X[:100]), None, p)
+            assert e.value.code == fga.FGA_EINVAL
+            with pytest.raises(fga.FGAError) as e:
+                fga.fga_register(_cuda(X), _cuda(X[:100]), fga.params(method=fga.FGA_BH, eps=1e-5))
+            assert e.value.code == fga.FGA_EINVAL
+
+
 def test_invalid_inputs_are_rejected(fga):
     X = np.random.default_rng(0).normal(size=(10, 3)).astype(np.float32)
     Xbad = X.copy()
