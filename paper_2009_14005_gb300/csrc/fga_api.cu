@@ -337,6 +337,7 @@ struct fga_state {
   unsigned bh_ntasks = 0;
   int bh_launches = 0;
   bool bh_have_order = false;
+  bool small_loop = false;       // all-pairs: the loop runs as one cluster launch (fga_small.cu)
   std::vector<cudaEvent_t> events;  // with p.profile: start/stop per force launch
   int timed = 0;                    // recorded start/stop pairs
 };
@@ -579,6 +580,7 @@ static int state_create_checked(const float* Xn, const float* mX, int64_t N, con
     FGA_LAUNCH_CHECK("pack4 X");
     st->plan = plan_direct(N, M);
     st->fb.S = st->plan.S;
+    st->small_loop = small_loop_eligible(N, M, st->plan) && small_loop_available(st->plan);
   }
   if (dev_alloc_n(&st->Y0, M, s) || dev_alloc_n(&st->V, M, s) || dev_alloc_n(&st->ds, 1, s) ||
       dev_alloc_n(&st->counter, 1, s))
@@ -638,7 +640,28 @@ struct StepGraphCache {
 };
 static thread_local StepGraphCache t_step_graph;
 
+static EpiParams epi_params(const fga_state* st) {
+  const fga_params& p = st->p;
+  EpiParams ep{p.G, p.dt, p.eta, p.velocity_mode, (double)p.conv_tol, st->max_traj,
+               1.0 / (double)st->M, 1.0 / (double)p.dt};
+  ep.dim = p.dim;
+  return ep;
+}
+
+// A small all-pairs pair: all n_iter iterations in one cluster launch, the
+// same results as step_launches.
+static int step_small(fga_state* st, int n_iter, cudaStream_t s) {
+  const int traj_iters = std::max(0, st->max_traj - st->queued);
+  const int rc = launch_small_loop(st->X4, st->N, st->Y0, st->M, st->ds, st->p.eps, st->plan, st->fb, st->V,
+                                   st->partials, st->traj, traj_iters, epi_params(st),
+                                   (unsigned long long)(st->N * st->M), n_iter, s);
+  if (rc) return rc;
+  st->queued += n_iter;
+  return FGA_OK;
+}
+
 static int step_impl(fga_state* st, int n_iter, cudaStream_t s) {
+  if (st->small_loop && !st->p.profile && st->p.method != FGA_BH) return step_small(st, n_iter, s);
   if (st->p.profile || n_iter < FGA_STEP_GRAPH_MIN) return step_launches(st, n_iter, s);
   cudaStream_t cs = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -707,9 +730,7 @@ static int step_impl(fga_state* st, int n_iter, cudaStream_t s) {
 
 static int step_launches(fga_state* st, int n_iter, cudaStream_t s) {
   const fga_params& p = st->p;
-  EpiParams ep{p.G, p.dt, p.eta, p.velocity_mode, (double)p.conv_tol, st->max_traj,
-               1.0 / (double)st->M, 1.0 / (double)p.dt};
-  ep.dim = p.dim;
+  const EpiParams ep = epi_params(st);
   const unsigned long long inter = p.method == FGA_BH ? 0ull : (unsigned long long)(st->N * st->M);
   if (p.profile) {
     const size_t need = 2 * (size_t)(st->timed + n_iter);

@@ -249,33 +249,21 @@ struct FitShared {
 };
 
 // Called by every thread of the block that finishes an iteration (Eqs. 14,
-// 16 and Algorithm 2's composition and stop test). A dependent FP64
-// operation costs a few hundred cycles on this GPU and the fit is the
-// iteration's tail, so its work is spread over the block:
-//  1. the block copies the state into shared memory (8 bytes per thread, one
-//     round trip; one thread reading the fields in global memory would wait
-//     behind its own earlier stores to the same struct);
-//  2. thread 0 forms C from the reductions and takes R' (polar or eigen
+// 16 and Algorithm 2's composition and stop test), with the state in shared
+// memory. A dependent FP64 operation costs a few hundred cycles on this GPU
+// and the fit is the iteration's tail, so its work is spread over the block:
+//  1. thread 0 forms C from the reductions and takes R' (polar or eigen
 //     route) and t';
-//  3. threads 0-11 compose [R | t] entry by entry with the convergence terms,
+//  2. threads 0-11 compose [R | t] entry by entry with the convergence terms,
 //     threads 12-23 the rigid-velocity coefficients;
-//  4. thread 0 sums the convergence terms, updates the flags, the history and
-//     the FP32 copies;
-//  5. the block copies the state back.
-// red: the NRED reduced values (shared memory).
-static __device__ void rigid_step_block(const double* red, int64_t M, DevState* ds_g, const EpiParams& ep,
-                                        double* traj, unsigned long long inter_add) {
-  static_assert(sizeof(DevState) % sizeof(unsigned long long) == 0, "state copied in 8-byte words");
-  constexpr int NW = (int)(sizeof(DevState) / sizeof(unsigned long long));
-  static_assert(NW <= EPI_BS_MIN, "one word per thread");
-  __shared__ DevState s_state;
+//  3. thread 0 sums the convergence terms, updates the flags, the history and
+//     the FP32 copies.
+// red: the NRED reduced values (shared memory); ds: the state (shared
+// memory), updated in place and visible to the whole block on return.
+static __device__ void rigid_step_smem(const double* red, int64_t M, DevState* ds, const EpiParams& ep,
+                                       double* traj, unsigned long long inter_add) {
   __shared__ FitShared f;
-  DevState* ds = &s_state;
-  unsigned long long* sw = reinterpret_cast<unsigned long long*>(&s_state);
-  unsigned long long* gw = reinterpret_cast<unsigned long long*>(ds_g);
   const int tid = threadIdx.x;
-  if (tid < NW) sw[tid] = __ldcg(gw + tid);
-  __syncthreads();
   if (tid == 0) {
     const double Md = (double)M;
     double ybar[3], mud[3];
@@ -378,6 +366,25 @@ static __device__ void rigid_step_block(const double* red, int64_t M, DevState* 
     if (ep.max_iter > 0 && k_it + 1 >= ep.max_iter) ds->done = 1;
   }
   __syncthreads();
+}
+
+// rigid_step_smem for a block whose state lives in global memory (ds_g): the
+// block copies the state into shared memory (8 bytes per thread, one round
+// trip; one thread reading the fields in global memory would wait behind its
+// own earlier stores to the same struct), takes the step there and copies the
+// state back.
+static __device__ void rigid_step_block(const double* red, int64_t M, DevState* ds_g, const EpiParams& ep,
+                                        double* traj, unsigned long long inter_add) {
+  static_assert(sizeof(DevState) % sizeof(unsigned long long) == 0, "state copied in 8-byte words");
+  constexpr int NW = (int)(sizeof(DevState) / sizeof(unsigned long long));
+  static_assert(NW <= EPI_BS_MIN, "one word per thread");
+  __shared__ DevState s_state;
+  unsigned long long* sw = reinterpret_cast<unsigned long long*>(&s_state);
+  unsigned long long* gw = reinterpret_cast<unsigned long long*>(ds_g);
+  const int tid = threadIdx.x;
+  if (tid < NW) sw[tid] = __ldcg(gw + tid);
+  __syncthreads();
+  rigid_step_smem(red, M, &s_state, ep, traj, inter_add);
   if (tid < NW) gw[tid] = sw[tid];
 }
 

@@ -314,6 +314,29 @@ int epilogue_blocks(int64_t M);
 // acc_out[perm[i]] = G * mY[i] * sum of partials (or the acceleration if mY is null).
 int launch_forces_out(const ForceBuffers& fb, int64_t M, const float4* Y0, int use_mass,
                       float G, const int* perm, float* acc_out, cudaStream_t s);
+// The whole iteration loop of a small all-pairs pair in one launch of one
+// thread-block cluster (fga_small.cu), bit-identical to the separate force
+// and epilogue launches. Eligible: N <= FGA_SMALL_LOOP_MAX_N (the sources are
+// staged in shared memory), M <= FGA_SMALL_LOOP_MAX_M and N * M <=
+// FGA_SMALL_LOOP_MAX_TERMS (beyond that the full GPU's separate launches are
+// faster than one cluster's SMs); available: the device holds a cluster of
+// the kernel (checked once per device and tile shape).
+#ifndef FGA_SMALL_LOOP_MAX_N
+#define FGA_SMALL_LOOP_MAX_N 4096
+#endif
+#ifndef FGA_SMALL_LOOP_MAX_M
+#define FGA_SMALL_LOOP_MAX_M 16384
+#endif
+#ifndef FGA_SMALL_LOOP_MAX_TERMS
+#define FGA_SMALL_LOOP_MAX_TERMS (1 << 20)
+#endif
+bool small_loop_eligible(int64_t N, int64_t M, const DirectPlan& plan);
+bool small_loop_available(const DirectPlan& plan);
+// n_iter iterations; the trajectory is written for the first traj_iters.
+int launch_small_loop(const float4* X4, int64_t N, const float4* Y0, int64_t M, DevState* ds, float eps,
+                      const DirectPlan& plan, const ForceBuffers& fb, float4* V, double* partials,
+                      double* traj, int traj_iters, const EpiParams& ep, unsigned long long inter_add,
+                      int n_iter, cudaStream_t s);
 // Initialise DevState (identity transform, mu0 from d_mu0).
 int launch_state_init(DevState* ds, const double* d_mu0, cudaStream_t s);
 
