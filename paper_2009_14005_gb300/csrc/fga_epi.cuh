@@ -103,12 +103,14 @@ static __device__ bool rigid_rotation(const double C[9], double R[9]) {
   return true;
 }
 
-// FP64 on this GPU has long dependent latencies (about 64 cycles per DFMA and
-// over 600 per division or square root), and the rigid fit is one thread's
-// dependency chain on the iteration's critical path. So the chain avoids FP64
-// division and square root: reciprocals are an FP32 seed refined by two
-// Newton steps in FP64 (r <- r + r (1 - d r), 24 -> 48 -> 53 bits), and sums
-// are pairwise.
+// FP64 on this GPU: an FP64 instruction (add, multiply, FMA, and the
+// conversions to and from FP32) occupies its warp's FP64 pipe for about 64
+// cycles, however few of the warp's lanes are active (measured: the same 64
+// cycles per instruction with 1, 9 or 32 active lanes, and for dependent or
+// independent operations). So the rigid fit spreads its 3 x 3 matrices over
+// the lanes of a warp, one entry per lane, and each FP64 step of it is one
+// instruction for all nine entries. Reciprocals are an FP32 seed refined by
+// two Newton steps in FP64 (r <- r + r (1 - d r), 24 -> 48 -> 53 bits).
 __device__ __forceinline__ double rcp64(double d) {
   double r = (double)__frcp_rn((float)d);
   r = fma(r, fma(-d, r, 1.0), r);
@@ -116,20 +118,9 @@ __device__ __forceinline__ double rcp64(double d) {
   return r;
 }
 
-__device__ __forceinline__ double sum9(const double v[9]) {
-  return ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) + v[8];
-}
-
-// Orthogonal polar factor of C by Newton's iteration X <- (X + X^{-T}) / 2
-// (Higham), started from a positive multiple of C. For det C > 0 the limit is
-// U V^T of C = U S V^T, i.e. Eq. 14's rotation (sgn det(U V^T) = +1). The
-// iteration runs on one thread and is the tail of every iteration of
-// Algorithm 2, so its dependent chain matters: the first, scaled steps
-// X <- (g X + X^{-T} / g) / 2, g = (|X^{-1}|_F / |X|_F)^{1/2} (any g > 0 keeps
-// the limit), run in FP32 until the iterate is within about 1e-6 of U V^T;
-// unscaled FP64 steps then converge quadratically to the FP64 fixed point.
-// Returns false when C is not safely positive-determinant (the caller then
-// takes the eigen-decomposition route, which also handles rank deficiency).
+// Cofactor matrix of X (returned det X): entry (r, c) is
+// X[r1][c1] X[r2][c2] - X[r1][c2] X[r2][c1] with r1, r2 = r + 1, r + 2 and
+// c1, c2 = c + 1, c + 2 (mod 3).
 template <class T>
 __device__ __forceinline__ T cof3(const T X[9], T cf[9]) {
   cf[0] = X[4] * X[8] - X[5] * X[7];
@@ -144,18 +135,50 @@ __device__ __forceinline__ T cof3(const T X[9], T cf[9]) {
   return X[0] * cf[0] + X[1] * cf[1] + X[2] * cf[2];  // det X
 }
 
-static __device__ bool polar_rotation(const double C[9], double R[9]) {
-  double sq[9];
-  for (int k = 0; k < 9; ++k) sq[k] = C[k] * C[k];
-  const double nc2 = sum9(sq);
+// Sum of entries 0..8 held one per lane (lanes 0..8), in the order
+// ((v0 + v1) + (v2 + v3)) + ((v4 + v5) + (v6 + v7)) + v8; the same in every lane.
+__device__ __forceinline__ double lane_sum9(double v) {
+  const double a1 = v + __shfl_down_sync(FULL, v, 1);
+  const double a2 = a1 + __shfl_down_sync(FULL, a1, 2);
+  const double a3 = a2 + __shfl_down_sync(FULL, a2, 4);
+  return __shfl_sync(FULL, a3 + __shfl_sync(FULL, v, 8), 0);
+}
+
+// Entry k of a 3 x 3 matrix held in registers by every lane.
+template <class T>
+__device__ __forceinline__ T pick9(const T (&A)[9], int k) {
+  T v = A[0];
+#pragma unroll
+  for (int j = 1; j < 9; ++j) v = k == j ? A[j] : v;
+  return v;
+}
+
+// Orthogonal polar factor of C by Newton's iteration X <- (X + X^{-T}) / 2
+// (Higham), started from a positive multiple of C. For det C > 0 the limit is
+// U V^T of C = U S V^T, i.e. Eq. 14's rotation (sgn det(U V^T) = +1). The
+// first, scaled steps X <- (g X + X^{-T} / g) / 2, g = (|X^{-1}|_F /
+// |X|_F)^{1/2} (any g > 0 keeps the limit), run in FP32 until the iterate is
+// within about 1e-6 of U V^T; unscaled FP64 steps then converge quadratically
+// to the FP64 fixed point: from a converged FP32 iterate (error about 1e-7)
+// one step leaves about 1e-14, far below what the registration resolves, so
+// one step is taken; otherwise steps repeat until they stop moving.
+// Called by all 32 lanes of a warp, with C (identical) in every lane and
+// entry k = min(lane, 8) of C in ck. The FP32 steps run in every lane on
+// the same values; the FP64 steps take one entry per lane. On true, lane
+// k < 9 holds entry k of the rotation in rk. Returns false (in every lane)
+// when C is not safely positive-determinant: the caller then takes the
+// eigen-decomposition route, which also handles rank deficiency.
+static __device__ bool polar_rotation_warp(double ck, int lane, double& rk) {
+  const double nc2 = lane_sum9(ck * ck);  // |C|_F^2
   if (!(nc2 > 0.0) || !isfinite(nc2)) return false;
   const double s0 = (double)rsqrtf((float)nc2);
-  // scaled steps in FP32, |X|_F ~ 1 throughout
-  float Xf[9];
-  for (int k = 0; k < 9; ++k) Xf[k] = (float)(C[k] * s0);
-  // The scale g only speeds the iteration up (any g > 0 keeps the limit) and
-  // the FP32 steps only have to come within about 1e-6 of U V^T, so the
-  // reciprocal and the fourth root are the SFU's approximations.
+  const float xk = (float)(ck * s0);
+  float Xf[9];  // |X|_F ~ 1 throughout
+#pragma unroll
+  for (int j = 0; j < 9; ++j) Xf[j] = __shfl_sync(FULL, xk, j);
+  // The scale g only speeds the iteration up and the FP32 steps only have to
+  // come within about 1e-6 of U V^T, so the reciprocal and the fourth root
+  // are the SFU's approximations.
   bool converged32 = false;
   for (int it = 0; it < 40; ++it) {
     float cf[9];
@@ -188,31 +211,31 @@ static __device__ bool polar_rotation(const double C[9], double R[9]) {
       break;
     }
   }
-  // unscaled steps in FP64 from the FP32 iterate: the error squares per
-  // step. From a converged FP32 iterate (error about 1e-7, FP32 rounding) one
-  // step leaves about 1e-14, far below what the registration resolves, and
-  // a dependent FP64 operation costs a few hundred cycles here: one step.
-  // Otherwise steps repeat until they stop moving.
-  double X[9];
-  for (int k = 0; k < 9; ++k) X[k] = (double)Xf[k];
+  // FP64 steps, entry k = (r, c) per lane; cofactor operands by shuffles
+  const int k = lane < 9 ? lane : 8;
+  const int r = k / 3, c = k - 3 * r;
+  const int r1 = r == 2 ? 0 : r + 1, r2 = r == 0 ? 2 : r - 1;
+  const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
+  double x = (double)pick9(Xf, k);
   for (int it = 0; it < 8; ++it) {
-    double cf[9];
-    const double det = cof3(X, cf);
+    const double xa = __shfl_sync(FULL, x, 3 * r1 + c1), xb = __shfl_sync(FULL, x, 3 * r2 + c2);
+    const double xc = __shfl_sync(FULL, x, 3 * r1 + c2), xd = __shfl_sync(FULL, x, 3 * r2 + c1);
+    const double cf = xa * xb - xc * xd;
+    const double det = __shfl_sync(FULL, x, 0) * __shfl_sync(FULL, cf, 0) +
+                       __shfl_sync(FULL, x, 1) * __shfl_sync(FULL, cf, 1) +
+                       __shfl_sync(FULL, x, 2) * __shfl_sync(FULL, cf, 2);
     if (!(det > 1e-9)) return false;
     const double h = 0.5 * rcp64(det);
+    const double xn = fma(h, cf, 0.5 * x);
     if (converged32) {
-      for (int k = 0; k < 9; ++k) X[k] = fma(h, cf[k], 0.5 * X[k]);
+      x = xn;
       break;
     }
-    double dd[9];
-    for (int k = 0; k < 9; ++k) {
-      const double xn = fma(h, cf[k], 0.5 * X[k]);
-      dd[k] = (xn - X[k]) * (xn - X[k]);
-      X[k] = xn;
-    }
-    if (sum9(dd) < 1e-28) break;
+    const double dd = (xn - x) * (xn - x);
+    x = xn;
+    if (lane_sum9(dd) < 1e-28) break;
   }
-  for (int k = 0; k < 9; ++k) R[k] = X[k];
+  rk = x;
   return true;
 }
 
@@ -244,126 +267,149 @@ constexpr int EPI_BS_MIN = 128;  // fewest threads of a block that calls rigid_s
 // Shared values between the phases of the fit.
 struct FitShared {
   double Rp[9], tp[3];  // R', t' of this iteration
-  double T[12];         // the composed [R | t]
-  double e[12];         // squared differences to [R | t] two iterations back
 };
 
 // Called by every thread of the block that finishes an iteration (Eqs. 14,
 // 16 and Algorithm 2's composition and stop test), with the state in shared
-// memory. A dependent FP64 operation costs a few hundred cycles on this GPU
-// and the fit is the iteration's tail, so its work is spread over the block:
-//  1. thread 0 forms C from the reductions and takes R' (polar or eigen
-//     route) and t';
-//  2. threads 0-11 compose [R | t] entry by entry with the convergence terms,
-//     threads 12-23 the rigid-velocity coefficients;
-//  3. thread 0 sums the convergence terms, updates the flags, the history and
-//     the FP32 copies.
+// memory; needs at least 44 threads. FP64 instructions cost a warp about 64
+// cycles each however few lanes are active, so the matrices of the fit are
+// spread over the lanes of warp 0, one entry per lane:
+//  1. lane k forms entry k of C from the reductions; the warp takes R'
+//     (polar route; the eigen route, or R' = I for a degenerate C, in every
+//     lane when that fails) and lanes 0-2 take t';
+//  2. lanes 0-11 of warp 0 compose [R | t] entry by entry with the
+//     convergence terms, which they add by shuffles; lanes 0-11 of warp 1 take
+//     the rigid-velocity coefficients at the same time;
+//  3. warp 0 updates the flags, the history and the FP32 copies, one entry
+//     per lane.
 // red: the NRED reduced values (shared memory); ds: the state (shared
 // memory), updated in place and visible to the whole block on return.
 static __device__ void rigid_step_smem(const double* red, int64_t M, DevState* ds, const EpiParams& ep,
                                        double* traj, unsigned long long inter_add) {
   __shared__ FitShared f;
   const int tid = threadIdx.x;
-  if (tid == 0) {
+  const int lane = tid & 31;
+  if (tid < 32) {
+    // C = S + Dy - M (ybar + mud) ybar^T: S = sum yc yc^T (symmetric: xx, xy,
+    // xz, yy, yz, zz in red[6..11]), Dy = sum d yc^T, ybar the mean of the
+    // centred template (~0), mud the mean displacement
+    const int k = lane < 9 ? lane : 8;
+    const int r = k / 3, c = k - 3 * r;
+    const int lo = r < c ? r : c, hi = r < c ? c : r;
+    const int si = 6 + (lo == 0 ? hi : (lo == 1 ? 2 + hi : 5));
     const double Md = (double)M;
-    double ybar[3], mud[3];
-    for (int k = 0; k < 3; ++k) {
-      ybar[k] = red[k] * ep.inv_M;     // mean of the centred template (~0)
-      mud[k] = red[3 + k] * ep.inv_M;  // mean displacement
+    const double ybar_r = red[r] * ep.inv_M, mud_r = red[3 + r] * ep.inv_M, ybar_c = red[c] * ep.inv_M;
+    const double ck = red[si] + red[12 + k] - Md * (ybar_r + mud_r) * ybar_c;
+    double rk = 0.0;
+    bool ok;
+    if (ep.dim == 2) {
+      double C[9], Rp[9];
+#pragma unroll
+      for (int j = 0; j < 9; ++j) C[j] = __shfl_sync(FULL, ck, j);
+      ok = planar_rotation(C, Rp);
+      if (ok) rk = pick9(Rp, k);
+    } else {
+      ok = polar_rotation_warp(ck, lane, rk);
+      if (!ok) {
+        double C[9], Rp[9];
+#pragma unroll
+        for (int j = 0; j < 9; ++j) C[j] = __shfl_sync(FULL, ck, j);
+        ok = rigid_rotation(C, Rp);
+        if (ok) rk = pick9(Rp, k);
+      }
     }
-    // symmetric S = sum yc yc^T (xx, xy, xz, yy, yz, zz) and Dy = sum d yc^T
-    const double S[9] = {red[6], red[7], red[8], red[7], red[9], red[10], red[8], red[10], red[11]};
-    double C[9];
-    for (int r = 0; r < 3; ++r)
-      for (int c = 0; c < 3; ++c)
-        C[3 * r + c] = S[3 * r + c] + red[12 + 3 * r + c] - Md * (ybar[r] + mud[r]) * ybar[c];
-    double Rp[9];
-    const bool ok = ep.dim == 2 ? planar_rotation(C, Rp) : (polar_rotation(C, Rp) || rigid_rotation(C, Rp));
     if (!ok) {
-      for (int k = 0; k < 9; ++k) Rp[k] = (k % 4 == 0) ? 1.0 : 0.0;
-      ds->degenerate += 1;
+      rk = (k % 4 == 0) ? 1.0 : 0.0;
+      if (lane == 0) ds->degenerate += 1;
     }
-    // mu_Y = muf + ybar (muf is the FP32 centre the kernels subtracted)
-    double muy[3];
-    for (int k = 0; k < 3; ++k) muy[k] = (double)ds->muf[k] + ybar[k];
-    for (int r = 0; r < 3; ++r)
-      f.tp[r] = muy[r] + mud[r] - (Rp[3 * r] * muy[0] + Rp[3 * r + 1] * muy[1] + Rp[3 * r + 2] * muy[2]);
-    for (int k = 0; k < 9; ++k) f.Rp[k] = Rp[k];
+    if (lane < 9) f.Rp[lane] = rk;
+    // t' = mu_Y + mu_D - R' mu_Y, mu_Y = muf + ybar (muf is the FP32 centre
+    // the kernels subtracted)
+    const int q3 = lane < 3 ? lane : 2;
+    const double muy = (double)ds->muf[q3] + red[q3] * ep.inv_M;
+    const double mu0 = __shfl_sync(FULL, muy, 0), mu1 = __shfl_sync(FULL, muy, 1),
+                 mu2 = __shfl_sync(FULL, muy, 2);
+    __syncwarp();
+    if (lane < 3) {
+      const double mud = red[3 + lane] * ep.inv_M;
+      f.tp[lane] = muy + mud - (f.Rp[3 * lane] * mu0 + f.Rp[3 * lane + 1] * mu1 + f.Rp[3 * lane + 2] * mu2);
+    }
   }
   __syncthreads();
   const int k_it = ds->iter;
-  if (tid < 12) {
-    // [R | t] <- [R'R | R't + t'], one entry per thread
-    const int r = tid < 9 ? tid / 3 : tid - 9;
+  if (tid < 32) {
+    // [R | t] <- [R'R | R't + t'], entry q per lane
+    const int q = lane < 12 ? lane : 11;
     double v;
-    if (tid < 9) {
-      const int c = tid % 3;
+    if (q < 9) {
+      const int r = q / 3, c = q % 3;
       v = f.Rp[3 * r] * ds->R[c] + f.Rp[3 * r + 1] * ds->R[3 + c] + f.Rp[3 * r + 2] * ds->R[6 + c];
     } else {
+      const int r = q - 9;
       v = f.Rp[3 * r] * ds->t[0] + f.Rp[3 * r + 1] * ds->t[1] + f.Rp[3 * r + 2] * ds->t[2] + f.tp[r];
     }
-    f.T[tid] = v;
-    f.e[tid] = (v - ds->Tm2[tid]) * (v - ds->Tm2[tid]);
-  } else if (tid < 24) {
+    const double e = (v - ds->Tm2[q]) * (v - ds->Tm2[q]);
+    // |T_k - T_{k-2}|_F^2 = ((e0 + e1) + (e2 + e3)) + ((e4 + e5) + (e6 + e7)) + ((e8 + e9) + (e10 + e11))
+    const double b1 = e + __shfl_down_sync(FULL, e, 1);
+    const double b2 = b1 + __shfl_down_sync(FULL, b1, 2);
+    const double b3 = b2 + __shfl_down_sync(FULL, b2, 4);
+    const double d2 = b3 + __shfl_sync(FULL, b2, 8);  // lane 0
+    const bool finite = __all_sync(FULL, lane >= 12 || isfinite(v));
+    __syncwarp();  // every lane has read R, t and the history before they change
+    if (lane == 0) {
+      if (k_it >= 2) {
+        ds->last_conv = d2;
+        if (ep.conv_tol > 0 && d2 <= ep.conv_tol) {
+          ds->done = 1;
+          ds->converged = 1;
+        }
+      } else {
+        ds->last_conv = -1.0;
+      }
+      if (!finite) {
+        ds->status |= 2;
+        ds->done = 1;
+      }
+      ds->interactions += inter_add;
+      ds->iter = k_it + 1;
+      if (ep.max_iter > 0 && k_it + 1 >= ep.max_iter) ds->done = 1;
+    }
+    if (lane < 12) {
+      ds->Tm2[lane] = ds->Tm1[lane];
+      ds->Tm1[lane] = v;
+      if (lane < 9) {
+        ds->R[lane] = v;
+        ds->Rf[lane] = (float)v;
+      } else {
+        ds->t[lane - 9] = v;
+        ds->tf[lane - 9] = (float)v;
+      }
+      if (traj && k_it < ep.max_traj) traj[12 * (int64_t)k_it + lane] = v;
+    } else if (lane < 15) {
+      ds->netF[lane - 12] = red[21 + lane - 12];
+    } else if (lane < 18) {
+      ds->torque[lane - 15] = red[24 + lane - 15];
+    }
+    __syncwarp();
+    // the FP32 centre that the kernels subtract (any value near the
+    // template's centroid serves, as long as the fit adds back the same one)
+    if (lane < 3) {
+      const float m0 = (float)ds->mu0[0], m1 = (float)ds->mu0[1], m2 = (float)ds->mu0[2];
+      const int r = lane;
+      ds->muf[r] = fmaf(ds->Rf[3 * r], m0, fmaf(ds->Rf[3 * r + 1], m1, fmaf(ds->Rf[3 * r + 2], m2, ds->tf[r])));
+    }
+  } else if (tid < 44) {
     // rigid velocity of the next iteration: v = (y_new - y_old)/dt with
     // y_old = R'^T (y_new - t'), i.e. v = (I - R'^T)/dt y_new + R'^T t'/dt
     const double idt = ep.inv_dt;
-    const int q = tid - 12;
+    const int q = tid - 32;
     if (q < 9) {
       const int r = q / 3, c = q % 3;
       ds->A[q] = (float)(((r == c ? 1.0 : 0.0) - f.Rp[3 * c + r]) * idt);
-    } else if (q < 12) {
+    } else {
       const int r = q - 9;
       ds->b[r] = (float)((f.Rp[r] * f.tp[0] + f.Rp[3 + r] * f.tp[1] + f.Rp[6 + r] * f.tp[2]) * idt);
     }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    const double* T = f.T;
-    if (k_it >= 2) {
-      const double* e = f.e;
-      const double d2 = (((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7]))) +
-                        ((e[8] + e[9]) + (e[10] + e[11]));
-      ds->last_conv = d2;
-      if (ep.conv_tol > 0 && d2 <= ep.conv_tol) {
-        ds->done = 1;
-        ds->converged = 1;
-      }
-    } else {
-      ds->last_conv = -1.0;
-    }
-    for (int q = 0; q < 12; ++q) {
-      ds->Tm2[q] = ds->Tm1[q];
-      ds->Tm1[q] = T[q];
-    }
-    bool finite = true;
-    for (int q = 0; q < 12; ++q) finite = finite && isfinite(T[q]);
-    if (!finite) {
-      ds->status |= 2;
-      ds->done = 1;
-    }
-    for (int k = 0; k < 9; ++k) {
-      ds->R[k] = T[k];
-      ds->Rf[k] = (float)T[k];
-    }
-    for (int k = 0; k < 3; ++k) {
-      ds->t[k] = T[9 + k];
-      ds->tf[k] = (float)T[9 + k];
-    }
-    // the FP32 centre that the kernels subtract (any value near the
-    // template's centroid serves, as long as the fit adds back the same one)
-    const float m0 = (float)ds->mu0[0], m1 = (float)ds->mu0[1], m2 = (float)ds->mu0[2];
-    for (int r = 0; r < 3; ++r)
-      ds->muf[r] = fmaf(ds->Rf[3 * r], m0, fmaf(ds->Rf[3 * r + 1], m1, fmaf(ds->Rf[3 * r + 2], m2, ds->tf[r])));
-    for (int k = 0; k < 3; ++k) {
-      ds->netF[k] = red[21 + k];
-      ds->torque[k] = red[24 + k];
-    }
-    if (traj && k_it < ep.max_traj)
-      for (int q = 0; q < 12; ++q) traj[12 * (int64_t)k_it + q] = T[q];
-    ds->interactions += inter_add;
-    ds->iter = k_it + 1;
-    if (ep.max_iter > 0 && k_it + 1 >= ep.max_iter) ds->done = 1;
   }
   __syncthreads();
 }
@@ -541,40 +587,53 @@ __device__ __forceinline__ void epi_ode(int64_t i, float4 y0, float sx, float sy
 
 // Block partial of r: FP32 within each warp (a few dozen terms), FP64 across
 // the block's warps in a fixed order; NRED doubles written to out. Every
-// thread of the block must call it.
+// thread of the block must call it. Each warp sum is converted to FP64 by a
+// thread of its own (an FP64 instruction costs the warp the same for one
+// lane as for 32), and NRED lanes add the warp sums at once.
 __device__ __forceinline__ void epi_block_partial(float (&r)[NRED], double* __restrict__ out) {
-  __shared__ double s_w[EPI_BS / 32][NRED];
+  constexpr int NWB = EPI_BS / 32;
+  __shared__ float s_wf[NWB][NRED];
+  __shared__ double s_w[NWB][NRED];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int k = 0; k < NRED; ++k)
     for (int off = 16; off > 0; off >>= 1) r[k] += __shfl_down_sync(FULL, r[k], off);
   if (lane == 0)
 #pragma unroll
-    for (int k = 0; k < NRED; ++k) s_w[w][k] = (double)r[k];
+    for (int k = 0; k < NRED; ++k) s_wf[w][k] = r[k];
+  __syncthreads();
+  if (threadIdx.x < NWB * NRED) {
+    const int ww = threadIdx.x / NRED, k = threadIdx.x - ww * NRED;
+    s_w[ww][k] = (double)s_wf[ww][k];
+  }
   __syncthreads();
   if (threadIdx.x < NRED) {
-    double acc = 0;
-    for (int ww = 0; ww < EPI_BS / 32; ++ww) acc += s_w[ww][threadIdx.x];
+    double acc = s_w[0][threadIdx.x];
+    for (int ww = 1; ww < NWB; ++ww) acc += s_w[ww][threadIdx.x];
     out[threadIdx.x] = acc;
   }
 }
 
 // FP64 sum of nblocks x NRED partials in a fixed order, by the whole block:
 // thread t < 8 NRED adds value t % NRED over blocks t / NRED, + 8, ...;
-// NRED threads then add the 8 strands into s_red (shared, NRED doubles).
-// FP64 adds are scarce on this GPU, so no FP64 warp shuffles are used.
+// NRED threads then add the strands (at most 8) into s_red (shared, NRED
+// doubles). FP64 adds are scarce on this GPU, so no FP64 warp shuffles are
+// used and no zero is added.
 __device__ __forceinline__ void epi_last_reduce(const double* partials, int nblocks, double* s_red) {
   __shared__ double s_strand[8][NRED];
   if (threadIdx.x < 8 * NRED) {
     const int k = threadIdx.x % NRED, j = threadIdx.x / NRED;
-    double acc = 0.0;
-    for (int b = j; b < nblocks; b += 8) acc += __ldcg(&partials[(int64_t)b * NRED + k]);
-    s_strand[j][k] = acc;
+    if (j < nblocks) {
+      double acc = __ldcg(&partials[(int64_t)j * NRED + k]);
+      for (int b = j + 8; b < nblocks; b += 8) acc += __ldcg(&partials[(int64_t)b * NRED + k]);
+      s_strand[j][k] = acc;
+    }
   }
   __syncthreads();
   if (threadIdx.x < NRED) {
-    double acc = 0.0;
-    for (int j = 0; j < 8; ++j) acc += s_strand[j][threadIdx.x];
+    double acc = s_strand[0][threadIdx.x];
+    const int ns = nblocks < 8 ? nblocks : 8;
+    for (int j = 1; j < ns; ++j) acc += s_strand[j][threadIdx.x];
     s_red[threadIdx.x] = acc;
   }
   __syncthreads();
