@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(BS) k_direct(const float4* __restrict__ X, int
 // Tile shape (threads per block, template points per thread) per template
 // size class: M < 8k, M < 64k, M >= 64k. Encoded bs * 16 + qpt; the
 // autotuner may replace the defaults.
-static std::atomic<int> g_direct_tile[3] = {{128 * 16 + 1}, {256 * 16 + 1}, {256 * 16 + 2}};
+static std::atomic<int> g_direct_tile[3] = {{128 * 16 + 2}, {256 * 16 + 1}, {256 * 16 + 2}};
 
 int direct_size_class(int64_t M) { return M < 8 * 1024 ? 0 : (M < 64 * 1024 ? 1 : 2); }
 
