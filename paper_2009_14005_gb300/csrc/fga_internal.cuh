@@ -57,7 +57,8 @@ int sm_count();
 
 // ------------------------------------------------------------------ device state
 // Per-registration state read by the force and epilogue kernels every iteration
-// and written by the rigid-fit step (one thread) at the end of every iteration.
+// and written by the rigid-fit step (the block that finishes an iteration) at
+// the end of every iteration.
 struct DevState {
   double R[9], t[3];      // accumulated transform, normalised frame
   double Tm1[12], Tm2[12];// [R|t] after the previous two iterations
