@@ -162,12 +162,12 @@ __device__ __forceinline__ T pick9(const T (&A)[9], int k) {
 // to the FP64 fixed point: from a converged FP32 iterate (error about 1e-7)
 // one step leaves about 1e-14, far below what the registration resolves, so
 // one step is taken; otherwise steps repeat until they stop moving.
-// Called by all 32 lanes of a warp, with C (identical) in every lane and
-// entry k = min(lane, 8) of C in ck. The FP32 steps run in every lane on
-// the same values; the FP64 steps take one entry per lane. On true, lane
-// k < 9 holds entry k of the rotation in rk. Returns false (in every lane)
-// when C is not safely positive-determinant: the caller then takes the
-// eigen-decomposition route, which also handles rank deficiency.
+// Called by all 32 lanes of a warp, with entry k = min(lane, 8) of C in ck
+// (row-major). The FP32 steps run in every lane on the same values (the nine
+// entries gathered by shuffles); the FP64 steps take one entry per lane. On
+// true, lane k < 9 holds entry k of the rotation in rk. Returns false (in
+// every lane) when C is not safely positive-determinant: the caller then
+// takes the eigen-decomposition route, which also handles rank deficiency.
 static __device__ bool polar_rotation_warp(double ck, int lane, double& rk) {
   const double nc2 = lane_sum9(ck * ck);  // |C|_F^2
   if (!(nc2 > 0.0) || !isfinite(nc2)) return false;

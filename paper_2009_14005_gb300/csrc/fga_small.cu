@@ -27,7 +27,6 @@
 #include <cooperative_groups.h>
 
 #include <algorithm>
-#include <atomic>
 #include <mutex>
 
 #include "fga_device.cuh"
@@ -243,9 +242,9 @@ size_t small_smem_bytes(int64_t N, int bs, int qpt) {
   return (size_t)npad * sizeof(float4) * (qpt % 2 == 0 ? 2 : 1);
 }
 
-// Per device and kernel: the attributes are set once, and the largest
-// cluster (16, else 8) that the device can hold at this kernel's shared
-// memory size is found once (0: none).
+// Per device (ordinals 0-7; others take the separate launches) and kernel:
+// the attributes are set once, and the largest cluster (16, else 8) that the
+// device can hold at this kernel's shared memory size is found once (0: none).
 struct SmallSetup {
   std::mutex mu;
   int max_cluster[8][6] = {};  // [device][tile shape], -1 unknown
