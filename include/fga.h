@@ -312,7 +312,12 @@ int fga_state_create(const float* Xn, const float* mX, int64_t N, const float* Y
  * synchronisation: Y = R Y0 + t; forces (Eq. 6 or BHForce); V, D (Eqs. 7-10);
  * rigid fit R', t' (Eqs. 14, 16, FP64 reduction and 3x3 SVD on the device);
  * R = R'R, t = R't + t'; convergence test. Once the test has fired, further
- * iterations are no-ops. Errors: FGA_EINVAL (n_iter < 0), FGA_ECUDA. */
+ * iterations are no-ops. The iterations run as one CUDA graph of force and
+ * epilogue launches; an all-pairs state with N <= 4096, M <= 16384 and
+ * N * M <= 2^20 runs them in one launch of one thread-block cluster instead,
+ * with bit-identical results. With p->profile = 1 the launches are plain,
+ * one force and one epilogue launch per iteration. Errors: FGA_EINVAL
+ * (n_iter < 0), FGA_ECUDA. */
 int fga_step(fga_state* s, int n_iter, void* stream);
 
 /* Synchronises `stream` and reads the state: R (row-major, 9) and t (3) in the
