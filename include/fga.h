@@ -153,6 +153,22 @@ int fga_normalize(const float* X, int64_t N, const float* Y, int64_t M, float a,
 void fga_denormalize(const double R[9], const double t_norm[3], const double info[8], float a,
                      double t_out[3]);
 
+/* One rigid fit of Algorithm 2 (Eqs. 14 and 16) from reduced sums, on the
+ * device, by the code every iteration of fga_step runs. With yc = y - c for a
+ * template of M points y, displacements d, and the centre c = mu0 rounded to
+ * FP32 (the centre the iteration kernels subtract), red (host, 27 doubles)
+ * holds sum yc (3), sum d (3), S = sum yc yc^T as xx, xy, xz, yy, yz, zz (6),
+ * sum d yc^T row-major (9), then 6 values the fit only copies (net force,
+ * torque). The fit forms C = sum (y + d - mu_Y - mu_D)(y - mu_Y)^T, takes
+ * R' = U diag(1, 1, sgn det(U V^T)) V^T of C = U S V^T (Eq. 14; R' = I when
+ * sigma_2 <= 1e-7 sigma_1) and t' = mu_Y + mu_D - R' mu_Y (Eq. 16); dim = 2
+ * takes the 2 x 2 fit of the x, y block. R_out (row-major 9) and t_out (3)
+ * are host arrays. Synchronises `stream`. Returns FGA_EDEGENERATE for a
+ * degenerate C (R' = I, t' = mu_D); FGA_EINVAL for M <= 0, dim not 2 or 3,
+ * or a non-finite sum. */
+int fga_rigid_fit(const double red[27], int64_t M, const double mu0[3], int dim, double R_out[9],
+                  double t_out[3], void* stream);
+
 /* ----------------------------------------------------------------- Sec. IV-F */
 /* Point masses (boundary conditions, Sec. IV-F), scaled so that they sum to
  * `total`. mode = FGA_MASS_KNN: m_i ~ r_k(i)^3, r_k the distance to the k-th
@@ -160,9 +176,11 @@ void fga_denormalize(const double R[9], const double t_norm[3], const double inf
  * mode = FGA_MASS_UNIFORM gives total/n each; FGA_MASS_NIV evaluates
  * Eq. 18 on a lattice^3 lattice over [a, b]^3 (points are expected inside the
  * normalised domain; outside points are clamped to the border cells): each
- * point carries a ball of radius (b-a)/(2*3*lattice), a cell holding n points
- * is covered to the fraction f = 1 - (1 - V(ball)/V(cell))^n, and a point's
- * weight is 1/f of its cell.
+ * point carries a ball of radius (b-a)/(2*3*lattice) centred at the point
+ * clamped to [a, b]^3, a cell is covered to the fraction f = V(union of its
+ * points' balls, inside the cell) / V(cell) (exact along the cell's last
+ * axis, where the balls cut chords on a line; midpoint rule on 64 x 64 lines
+ * across it), and a point's weight is 1/f of its cell.
  * pts: device (n x 3); masses_out: device (n). lattice in 1..256.
  * Errors: FGA_EINVAL for n <= 0, bad mode/lattice, b <= a, total <= 0. */
 int fga_masses(const float* pts, int64_t n, int mode, int lattice, float a, float b,

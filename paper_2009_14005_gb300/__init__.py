@@ -62,7 +62,7 @@ SYMBOLS = [
     "fga_forces_direct_static", "fga_register_batch", "fga_direct_max_n",
     "fga_server_create", "fga_server_submit", "fga_server_poll", "fga_server_stats_get",
     "fga_server_destroy", "fga_autotune", "fga_set_direct_tile", "fga_get_direct_tile",
-    "fga_masses_landmarks", "fga_forces_terms",
+    "fga_masses_landmarks", "fga_forces_terms", "fga_rigid_fit",
 ]
 FGA_STATIC_SCRATCH_FLOAT4 = 524288
 FGA_STATIC_STATE_FLOAT4 = 33
@@ -193,6 +193,7 @@ def _load():
         "fga_register": (ctypes.c_int, [P, I64, P, I64, P, P, PP, DP, DP,
                                         ctypes.POINTER(fga_stats), VP]),
         "fga_forces_direct_static": (ctypes.c_int, [P, P, I64, P, P, I64, PP, P, VP]),
+        "fga_rigid_fit": (ctypes.c_int, [DP, I64, DP, ctypes.c_int, DP, DP, VP]),
         "fga_register_batch": (ctypes.c_int, [ctypes.POINTER(fga_pair), ctypes.c_int, PP,
                                               ctypes.POINTER(fga_pair_result),
                                               ctypes.POINTER(fga_stats), VP]),
@@ -512,6 +513,21 @@ def fga_state_trajectory(state: State, n: int, stream=None):
     if rows < 0:
         _err(rows)
     return out[:rows]
+
+
+def fga_rigid_fit(red, M: int, mu0, dim: int = 3, stream=None):
+    """One rigid fit (Eqs. 14, 16) on the device from the 27 reduced sums
+    (see include/fga.h); returns (R', t', status)."""
+    red = np.ascontiguousarray(np.asarray(red, dtype=np.float64))
+    mu0 = np.ascontiguousarray(np.asarray(mu0, dtype=np.float64))
+    if red.shape != (27,) or mu0.shape != (3,):
+        raise ValueError("fga_rigid_fit: red must hold 27 values and mu0 3")
+    R = np.zeros(9)
+    t = np.zeros(3)
+    code = lib.fga_rigid_fit(_dp(red), int(M), _dp(mu0), int(dim), _dp(R), _dp(t), _stream(stream))
+    if code not in (FGA_OK, FGA_EDEGENERATE):
+        _err(code)
+    return R.reshape(3, 3), t, code
 
 
 def fga_register(X, Y, p: fga_params | None = None, mX=None, mY=None, stream=None):

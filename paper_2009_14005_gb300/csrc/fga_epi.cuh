@@ -153,6 +153,18 @@ __device__ __forceinline__ T pick9(const T (&A)[9], int k) {
   return v;
 }
 
+// Cofactor (r, c) of a 3 x 3 matrix held one entry per lane (lane 3 r + c):
+// a[r1][c1] a[r2][c2] - a[r1][c2] a[r2][c1] with r1, r2 = r + 1, r + 2 and c1,
+// c2 = c + 1, c + 2 (mod 3); det = a0 cf0 + a1 cf1 + a2 cf2 in every lane.
+__device__ __forceinline__ double lane_cof3(double a, int r1, int r2, int c1, int c2, double& det) {
+  const double xa = __shfl_sync(FULL, a, 3 * r1 + c1), xb = __shfl_sync(FULL, a, 3 * r2 + c2);
+  const double xc = __shfl_sync(FULL, a, 3 * r1 + c2), xd = __shfl_sync(FULL, a, 3 * r2 + c1);
+  const double cf = xa * xb - xc * xd;
+  det = __shfl_sync(FULL, a, 0) * __shfl_sync(FULL, cf, 0) + __shfl_sync(FULL, a, 1) * __shfl_sync(FULL, cf, 1) +
+        __shfl_sync(FULL, a, 2) * __shfl_sync(FULL, cf, 2);
+  return cf;
+}
+
 // Orthogonal polar factor of C by Newton's iteration X <- (X + X^{-T}) / 2
 // (Higham), started from a positive multiple of C. For det C > 0 the limit is
 // U V^T of C = U S V^T, i.e. Eq. 14's rotation (sgn det(U V^T) = +1). The
@@ -160,8 +172,9 @@ __device__ __forceinline__ T pick9(const T (&A)[9], int k) {
 // |X|_F)^{1/2} (any g > 0 keeps the limit), run in FP32 until the iterate is
 // within about 1e-6 of U V^T; unscaled FP64 steps then converge quadratically
 // to the FP64 fixed point: from a converged FP32 iterate (error about 1e-7)
-// one step leaves about 1e-14, far below what the registration resolves, so
-// one step is taken; otherwise steps repeat until they stop moving.
+// one step leaves an orthogonal matrix to FP64 precision, so one step is
+// taken (otherwise steps repeat until they stop moving); a last correction
+// against C (below) then moves it onto C's own polar factor.
 // Called by all 32 lanes of a warp, with entry k = min(lane, 8) of C in ck
 // (row-major). The FP32 steps run in every lane on the same values (the nine
 // entries gathered by shuffles); the FP64 steps take one entry per lane. On
@@ -218,12 +231,8 @@ static __device__ bool polar_rotation_warp(double ck, int lane, double& rk) {
   const int c1 = c == 2 ? 0 : c + 1, c2 = c == 0 ? 2 : c - 1;
   double x = (double)pick9(Xf, k);
   for (int it = 0; it < 8; ++it) {
-    const double xa = __shfl_sync(FULL, x, 3 * r1 + c1), xb = __shfl_sync(FULL, x, 3 * r2 + c2);
-    const double xc = __shfl_sync(FULL, x, 3 * r1 + c2), xd = __shfl_sync(FULL, x, 3 * r2 + c1);
-    const double cf = xa * xb - xc * xd;
-    const double det = __shfl_sync(FULL, x, 0) * __shfl_sync(FULL, cf, 0) +
-                       __shfl_sync(FULL, x, 1) * __shfl_sync(FULL, cf, 1) +
-                       __shfl_sync(FULL, x, 2) * __shfl_sync(FULL, cf, 2);
+    double det;
+    const double cf = lane_cof3(x, r1, r2, c1, c2, det);
     if (!(det > 1e-9)) return false;
     const double h = 0.5 * rcp64(det);
     const double xn = fma(h, cf, 0.5 * x);
@@ -234,6 +243,40 @@ static __device__ bool polar_rotation_warp(double ck, int lane, double& rk) {
     const double dd = (xn - x) * (xn - x);
     x = xn;
     if (lane_sum9(dd) < 1e-28) break;
+  }
+  // Newton's iteration keeps the singular vectors of its start, so its limit
+  // is the polar factor of the FP32 iterate, whose rotation still carries the
+  // FP32 steps' rounding (about 1e-9). One correction against C itself
+  // removes it. With Q0 = x (orthogonal to FP64 precision) and C = Q H (H
+  // symmetric positive definite), M = Q0^T C = R_d H, R_d = Q0^T Q =
+  // exp([w]x); to first order in w, M - M^T = [w]x H + H [w]x =
+  // [(tr H I - H) w]x with H = (M + M^T) / 2, so w solves
+  // (tr H I - H) w = axial(M - M^T), and Q = Q0 (I + [w]x), whose row r is
+  // q_r + q_r x w, up to an error of order |w|^2. C enters scaled to unit
+  // Frobenius norm (w does not depend on the scale).
+  {
+    const double cs = ck * s0;
+    const double m = __shfl_sync(FULL, x, r) * __shfl_sync(FULL, cs, c) +
+                     __shfl_sync(FULL, x, 3 + r) * __shfl_sync(FULL, cs, 3 + c) +
+                     __shfl_sync(FULL, x, 6 + r) * __shfl_sync(FULL, cs, 6 + c);
+    const double trh = __shfl_sync(FULL, m, 0) + __shfl_sync(FULL, m, 4) + __shfl_sync(FULL, m, 8);
+    const double a = (r == c ? trh : 0.0) - 0.5 * (m + __shfl_sync(FULL, m, 3 * c + r));
+    double deta;
+    const double cfa = lane_cof3(a, r1, r2, c1, c2, deta);
+    if (deta > 1e-30) {
+      // axial(M - M^T) = (m21 - m12, m02 - m20, m10 - m01); A = tr H I - H is
+      // symmetric, so A^{-1} = cof(A) / det A; lane j < 3 takes w_j
+      const double ax0 = __shfl_sync(FULL, m, 7) - __shfl_sync(FULL, m, 5);
+      const double ax1 = __shfl_sync(FULL, m, 2) - __shfl_sync(FULL, m, 6);
+      const double ax2 = __shfl_sync(FULL, m, 3) - __shfl_sync(FULL, m, 1);
+      const int j = lane < 3 ? lane : 2;
+      const double wj = (__shfl_sync(FULL, cfa, 3 * j) * ax0 + __shfl_sync(FULL, cfa, 3 * j + 1) * ax1 +
+                         __shfl_sync(FULL, cfa, 3 * j + 2) * ax2) * rcp64(deta);
+      const double w0 = __shfl_sync(FULL, wj, 0), w1 = __shfl_sync(FULL, wj, 1), w2 = __shfl_sync(FULL, wj, 2);
+      const double wc1 = c1 == 0 ? w0 : (c1 == 1 ? w1 : w2), wc2 = c2 == 0 ? w0 : (c2 == 1 ? w1 : w2);
+      // entry c of q_r x w: q_r[c + 1] w[c + 2] - q_r[c + 2] w[c + 1]
+      x += __shfl_sync(FULL, x, 3 * r + c1) * wc2 - __shfl_sync(FULL, x, 3 * r + c2) * wc1;
+    }
   }
   rk = x;
   return true;
