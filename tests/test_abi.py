@@ -135,3 +135,19 @@ def test_host_tables_round_trip(fga):
         for c, (bs, q) in enumerate(saved):
             fga.set_direct_tile(c, bs, q)
         fga.fga_direct_max_n(old_n)
+
+
+def test_rigid_fit_rejects_bad_arguments_without_gpu_work(fga):
+    red = np.zeros(27)
+    R, t = np.zeros(9), np.zeros(3)
+    dp = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))  # noqa: E731
+    mu0 = np.zeros(3)
+    assert fga.lib.fga_rigid_fit(dp(red), 0, dp(mu0), 3, dp(R), dp(t), None) == fga.FGA_EINVAL
+    assert fga.lib.fga_rigid_fit(dp(red), 10, dp(mu0), 4, dp(R), dp(t), None) == fga.FGA_EINVAL
+    assert fga.lib.fga_rigid_fit(None, 10, dp(mu0), 3, dp(R), dp(t), None) == fga.FGA_EINVAL
+    bad = red.copy()
+    bad[20] = np.inf
+    assert fga.lib.fga_rigid_fit(dp(bad), 10, dp(mu0), 3, dp(R), dp(t), None) == fga.FGA_EINVAL
+    assert "non-finite" in fga.last_error()
+    with pytest.raises(ValueError):
+        fga.fga_rigid_fit(np.zeros(26), 10, mu0)
